@@ -1,0 +1,733 @@
+/*
+ * teno7_oracle.c -- plain, slow, FP64 oracle for the extended seventh-order
+ * TENO scheme ("TENO7-ext") of F. Zhang, J. Liu, H. Zhang, C. Xu,
+ * "An extending strategy based on TENO framework for hyperbolic conservation
+ * laws", arXiv:1808.00037.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path loads this library:
+ * only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg do.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * It runs the method step by step, in the paper's order:
+ *   pass 1 -- every face's five-point smoothness measure and cutoff bits
+ *             (Eqs. smooth_expl, tau5, TENO1, norm, seclect; epsilon = dx^3,
+ *             Sec. "The parameter epsilon"), stored for the whole field
+ *             (Sec. "The stencil-selection procedure": measure first, then
+ *             reconstruct);
+ *   pass 2 -- the binary vector Delta_i (Eq. vec) from this face's and the two
+ *             neighbouring faces' bits, the selection of Table co3, and the
+ *             polynomial of Table co2;
+ * inside the conservative finite-difference form (Eq. app), characteristic-wise
+ * with Roe-averaged eigenvectors and global Lax-Friedrichs splitting
+ * (Remark 3; Sec. "One dimensional Euler equations"), and the third-order SSP
+ * Runge-Kutta method (Sec. "The fundamental of the spatial solution").
+ *
+ * Build with -O2 -ffp-contract=off and without fast-math, so that each
+ * expression is evaluated exactly as written, one IEEE operation at a time.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ENONPHYSICAL (-3)
+#define OR_ENONFINITE (-4)
+
+#define SYS_ADVECTION 0
+#define SYS_EULER1D 1
+#define SYS_EULER2D 2
+#define SYS_BURGERS 3
+
+#define BC_PERIODIC 0
+#define BC_ZERO_GRADIENT 1
+
+#define NG 4 /* ghost cells per side */
+
+/* ------------------------------------------------------------------------ */
+/* Table co2: coefficients a_{m,l} of the 13 candidate polynomials on        */
+/* f_{i-3} .. f_{i+3}, rows exactly as printed.                              */
+/* ------------------------------------------------------------------------ */
+static const double COEF[13][7] = {
+    {-1.0 / 140.0, 5.0 / 84.0, -101.0 / 420.0, 319.0 / 420.0, 107.0 / 210.0, -19.0 / 210.0, 1.0 / 105.0},
+    {0.0, 1.0 / 60.0, -2.0 / 15.0, 37.0 / 60.0, 37.0 / 60.0, -2.0 / 15.0, 1.0 / 60.0},
+    {-1.0 / 60.0, 7.0 / 60.0, -23.0 / 60.0, 19.0 / 20.0, 11.0 / 30.0, -1.0 / 30.0, 0.0},
+    {0.0, 0.0, -1.0 / 20.0, 9.0 / 20.0, 47.0 / 60.0, -13.0 / 60.0, 1.0 / 30.0},
+    {0.0, 1.0 / 30.0, -13.0 / 60.0, 47.0 / 60.0, 9.0 / 20.0, -1.0 / 20.0, 0.0},
+    {-1.0 / 20.0, 17.0 / 60.0, -43.0 / 60.0, 77.0 / 60.0, 1.0 / 5.0, 0.0, 0.0},
+    {0.0, 0.0, 0.0, 1.0 / 4.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0},
+    {0.0, 0.0, -1.0 / 12.0, 7.0 / 12.0, 7.0 / 12.0, -1.0 / 12.0, 0.0},
+    {0.0, 1.0 / 12.0, -5.0 / 12.0, 13.0 / 12.0, 1.0 / 4.0, 0.0, 0.0},
+    {-1.0 / 4.0, 13.0 / 12.0, -23.0 / 12.0, 25.0 / 12.0, 0.0, 0.0, 0.0},
+    {0.0, 0.0, 0.0, 1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
+    {0.0, 0.0, -1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0, 0.0},
+    {0.0, 1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0, 0.0},
+};
+
+/* Table co3: the binary vector Delta_i = (d_{i-1,0}, d_{i,0}, d_{i,1},
+ * d_{i,2}, d_{i+1,2}) selects polynomial m; '*' matches 0 or 1.  The pattern
+ * (*,0,0,0,*) is marked "no exist" in the table and has no row here. */
+static const char *PATTERN[13] = {
+    "11111", /* f0 */
+    "01111", /* f1 */
+    "11110", /* f2 */
+    "*0111", /* f3 */
+    "01110", /* f4 */
+    "1110*", /* f5 */
+    "**011", /* f6 */
+    "*0110", /* f7 */
+    "0110*", /* f8 */
+    "1100*", /* f9 */
+    "**010", /* f10 */
+    "*010*", /* f11 */
+    "0100*", /* f12 */
+};
+
+void or_coeffs(double *out /* 13*7 */) {
+    for (int m = 0; m < 13; m++)
+        for (int t = 0; t < 7; t++) out[m * 7 + t] = COEF[m][t];
+}
+
+/* Delta packed as an integer: bit 4 = first component d_{i-1,0}, ...,
+ * bit 0 = last component d_{i+1,2}.  Returns m, or -1 for "no exist". */
+int or_select(int Delta) {
+    int d[5];
+    for (int c = 0; c < 5; c++) d[c] = (Delta >> (4 - c)) & 1;
+    for (int m = 0; m < 13; m++) {
+        int match = 1;
+        for (int c = 0; c < 5; c++) {
+            char p = PATTERN[m][c];
+            if (p != '*' && (p - '0') != d[c]) match = 0;
+        }
+        if (match) return m;
+    }
+    return -1;
+}
+
+/* Five-point smoothness measure of one window w0..w4 = f_{i-2}..f_{i+2}
+ * (upwind order), Eqs. smooth_expl, tau5, TENO1 (C = 1, q = 6), norm and
+ * seclect.  Returns bits d0 | d1<<1 | d2<<2, delta_k = 0 iff chi_k < CT.
+ * beta_out (nullable) receives beta_0..2. */
+int or_face_bits(const double *w, double eps, double CT, double *beta_out) {
+    double s0a = w[0] - 4.0 * w[1] + 3.0 * w[2];
+    double s0b = w[0] - 2.0 * w[1] + w[2];
+    double s1a = w[1] - w[3];
+    double s1b = w[1] - 2.0 * w[2] + w[3];
+    double s2a = 3.0 * w[2] - 4.0 * w[3] + w[4];
+    double s2b = w[2] - 2.0 * w[3] + w[4];
+    double beta[3];
+    beta[0] = 0.25 * (s0a * s0a) + (13.0 / 12.0) * (s0b * s0b);
+    beta[1] = 0.25 * (s1a * s1a) + (13.0 / 12.0) * (s1b * s1b);
+    beta[2] = 0.25 * (s2a * s2a) + (13.0 / 12.0) * (s2b * s2b);
+    double tau = fabs(beta[0] - beta[2]);
+    double gam[3];
+    for (int k = 0; k < 3; k++) {
+        double g = 1.0 + tau / (beta[k] + eps);
+        double g2 = g * g;
+        gam[k] = (g2 * g2) * g2; /* (C + tau/(beta+eps))^6 */
+    }
+    double S = (gam[0] + gam[1]) + gam[2];
+    int bits = 0;
+    for (int k = 0; k < 3; k++) {
+        double chi = gam[k] / S;
+        int delta = (chi < CT) ? 0 : 1;
+        bits |= delta << k;
+    }
+    if (beta_out) {
+        beta_out[0] = beta[0];
+        beta_out[1] = beta[1];
+        beta_out[2] = beta[2];
+    }
+    return bits;
+}
+
+/* Delta_i for the '+' (left-biased) split at face i+1/2 from the stored
+ * three-bit codes of faces i-1/2 (dm), i+1/2 (d0), i+3/2 (dp) (Eq. vec); the
+ * '-' split is its mirror image, with the roles of dm and dp exchanged by the
+ * caller. */
+static int pack_delta(int dm, int d0, int dp) {
+    int v0 = dm & 1, v1 = d0 & 1, v2 = (d0 >> 1) & 1, v3 = (d0 >> 2) & 1, v4 = (dp >> 2) & 1;
+    return (v0 << 4) | (v1 << 3) | (v2 << 2) | (v3 << 1) | v4;
+}
+
+static double poly(int m, const double *v) {
+    double s = 0.0;
+    for (int t = 0; t < 7; t++) s = s + COEF[m][t] * v[t];
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scalar reconstruction of one sequence of point values.                    */
+/*   v[0 .. n+7]  values at cells -4 .. n+3 (caller-padded)                  */
+/*   sign = +1: upwind from the left; sign = -1: the mirror image            */
+/*   fhat[0 .. n]  face values at i+1/2, i = -1 .. n-1                       */
+/*   d3[0 .. n+2]  (nullable) three-bit codes of faces -2 .. n               */
+/*   D5[0 .. n]    (nullable) five-bit Delta of faces -1 .. n-1              */
+/* ------------------------------------------------------------------------ */
+int or_teno7_reconstruct(const double *v, int n, int sign, double eps, double CT, double *fhat, uint8_t *d3,
+                         uint8_t *D5) {
+    if (n < 1 || (sign != 1 && sign != -1)) return OR_EINVAL;
+    int nf = n + 3;
+    int *bits = (int *)malloc(sizeof(int) * nf);
+    const double *c = v + NG; /* c[l] = value at cell l */
+    int status = OR_OK;
+    for (int j = -2; j <= n; j++) {
+        double w[5];
+        for (int t = 0; t < 5; t++) w[t] = (sign > 0) ? c[j - 2 + t] : c[j + 3 - t];
+        bits[j + 2] = or_face_bits(w, eps, CT, NULL);
+        if (d3) d3[j + 2] = (uint8_t)bits[j + 2];
+    }
+    for (int i = -1; i <= n - 1; i++) {
+        int D = (sign > 0) ? pack_delta(bits[i + 1], bits[i + 2], bits[i + 3])
+                           : pack_delta(bits[i + 3], bits[i + 2], bits[i + 1]);
+        int m = or_select(D);
+        if (m < 0) {
+            m = 11;
+            status = OR_ENONFINITE;
+        }
+        double vv[7];
+        for (int t = 0; t < 7; t++) vv[t] = (sign > 0) ? c[i - 3 + t] : c[i + 4 - t];
+        fhat[i + 1] = poly(m, vv);
+        if (D5) D5[i + 1] = (uint8_t)D;
+    }
+    free(bits);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Physical systems.                                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int sys;
+    int m;
+    double gamma;
+    double a; /* advection speed */
+} sysdef;
+
+static int nvars_of(int sys) { return sys == SYS_EULER1D ? 3 : (sys == SYS_EULER2D ? 4 : 1); }
+
+/* Physical flux along the sweep direction; for 2D Euler, dir 0 = x, 1 = y. */
+static void flux(const sysdef *S, int dir, const double *U, double *F) {
+    if (S->sys == SYS_ADVECTION) {
+        F[0] = S->a * U[0];
+    } else if (S->sys == SYS_BURGERS) {
+        F[0] = 0.5 * U[0] * U[0];
+    } else if (S->sys == SYS_EULER1D) {
+        double u = U[1] / U[0];
+        double p = (S->gamma - 1.0) * (U[2] - 0.5 * U[1] * u);
+        F[0] = U[1];
+        F[1] = U[1] * u + p;
+        F[2] = u * (U[2] + p);
+    } else {
+        double u = U[1] / U[0];
+        double v = U[2] / U[0];
+        double p = (S->gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+        if (dir == 0) {
+            F[0] = U[1];
+            F[1] = U[1] * u + p;
+            F[2] = U[2] * u;
+            F[3] = u * (U[3] + p);
+        } else {
+            F[0] = U[2];
+            F[1] = U[1] * v;
+            F[2] = U[2] * v + p;
+            F[3] = v * (U[3] + p);
+        }
+    }
+}
+
+/* Largest characteristic speed of one cell along dir; sets *bad on a
+ * non-physical or non-finite state. */
+static double wavespeed(const sysdef *S, int dir, const double *U, int *bad) {
+    if (S->sys == SYS_ADVECTION) return fabs(S->a);
+    if (S->sys == SYS_BURGERS) {
+        if (!isfinite(U[0])) *bad |= 2;
+        return fabs(U[0]);
+    }
+    if (S->sys == SYS_EULER1D) {
+        double u = U[1] / U[0];
+        double p = (S->gamma - 1.0) * (U[2] - 0.5 * U[1] * u);
+        double c = sqrt(S->gamma * p / U[0]);
+        if (!(U[0] > 0.0) || !(p > 0.0)) *bad |= 1;
+        if (!isfinite(U[0]) || !isfinite(U[1]) || !isfinite(U[2])) *bad |= 2;
+        return fabs(u) + c;
+    }
+    double u = U[1] / U[0];
+    double v = U[2] / U[0];
+    double p = (S->gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+    double c = sqrt(S->gamma * p / U[0]);
+    if (!(U[0] > 0.0) || !(p > 0.0)) *bad |= 1;
+    if (!isfinite(U[0]) || !isfinite(U[1]) || !isfinite(U[2]) || !isfinite(U[3])) *bad |= 2;
+    return (dir == 0 ? fabs(u) : fabs(v)) + c;
+}
+
+/* Roe-averaged left (L, rows) and right (R, columns) eigenvectors of the flux
+ * Jacobian at the face between states UL and UR (Remark 3).  Field order:
+ * 1D Euler (u-c, u, u+c); 2D Euler along dir (un-c, un, shear, un+c).
+ * Scalar systems: L = R = 1.  Returns nonzero if the Roe state has c^2 <= 0. */
+static int frame(const sysdef *S, int dir, const double *UL, const double *UR, double L[4][4], double R[4][4]) {
+    if (S->m == 1) {
+        L[0][0] = 1.0;
+        R[0][0] = 1.0;
+        return 0;
+    }
+    double g = S->gamma;
+    if (S->sys == SYS_EULER1D) {
+        double rl = UL[0], rr = UR[0];
+        double ul = UL[1] / rl, ur = UR[1] / rr;
+        double pl = (g - 1.0) * (UL[2] - 0.5 * UL[1] * ul);
+        double pr = (g - 1.0) * (UR[2] - 0.5 * UR[1] * ur);
+        double Hl = (UL[2] + pl) / rl, Hr = (UR[2] + pr) / rr;
+        double sl = sqrt(rl), sr = sqrt(rr);
+        double ut = (sl * ul + sr * ur) / (sl + sr);
+        double Ht = (sl * Hl + sr * Hr) / (sl + sr);
+        double c2 = (g - 1.0) * (Ht - 0.5 * ut * ut);
+        double c = sqrt(c2);
+        double b1 = (g - 1.0) / c2;
+        double b2 = 0.5 * ut * ut * b1;
+        R[0][0] = 1.0;            R[0][1] = 1.0;           R[0][2] = 1.0;
+        R[1][0] = ut - c;         R[1][1] = ut;            R[1][2] = ut + c;
+        R[2][0] = Ht - ut * c;    R[2][1] = 0.5 * ut * ut; R[2][2] = Ht + ut * c;
+        L[0][0] = 0.5 * (b2 + ut / c); L[0][1] = -0.5 * (b1 * ut + 1.0 / c); L[0][2] = 0.5 * b1;
+        L[1][0] = 1.0 - b2;            L[1][1] = b1 * ut;                   L[1][2] = -b1;
+        L[2][0] = 0.5 * (b2 - ut / c); L[2][1] = -0.5 * (b1 * ut - 1.0 / c); L[2][2] = 0.5 * b1;
+        return !(c2 > 0.0);
+    }
+    /* 2D Euler: work in rotated order (rho, rho*un, rho*ut, E), then map back
+     * to the physical order (rho, rho*u, rho*v, E). */
+    int in = (dir == 0) ? 1 : 2, it = (dir == 0) ? 2 : 1;
+    double rl = UL[0], rr = UR[0];
+    double unl = UL[in] / rl, unr = UR[in] / rr;
+    double utl = UL[it] / rl, utr = UR[it] / rr;
+    double pl = (g - 1.0) * (UL[3] - 0.5 * (UL[1] * (UL[1] / rl) + UL[2] * (UL[2] / rl)));
+    double pr = (g - 1.0) * (UR[3] - 0.5 * (UR[1] * (UR[1] / rr) + UR[2] * (UR[2] / rr)));
+    double Hl = (UL[3] + pl) / rl, Hr = (UR[3] + pr) / rr;
+    double sl = sqrt(rl), sr = sqrt(rr);
+    double un = (sl * unl + sr * unr) / (sl + sr);
+    double vt = (sl * utl + sr * utr) / (sl + sr);
+    double Ht = (sl * Hl + sr * Hr) / (sl + sr);
+    double q2 = 0.5 * (un * un + vt * vt);
+    double c2 = (g - 1.0) * (Ht - q2);
+    double c = sqrt(c2);
+    double b1 = (g - 1.0) / c2;
+    double b2 = q2 * b1;
+    double Rr[4][4] = {
+        {1.0, 1.0, 0.0, 1.0},
+        {un - c, un, 0.0, un + c},
+        {vt, vt, 1.0, vt},
+        {Ht - un * c, q2, vt, Ht + un * c},
+    };
+    double Lr[4][4] = {
+        {0.5 * (b2 + un / c), -0.5 * (b1 * un + 1.0 / c), -0.5 * (b1 * vt), 0.5 * b1},
+        {1.0 - b2, b1 * un, b1 * vt, -b1},
+        {-vt, 0.0, 1.0, 0.0},
+        {0.5 * (b2 - un / c), -0.5 * (b1 * un - 1.0 / c), -0.5 * (b1 * vt), 0.5 * b1},
+    };
+    int perm[4] = {0, in, it, 3}; /* rotated index r <-> physical index perm[r] */
+    for (int k = 0; k < 4; k++)
+        for (int r = 0; r < 4; r++) {
+            L[k][perm[r]] = Lr[k][r];
+            R[perm[r]][k] = Rr[r][k];
+        }
+    return !(c2 > 0.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One directional sweep over a line of n cells with stride 1 in a padded    */
+/* buffer P (m variables, each n + 2*NG long, cell l at P[c][l+NG]).          */
+/* Writes the face fluxes Fh[c][i+1], i = -1..n-1 (face i+1/2) and, if masks  */
+/* is non-null, the Delta codes masks[(s*m + k)*(n+1) + i+1].                 */
+/* ------------------------------------------------------------------------ */
+static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, double eps, double CT, double **Fh,
+                 uint8_t *masks) {
+    int m = S->m, np = n + 2 * NG;
+    int status = OR_OK;
+    /* global Lax-Friedrichs split fluxes G+- = (F +- alpha U)/2 per cell */
+    double *Gp = (double *)malloc(sizeof(double) * m * np);
+    double *Gm = (double *)malloc(sizeof(double) * m * np);
+    for (int l = 0; l < np; l++) {
+        double U[4], F[4];
+        for (int c = 0; c < m; c++) U[c] = P[c][l];
+        flux(S, dir, U, F);
+        for (int c = 0; c < m; c++) {
+            Gp[c * np + l] = 0.5 * (F[c] + alpha * U[c]);
+            Gm[c * np + l] = 0.5 * (F[c] - alpha * U[c]);
+        }
+    }
+    /* pass 1: every face's bits in its own characteristic frame */
+    int nf = n + 3;
+    int *bits = (int *)malloc(sizeof(int) * 2 * m * nf); /* [s][k][face] */
+    for (int j = -2; j <= n; j++) {
+        double L[4][4], R[4][4], UL[4], UR[4];
+        for (int c = 0; c < m; c++) {
+            UL[c] = P[c][j + NG];
+            UR[c] = P[c][j + 1 + NG];
+        }
+        if (frame(S, dir, UL, UR, L, R)) status = OR_ENONPHYSICAL;
+        for (int k = 0; k < m; k++) {
+            double wp[5], wm[5];
+            for (int t = 0; t < 5; t++) {
+                int lp = j - 2 + t + NG, lm = j + 3 - t + NG;
+                double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
+                for (int c = 1; c < m; c++) {
+                    sp = sp + L[k][c] * Gp[c * np + lp];
+                    sm = sm + L[k][c] * Gm[c * np + lm];
+                }
+                wp[t] = sp;
+                wm[t] = sm;
+            }
+            bits[(0 * m + k) * nf + j + 2] = or_face_bits(wp, eps, CT, NULL);
+            bits[(1 * m + k) * nf + j + 2] = or_face_bits(wm, eps, CT, NULL);
+        }
+    }
+    /* pass 2: selection and polynomial at faces -1 .. n-1 */
+    for (int i = -1; i <= n - 1; i++) {
+        double L[4][4], R[4][4], UL[4], UR[4], f[4];
+        for (int c = 0; c < m; c++) {
+            UL[c] = P[c][i + NG];
+            UR[c] = P[c][i + 1 + NG];
+        }
+        frame(S, dir, UL, UR, L, R);
+        for (int k = 0; k < m; k++) {
+            const int *bp = bits + (0 * m + k) * nf, *bm = bits + (1 * m + k) * nf;
+            int Dp = pack_delta(bp[i + 1], bp[i + 2], bp[i + 3]);
+            int Dm = pack_delta(bm[i + 3], bm[i + 2], bm[i + 1]);
+            int mp = or_select(Dp), mm = or_select(Dm);
+            if (mp < 0) {
+                mp = 11;
+                status = OR_ENONFINITE;
+            }
+            if (mm < 0) {
+                mm = 11;
+                status = OR_ENONFINITE;
+            }
+            double vp[7], vm[7];
+            for (int t = 0; t < 7; t++) {
+                int lp = i - 3 + t + NG, lm = i + 4 - t + NG;
+                double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
+                for (int c = 1; c < m; c++) {
+                    sp = sp + L[k][c] * Gp[c * np + lp];
+                    sm = sm + L[k][c] * Gm[c * np + lm];
+                }
+                vp[t] = sp;
+                vm[t] = sm;
+            }
+            f[k] = poly(mp, vp) + poly(mm, vm);
+            if (masks) {
+                masks[(0 * m + k) * (n + 1) + i + 1] = (uint8_t)Dp;
+                masks[(1 * m + k) * (n + 1) + i + 1] = (uint8_t)Dm;
+            }
+        }
+        for (int c = 0; c < m; c++) {
+            double s = R[c][0] * f[0];
+            for (int k = 1; k < m; k++) s = s + R[c][k] * f[k];
+            Fh[c][i + 1] = s;
+        }
+    }
+    free(bits);
+    free(Gp);
+    free(Gm);
+    return status;
+}
+
+static int ghost_index(int l, int n, int bc_lo, int bc_hi) {
+    if (l < 0) return bc_lo == BC_PERIODIC ? l + n : 0;
+    if (l >= n) return bc_hi == BC_PERIODIC ? l - n : n - 1;
+    return l;
+}
+
+static int check_sys(int sys, int bc_lo, int bc_hi) {
+    if (sys != SYS_ADVECTION && sys != SYS_EULER1D && sys != SYS_BURGERS) return 0;
+    if (bc_lo != BC_PERIODIC && bc_lo != BC_ZERO_GRADIENT) return 0;
+    if (bc_hi != BC_PERIODIC && bc_hi != BC_ZERO_GRADIENT) return 0;
+    return 1;
+}
+
+/* Global Lax-Friedrichs alpha of a 1D state U[m][n]: max_i of the largest
+ * characteristic speed over interior cells. */
+static double alpha_1d(const sysdef *S, const double *U, int n, int *bad) {
+    double a = 0.0;
+    for (int i = 0; i < n; i++) {
+        double Uc[4];
+        for (int c = 0; c < S->m; c++) Uc[c] = U[c * n + i];
+        double s = wavespeed(S, 0, Uc, bad);
+        if (s > a || s != s) a = s;
+    }
+    return a;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1D right-hand side L(U) = -(F_{i+1/2} - F_{i-1/2})/dx (Eq. app).           */
+/*   U, dUdt: [m][n] row-major (variable-major).  alpha_in < 0: computed from */
+/*   U; otherwise used as given.  masks (nullable): [2][m][n+1] Delta codes.  */
+/*   alpha_out (nullable) receives the alpha used.                            */
+/* ------------------------------------------------------------------------ */
+int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a, double CT, double eps_in,
+              int bc_lo, int bc_hi, double alpha_in, double *dUdt, uint8_t *masks, double *alpha_out) {
+    if (n < 1 || !check_sys(sys, bc_lo, bc_hi) || !(dx > 0.0)) return OR_EINVAL;
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int m = S.m, np = n + 2 * NG;
+    int bad = 0;
+    double eps = (eps_in < 0.0) ? dx * dx * dx : eps_in;
+    double alpha = (alpha_in < 0.0) ? alpha_1d(&S, U, n, &bad) : alpha_in;
+    if (alpha_out) *alpha_out = alpha;
+    double *P[4], *Fh[4];
+    for (int c = 0; c < m; c++) {
+        P[c] = (double *)malloc(sizeof(double) * np);
+        Fh[c] = (double *)malloc(sizeof(double) * (n + 1));
+        for (int l = -NG; l < n + NG; l++) P[c][l + NG] = U[c * n + ghost_index(l, n, bc_lo, bc_hi)];
+    }
+    int status = sweep(&S, 0, P, n, alpha, eps, CT, Fh, masks);
+    for (int c = 0; c < m; c++)
+        for (int i = 0; i < n; i++) dUdt[c * n + i] = (Fh[c][i] - Fh[c][i + 1]) / dx;
+    for (int c = 0; c < m; c++) {
+        free(P[c]);
+        free(Fh[c]);
+    }
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return status;
+}
+
+/* Third-order SSP Runge-Kutta step (Shu-Osher form), in place on U[m][n]. */
+int or_rk3_step_1d(int sys, double *U, int n, double dx, double gamma, double a, double CT, double eps, int bc_lo,
+                   int bc_hi, double dt) {
+    int m = nvars_of(sys), N = m * n, st, status = OR_OK;
+    double *U0 = (double *)malloc(sizeof(double) * N);
+    double *U1 = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N);
+    memcpy(U0, U, sizeof(double) * N);
+    st = or_rhs_1d(sys, U0, n, dx, gamma, a, CT, eps, bc_lo, bc_hi, -1.0, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U1[q] = U0[q] + dt * r[q];
+    st = or_rhs_1d(sys, U1, n, dx, gamma, a, CT, eps, bc_lo, bc_hi, -1.0, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U1[q] = 0.75 * U0[q] + 0.25 * (U1[q] + dt * r[q]);
+    st = or_rhs_1d(sys, U1, n, dx, gamma, a, CT, eps, bc_lo, bc_hi, -1.0, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U[q] = (1.0 / 3.0) * U0[q] + (2.0 / 3.0) * (U1[q] + dt * r[q]);
+    free(U0);
+    free(U1);
+    free(r);
+    return status;
+}
+
+/* CFL time step dt = CFL dx / alpha(U). */
+int or_cfl_dt_1d(int sys, const double *U, int n, double dx, double gamma, double a, double cfl, double *dt_out) {
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int bad = 0;
+    double alpha = alpha_1d(&S, U, n, &bad);
+    *dt_out = (cfl * dx) / alpha;
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
+}
+
+/* March U to t_end (last step clipped to land on it) or for max_steps steps.
+ * dt_fixed > 0 uses that step; otherwise dt = CFL dx / alpha(U^n) each step. */
+int or_run_1d(int sys, double *U, int n, double dx, double gamma, double a, double CT, double eps, int bc_lo,
+              int bc_hi, double cfl, double dt_fixed, double t_end, int max_steps, int *steps_out, double *t_out) {
+    double t = 0.0;
+    int steps = 0, status = OR_OK;
+    while (steps < max_steps && t < t_end) {
+        double dt;
+        if (dt_fixed > 0.0) {
+            dt = dt_fixed;
+        } else {
+            int st = or_cfl_dt_1d(sys, U, n, dx, gamma, a, cfl, &dt);
+            if (st) {
+                status = st;
+                break;
+            }
+        }
+        if (t + dt > t_end) dt = t_end - t;
+        int st = or_rk3_step_1d(sys, U, n, dx, gamma, a, CT, eps, bc_lo, bc_hi, dt);
+        t = t + dt;
+        steps++;
+        if (st) {
+            status = st;
+            break;
+        }
+    }
+    if (steps_out) *steps_out = steps;
+    if (t_out) *t_out = t;
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2D Euler, dimension by dimension: L(U) = Lx(U) + Ly(U).  U, dUdt are      */
+/* [4][ny][nx] (x fastest).  bc[4] = {x_lo, x_hi, y_lo, y_hi}.               */
+/* alpha_in[2] (nullable) overrides the (x, y) global Lax-Friedrichs alphas. */
+/* masks (nullable): x faces [2][4][ny][nx+1] followed by y faces            */
+/* [2][4][nx][ny+1] (column-major for y, one column per x index).           */
+/* ------------------------------------------------------------------------ */
+static void alpha_2d(const sysdef *S, const double *U, int nx, int ny, double *ax, double *ay, int *bad) {
+    int N = nx * ny;
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = 0; q < N; q++) {
+        double Uc[4] = {U[q], U[N + q], U[2 * N + q], U[3 * N + q]};
+        double sx = wavespeed(S, 0, Uc, bad), sy = wavespeed(S, 1, Uc, bad);
+        if (sx > a0 || sx != sx) a0 = sx;
+        if (sy > a1 || sy != sy) a1 = sy;
+    }
+    *ax = a0;
+    *ay = a1;
+}
+
+int or_rhs_2d(const double *U, int nx, int ny, double dx, double dy, double gamma, double CT, double eps_x_in,
+              double eps_y_in, const int *bc, const double *alpha_in, double *dUdt, uint8_t *masks,
+              double *alpha_out) {
+    if (nx < 1 || ny < 1) return OR_EINVAL;
+    sysdef S = {SYS_EULER2D, 4, gamma, 0.0};
+    int N = nx * ny, bad = 0, status = OR_OK;
+    double ax, ay;
+    if (alpha_in) {
+        ax = alpha_in[0];
+        ay = alpha_in[1];
+    } else {
+        alpha_2d(&S, U, nx, ny, &ax, &ay, &bad);
+    }
+    if (alpha_out) {
+        alpha_out[0] = ax;
+        alpha_out[1] = ay;
+    }
+    double epsx = (eps_x_in < 0.0) ? dx * dx * dx : eps_x_in;
+    double epsy = (eps_y_in < 0.0) ? dy * dy * dy : eps_y_in;
+    double *P[4], *Fh[4];
+    int nmax = nx > ny ? nx : ny;
+    for (int c = 0; c < 4; c++) {
+        P[c] = (double *)malloc(sizeof(double) * (nmax + 2 * NG));
+        Fh[c] = (double *)malloc(sizeof(double) * (nmax + 1));
+    }
+    /* x sweeps */
+    for (int y = 0; y < ny; y++) {
+        for (int c = 0; c < 4; c++)
+            for (int l = -NG; l < nx + NG; l++) P[c][l + NG] = U[c * N + y * nx + ghost_index(l, nx, bc[0], bc[1])];
+        uint8_t *mk = masks ? masks + (size_t)y * (nx + 1) : NULL;
+        /* per-row masks are scattered below, so sweep into a temporary */
+        uint8_t *tmp = masks ? (uint8_t *)malloc(2 * 4 * (nx + 1)) : NULL;
+        int st = sweep(&S, 0, P, nx, ax, epsx, CT, Fh, tmp);
+        if (st) status = st;
+        for (int c = 0; c < 4; c++)
+            for (int i = 0; i < nx; i++) dUdt[c * N + y * nx + i] = (Fh[c][i] - Fh[c][i + 1]) / dx;
+        if (masks) {
+            for (int sk = 0; sk < 8; sk++) memcpy(mk + (size_t)sk * ny * (nx + 1), tmp + sk * (nx + 1), nx + 1);
+            free(tmp);
+        }
+    }
+    /* y sweeps, added to the x part */
+    uint8_t *ymasks = masks ? masks + (size_t)8 * ny * (nx + 1) : NULL;
+    for (int x = 0; x < nx; x++) {
+        for (int c = 0; c < 4; c++)
+            for (int l = -NG; l < ny + NG; l++) P[c][l + NG] = U[c * N + ghost_index(l, ny, bc[2], bc[3]) * nx + x];
+        uint8_t *tmp = masks ? (uint8_t *)malloc(2 * 4 * (ny + 1)) : NULL;
+        int st = sweep(&S, 1, P, ny, ay, epsy, CT, Fh, tmp);
+        if (st) status = st;
+        for (int c = 0; c < 4; c++)
+            for (int j = 0; j < ny; j++) {
+                double ry = (Fh[c][j] - Fh[c][j + 1]) / dy;
+                dUdt[c * N + j * nx + x] = dUdt[c * N + j * nx + x] + ry;
+            }
+        if (masks) {
+            for (int sk = 0; sk < 8; sk++)
+                memcpy(ymasks + (size_t)sk * nx * (ny + 1) + (size_t)x * (ny + 1), tmp + sk * (ny + 1), ny + 1);
+            free(tmp);
+        }
+    }
+    for (int c = 0; c < 4; c++) {
+        free(P[c]);
+        free(Fh[c]);
+    }
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return status;
+}
+
+int or_cfl_dt_2d(const double *U, int nx, int ny, double dx, double dy, double gamma, double cfl, double *dt_out) {
+    sysdef S = {SYS_EULER2D, 4, gamma, 0.0};
+    int bad = 0;
+    double ax, ay;
+    alpha_2d(&S, U, nx, ny, &ax, &ay, &bad);
+    *dt_out = cfl / (ax / dx + ay / dy);
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
+}
+
+int or_rk3_step_2d(double *U, int nx, int ny, double dx, double dy, double gamma, double CT, double epsx,
+                   double epsy, const int *bc, double dt) {
+    int N = 4 * nx * ny, st, status = OR_OK;
+    double *U0 = (double *)malloc(sizeof(double) * N);
+    double *U1 = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N);
+    memcpy(U0, U, sizeof(double) * N);
+    st = or_rhs_2d(U0, nx, ny, dx, dy, gamma, CT, epsx, epsy, bc, NULL, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U1[q] = U0[q] + dt * r[q];
+    st = or_rhs_2d(U1, nx, ny, dx, dy, gamma, CT, epsx, epsy, bc, NULL, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U1[q] = 0.75 * U0[q] + 0.25 * (U1[q] + dt * r[q]);
+    st = or_rhs_2d(U1, nx, ny, dx, dy, gamma, CT, epsx, epsy, bc, NULL, r, NULL, NULL);
+    if (st) status = st;
+    for (int q = 0; q < N; q++) U[q] = (1.0 / 3.0) * U0[q] + (2.0 / 3.0) * (U1[q] + dt * r[q]);
+    free(U0);
+    free(U1);
+    free(r);
+    return status;
+}
+
+int or_run_2d(double *U, int nx, int ny, double dx, double dy, double gamma, double CT, double epsx, double epsy,
+              const int *bc, double cfl, double dt_fixed, double t_end, int max_steps, int *steps_out,
+              double *t_out) {
+    double t = 0.0;
+    int steps = 0, status = OR_OK;
+    while (steps < max_steps && t < t_end) {
+        double dt;
+        if (dt_fixed > 0.0) {
+            dt = dt_fixed;
+        } else {
+            int st = or_cfl_dt_2d(U, nx, ny, dx, dy, gamma, cfl, &dt);
+            if (st) {
+                status = st;
+                break;
+            }
+        }
+        if (t + dt > t_end) dt = t_end - t;
+        int st = or_rk3_step_2d(U, nx, ny, dx, dy, gamma, CT, epsx, epsy, bc, dt);
+        t = t + dt;
+        steps++;
+        if (st) {
+            status = st;
+            break;
+        }
+    }
+    if (steps_out) *steps_out = steps;
+    if (t_out) *t_out = t;
+    return status;
+}
+
+/* Euler-1D characteristic frame, exported for the tests' eigen checks. */
+int or_frame_1d(const double *UL, const double *UR, double gamma, double *L9, double *R9) {
+    sysdef S = {SYS_EULER1D, 3, gamma, 0.0};
+    double L[4][4], R[4][4];
+    int st = frame(&S, 0, UL, UR, L, R);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            L9[a * 3 + b] = L[a][b];
+            R9[a * 3 + b] = R[a][b];
+        }
+    return st;
+}
+
+int or_frame_2d(const double *UL, const double *UR, double gamma, int dir, double *L16, double *R16) {
+    sysdef S = {SYS_EULER2D, 4, gamma, 0.0};
+    double L[4][4], R[4][4];
+    int st = frame(&S, dir, UL, UR, L, R);
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) {
+            L16[a * 4 + b] = L[a][b];
+            R16[a * 4 + b] = R[a][b];
+        }
+    return st;
+}
