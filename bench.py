@@ -1,0 +1,311 @@
+"""Benchmark of the TENO7-ext hot path: SSP-RK3 steps of the 1D Euler equations
+with characteristic-wise TENO7-ext reconstruction on one GB300.
+
+Workload: the Shu-Osher shock / entropy-wave problem (gamma = 1.4; left state
+(3.857143, 2.629369, 10.33333) for x < -4, right state (1 + 0.2 sin 5x, 0, 1)
+on [-5, 5] with 1600 cells, dx = 1/160), its profile tiled end to end 10486
+times to N = 16,777,600 cells (same dx, so the same epsilon = dx^3 and local
+structure), zero-gradient ends, CFL 0.5 with the step computed on the device
+from max(|u| + c) every step.  A "step" is one full SSP-RK3 step (3 fused stage
+launches) over all cells; value = cells x steps / time in Gcell-steps/s.
+The state (201 MB in FP32, 403 MB in FP64) is larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Lines: the primary line is the FP32 path (dtype f32); the FP64 path (results
+bit-identical to the CPU oracle) is reported beside it under "f64", with the
+FP32-vs-FP64 error and mask-flip fraction on the 1600-cell Shu-Osher run to
+t = 1.8.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1808_00037_gb300 import inputs as I  # noqa: E402
+
+TILES = 10486
+N1 = 1600
+CFL = 0.5
+GAMMA = 1.4
+# FP32 / FP64 lanes: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (nominal)
+# Floating-point operations per cell per stage launch of the fused Euler-1D
+# stage kernel, counted by ncu (fadd + fmul + 2 ffma, plus the double-precision
+# equivalents) on the tiled Shu-Osher workload: see profiles/.
+FLOPS_PER_CELL_STAGE = {"f32": None, "f64": None}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(ngpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    """The CPU oracle timed on the host cores (bounded sample of the workload)."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    tiles = args.ref_tiles
+    U, dx = I.shu_osher(N1, tiles=tiles)
+    n = U.shape[1]
+    for _ in range(args.warmup):
+        U, _, _, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=math.inf, cfl=CFL, bc=(1, 1), max_steps=1)
+    t0 = time.perf_counter()
+    U, steps, _, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=math.inf, cfl=CFL, bc=(1, 1),
+                                   max_steps=args.steps)
+    dt = time.perf_counter() - t0
+    val = n * steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "TENO7 RK3 Gcell-updates/s (1D Euler, tiled Shu-Osher)", "value": val,
+        "unit": "Gcell-steps/s", "n_gpus": 0, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Shu-Osher profile tiled x{tiles} (N={n}, dx=1/160), zero-gradient, CFL 0.5",
+                   "sample_of": f"N={N1 * TILES}"},
+        "cpu_baseline": {"value": val, "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} RK3 steps on {n} cells (single-threaded C oracle)"},
+        "e2e": {"value": val, "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(budget_s=15.0):
+    import oracle
+    oracle.build()
+    U, dx = I.shu_osher(N1, tiles=4)
+    n = U.shape[1]
+    oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=math.inf, cfl=CFL, bc=(1, 1), max_steps=1)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        U, s, _, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=math.inf, cfl=CFL, bc=(1, 1), max_steps=10)
+        steps += s
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt / 1e9, "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK3 steps of the Shu-Osher profile tiled x4 (N={n}), single-threaded C oracle"}
+
+
+def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
+    stream = ctx.stream
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(sampler_index) if sampler_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    start.record(stream)
+    done, _ = ctx.run(U, CFL, max_steps=steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+    ms = start.elapsed_time(end)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    assert done == steps
+    return ms, (sampler.summary() if sampler else None)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tiles", type=int, default=TILES)
+    ap.add_argument("--ref-tiles", type=int, default=8)
+    ap.add_argument("--f64-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args.gpus)
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    from paper_1808_00037_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    U0, dx = I.shu_osher(N1, tiles=args.tiles)
+    n = U0.shape[1]
+    hbm_peak, peak_kind = peaks()
+    res = {}
+    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        steps = args.steps if name == "f32" or args.f64_steps is None else args.f64_steps
+        ctx = B.Context(B.T7_EULER1D, n, dx, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
+        U = torch.tensor(U0, dtype=dtype, device="cuda")
+        ctx.run(U, CFL, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        ms, clocks = time_run(torch, ctx, U, steps, dist, world, sampler_index=local if rank == 0 else None)
+        s = 4 if name == "f32" else 8
+        launches = 3 * steps
+        stage_ms = ms / launches  # the stage kernel is the only per-step launch
+        alg_bytes = 8 * 3 * s / 3 * n  # per stage launch, averaged over the three stages
+        achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
+        res[name] = {
+            "value": n * steps * world / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps, "steps": steps,
+            "clocks": clocks, "gpu_launches": launches + 2,
+            "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                    "peak_kind": peak_kind, "bytes_per_cell_step": 8 * 3 * s},
+        }
+        # end-to-end through the host-array entry point: per step H2D + step + D2H
+        if not args.no_e2e:
+            Uh = torch.tensor(U0, dtype=dtype).pin_memory()
+            ctx.run_host(Uh, CFL, max_steps=1)
+            e2e_steps = min(steps, 10)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                ctx.run_host(Uh, CFL, max_steps=1)
+            el = time.perf_counter() - t0
+            if dist:
+                t = torch.tensor([el], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                el = float(t.item())
+            nbytes = U0.size * s
+            res[name]["e2e"] = {"value": n * e2e_steps * world / el / 1e9, "unit": "Gcell-steps/s",
+                                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        ctx.close()
+        del U
+        torch.cuda.empty_cache()
+
+    # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
+    acc = {}
+    Ua, dxa = I.shu_osher(N1)
+    outs = {}
+    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        c = B.Context(B.T7_EULER1D, N1, dxa, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
+        Ug = torch.tensor(Ua, dtype=dtype, device="cuda")
+        c.run(Ug, CFL, t_end=1.8)
+        outs[name] = (c, Ug)
+    f32 = outs["f32"][1].double().cpu().numpy()
+    f64 = outs["f64"][1].double().cpu().numpy()
+    acc["f32_vs_f64_rel_l1_rho"] = float(np.abs(f32[0] - f64[0]).sum() / np.abs(f64[0]).sum())
+    # stencil-selection flips: both precisions evaluate L(U) on the same FP64 end state
+    _, m64 = outs["f64"][0].euler_rhs(outs["f64"][1], want_masks=True)
+    _, m32 = outs["f32"][0].euler_rhs(outs["f64"][1].float(), want_masks=True)
+    torch.cuda.synchronize()
+    acc["mask_flip_fraction"] = float((m64 != m32).double().mean().item())
+    acc["case"] = "Shu-Osher N=1600, CFL 0.5, t=1.8"
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    main_res = res["f32"]
+    line = {
+        "metric": "TENO7 RK3 Gcell-updates/s (1D Euler, tiled Shu-Osher)", "value": main_res["value"],
+        "unit": "Gcell-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Shu-Osher profile (1600 cells on [-5,5], dx=1/160) tiled x{args.tiles}, "
+                               f"N={n} cells per GPU, zero-gradient ends, CFL 0.5, device-side dt",
+                   "l2": "inputs larger than L2 (state 201 MB f32 / 403 MB f64 > 129 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": main_res["hbm"]["achieved"], "peak": hbm_peak, "unit": "GB/s",
+                     "frac": main_res["hbm"]["frac"], "traffic": None,
+                     "note": f"peak = {peak_kind} HBM copy bandwidth; achieved = 8 m s bytes per cell-step / "
+                             "average stage-launch time"},
+        "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
+        "e2e": main_res.get("e2e"),
+        "f64": res["f64"], "accuracy": acc, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,131 @@
+/*
+ * teno7.h -- C ABI of the GB300 (sm_103a) implementation of the extended
+ * seventh-order TENO scheme ("TENO7-ext") of F. Zhang, J. Liu, H. Zhang and
+ * C. Xu, "An extending strategy based on TENO framework for hyperbolic
+ * conservation laws", arXiv:1808.00037.
+ *
+ * The method (the paper's Sections 2-4):
+ *   - conservative finite differences, du_i/dt = -(f_{i+1/2} - f_{i-1/2})/dx
+ *     (Eq. app), with global Lax-Friedrichs flux splitting and Roe-averaged
+ *     characteristic projection for the Euler equations (Remark 3; Sec.
+ *     "One dimensional Euler equations");
+ *   - per face, the five-point TENO smoothness measure on three 3-point
+ *     stencils (Eqs. smooth_expl, tau5, TENO1 with C = 1, q = 6, norm,
+ *     seclect with C_T = 1e-5, epsilon = dx^3);
+ *   - the binary vector Delta_i built from this face's and the two neighbouring
+ *     faces' cutoff bits (Eq. vec), which selects one of 13 polynomials
+ *     (Table co3) whose coefficients are Table co2;
+ *   - the third-order SSP Runge-Kutta method in time (Sec. 2.1).
+ *
+ * Conventions for every call:
+ *   - Device arrays are caller-owned, contiguous, and hold `double` for
+ *     T7_F64 and `float` for T7_F32 contexts.  Conserved variables are
+ *     variable-major ("SoA"): 1D [m][nx], 2D [m][ny][nx] with x fastest;
+ *     (rho, rho u, E) for 1D Euler, (rho, rho u, rho v, E) for 2D Euler, u for
+ *     the scalar laws.
+ *   - The library owns only the workspace inside a t7_ctx (two stage buffers,
+ *     a host-API state buffer and a small control block).
+ *   - Calls are asynchronous on the context's stream unless stated.  Device-
+ *     side errors (non-physical or non-finite states) are latched in the
+ *     control block and returned by the next synchronising call (t7_sync,
+ *     t7_cfl_dt, t7_run, t7_run_host), which clears them.
+ *   - A call never aborts the process; it returns a t7_status and, on
+ *     failure, t7_last_error() describes the cause.
+ */
+#ifndef TENO7_H
+#define TENO7_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    T7_OK = 0,
+    T7_EINVAL = -1,       /* bad argument: null pointer, size, enum value    */
+    T7_ECUDA = -2,        /* a CUDA runtime call failed                       */
+    T7_ENONPHYSICAL = -3, /* rho <= 0, p <= 0 or Roe c^2 <= 0 was met          */
+    T7_ENONFINITE = -4,   /* Inf/NaN met (or the "no exist" pattern of Table co3) */
+    T7_ETIMEOUT = -5,     /* a bounded device wait gave up                    */
+    T7_ENOMEM = -6        /* workspace allocation failed                      */
+} t7_status;
+
+typedef enum { T7_BC_PERIODIC = 0, T7_BC_ZERO_GRADIENT = 1 /* = transmissive */ } t7_bc;
+typedef enum { T7_F64 = 0, T7_F32 = 1 } t7_prec;
+typedef enum { T7_SCALAR_ADVECTION = 0, T7_EULER1D = 1, T7_EULER2D = 2, T7_BURGERS = 3 } t7_system;
+
+/* Grid and parameters of one problem.  Cell-centred uniform grid with cell
+ * widths dx, dy; four ghost cells per side are built inside the kernels from
+ * bc[] = {x_lo, x_hi, y_lo, y_hi} (y entries ignored in 1D).
+ *   gamma     ratio of specific heats (Euler; the paper uses 1.4)
+ *   adv_speed a in u_t + a u_x = 0 (scalar advection)
+ *   CT        cutoff C_T of Eq. seclect (the paper uses 1e-5)
+ *   eps_x/y   epsilon of Eq. TENO1; a negative value selects dx^3 (dy^3),
+ *             the paper's choice (Sec. "The parameter epsilon").            */
+typedef struct {
+    int sys;  /* t7_system */
+    int prec; /* t7_prec   */
+    int nx, ny; /* ny = 1 for 1D systems */
+    double dx, dy;
+    int bc[4];
+    double gamma, adv_speed, CT, eps_x, eps_y;
+} t7_grid;
+
+typedef struct t7_ctx t7_ctx;
+
+/* Create a context on the current CUDA device bound to `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  Allocates the workspace
+ * (3 state-sized buffers + a control block).  On success *out owns it. */
+t7_status t7_create(const t7_grid *grid, void *stream, t7_ctx **out);
+t7_status t7_destroy(t7_ctx *ctx);
+t7_status t7_set_stream(t7_ctx *ctx, void *stream);
+/* Last error message of this context (never NULL). */
+const char *t7_last_error(const t7_ctx *ctx);
+/* Block until the stream is idle; return and clear any latched device error. */
+t7_status t7_sync(t7_ctx *ctx);
+
+/* Scalar TENO7-ext reconstruction of one sequence of point values
+ * (Eqs. smooth_expl .. seclect, Eq. vec, Tables co2/co3).
+ *   v_padded  device, n + 8 values at cells -4 .. n+3 (caller-padded)
+ *   sign      +1: reconstruction upwind from the left; -1: its mirror image
+ *   eps       epsilon of Eq. TENO1 (> 0)
+ *   fhat      device, n + 1 face values at i+1/2, i = -1 .. n-1
+ *   d3        device or NULL, n + 3 bytes: cutoff bits (d0 | d1<<1 | d2<<2)
+ *             of faces -2 .. n
+ *   D5        device or NULL, n + 1 bytes: Delta_i of faces -1 .. n-1 packed
+ *             with its first component in bit 4 and its last in bit 0.
+ * Uses the context's precision and CT; the system is irrelevant.  Async. */
+t7_status t7_teno7_reconstruct(t7_ctx *ctx, const void *v_padded, int n, int sign, double eps, void *fhat,
+                               uint8_t *d3, uint8_t *D5);
+
+/* Right-hand side L(U) = -(F_{i+1/2} - F_{i-1/2})/dx (Eq. app) of the
+ * context's 1D system, characteristic-wise with global Lax-Friedrichs
+ * splitting, alpha = max_i (|u_i| + c_i) over the interior cells of U.
+ *   U, dUdt   device, [m][nx]
+ *   masks     device or NULL, [2][m][nx+1] bytes: Delta_i of the '+' (index 0)
+ *             and '-' (index 1) splits per characteristic field and face
+ *             i+1/2, i = -1 .. nx-1.  Async. */
+t7_status t7_euler_rhs(t7_ctx *ctx, const void *U, void *dUdt, uint8_t *masks);
+
+/* dt = CFL dx / alpha(U) (1D).  Synchronises; *dt_out is a host double. */
+t7_status t7_cfl_dt(t7_ctx *ctx, const void *U, double cfl, double *dt_out);
+
+/* One SSP-RK3 step (Shu-Osher form) of size dt, in place on device U.  Async. */
+t7_status t7_rk3_step(t7_ctx *ctx, void *U, double dt);
+
+/* March device U in place until t_end (last step clipped to land on it) or
+ * max_steps steps, dt = CFL dx / alpha(U^n) computed on the device each step.
+ * t_end may be +inf.  Synchronises; steps_out / t_out (host, nullable). */
+t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out);
+
+/* As t7_run on a HOST array U_host ([m][nx], context precision): copies it to
+ * the context's device state, runs, copies the result back.  Synchronises. */
+t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
+                      double *t_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENO7_H */

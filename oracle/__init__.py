@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
         _lib.or_rk3_step_2d.argtypes = [p, i, i, d, d, d, d, d, d, p, d]
         _lib.or_run_2d.argtypes = [p, i, i, d, d, d, d, d, d, p, d, d, d, i, p, p]
         _lib.or_frame_1d.argtypes = [p, p, d, p, p]
+        _lib.or_alpha_1d.argtypes = [i, p, i, d, d, p]
         _lib.or_frame_2d.argtypes = [p, p, d, i, p, p]
     return _lib
 
@@ -163,6 +164,16 @@ def cfl_dt_1d(sys, U, dx, cfl, *, gamma=1.4, a=1.0):
     st = lib().or_cfl_dt_1d(sys, _ptr(U), U.shape[1], dx, gamma, a, cfl, _ptr(dt))
     _check(st, "cfl_dt_1d", True)
     return float(dt[0])
+
+
+def alpha_1d(sys, U, *, gamma=1.4, a=1.0):
+    """max_i of the largest characteristic speed over the cells of U[m, n]."""
+    U = _f64(U)
+    U = U.reshape(nvars(sys), -1)
+    out = np.zeros(1)
+    st = lib().or_alpha_1d(sys, _ptr(U), U.shape[1], gamma, a, _ptr(out))
+    _check(st, "alpha_1d", True)
+    return float(out[0])
 
 
 def run_1d(sys, U, dx, *, t_end, cfl=0.5, dt_fixed=-1.0, max_steps=1 << 30, gamma=1.4, a=1.0, CT=1e-5,

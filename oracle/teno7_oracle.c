@@ -431,9 +431,11 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
     return status;
 }
 
+/* Ghost cells: periodic U_l = U_(l mod n) (U_{-k} = U_{n-k} when n >= 4);
+ * zero-gradient copies the nearest interior cell. */
 static int ghost_index(int l, int n, int bc_lo, int bc_hi) {
-    if (l < 0) return bc_lo == BC_PERIODIC ? l + n : 0;
-    if (l >= n) return bc_hi == BC_PERIODIC ? l - n : n - 1;
+    if (l < 0) return bc_lo == BC_PERIODIC ? ((l % n) + n) % n : 0;
+    if (l >= n) return bc_hi == BC_PERIODIC ? l % n : n - 1;
     return l;
 }
 
@@ -730,4 +732,14 @@ int or_frame_2d(const double *UL, const double *UR, double gamma, int dir, doubl
             R16[a * 4 + b] = R[a][b];
         }
     return st;
+}
+
+/* Global Lax-Friedrichs alpha of a 1D state (exported for sampled checks). */
+int or_alpha_1d(int sys, const double *U, int n, double gamma, double a, double *alpha_out) {
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int bad = 0;
+    *alpha_out = alpha_1d(&S, U, n, &bad);
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
 }

@@ -1,0 +1,182 @@
+"""Thin Python binding of libteno7 (include/teno7.h): argument marshalling only.
+
+Every step of the scheme runs in the CUDA kernels behind the C ABI; this module
+loads the in-tree shared library with ctypes, allocates output tensors with
+PyTorch (device memory and streams only) and passes raw pointers.  There is no
+CPU fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "libteno7.so"
+
+T7_OK, T7_EINVAL, T7_ECUDA, T7_ENONPHYSICAL, T7_ENONFINITE, T7_ETIMEOUT, T7_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
+T7_F64, T7_F32 = 0, 1
+T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
+
+_STATUS = {0: "T7_OK", -1: "T7_EINVAL", -2: "T7_ECUDA", -3: "T7_ENONPHYSICAL", -4: "T7_ENONFINITE",
+           -5: "T7_ETIMEOUT", -6: "T7_ENOMEM"}
+
+
+class T7Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class t7_grid(ctypes.Structure):
+    _fields_ = [("sys", ctypes.c_int), ("prec", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("bc", ctypes.c_int * 4),
+                ("gamma", ctypes.c_double), ("adv_speed", ctypes.c_double), ("CT", ctypes.c_double),
+                ("eps_x", ctypes.c_double), ("eps_y", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: Path | str | None = None) -> ctypes.CDLL:
+    """Load libteno7.so (build it first with __graft_entry__.build() or
+    paper_1808_00037_gb300.build.build())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"CUDA library {p} is missing: build it first (no CPU fallback exists)")
+    lib = ctypes.CDLL(str(p))
+    vp, i, d, u8p = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sigs = {
+        "t7_create": ([ctypes.POINTER(t7_grid), vp, ctypes.POINTER(vp)], i),
+        "t7_destroy": ([vp], i),
+        "t7_set_stream": ([vp, vp], i),
+        "t7_last_error": ([vp], ctypes.c_char_p),
+        "t7_sync": ([vp], i),
+        "t7_teno7_reconstruct": ([vp, vp, i, i, d, vp, u8p, u8p], i),
+        "t7_euler_rhs": ([vp, vp, vp, u8p], i),
+        "t7_cfl_dt": ([vp, vp, d, ctypes.POINTER(d)], i),
+        "t7_rk3_step": ([vp, vp, d], i),
+        "t7_run": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+        "t7_run_host": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+class Context:
+    """One problem (grid + parameters + precision) bound to a CUDA stream."""
+
+    def __init__(self, sys: int, nx: int, dx: float, *, prec: int = T7_F64, ny: int = 1, dy: float = 0.0,
+                 bc=(T7_BC_PERIODIC,) * 4, gamma: float = 1.4, adv_speed: float = 1.0, CT: float = 1e-5,
+                 eps_x: float = -1.0, eps_y: float = -1.0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.sys, self.prec, self.nx, self.ny = sys, prec, nx, ny
+        self.m = {T7_SCALAR_ADVECTION: 1, T7_BURGERS: 1, T7_EULER1D: 3, T7_EULER2D: 4}[sys]
+        self.dtype = torch.float64 if prec == T7_F64 else torch.float32
+        self.np_dtype = np.float64 if prec == T7_F64 else np.float32
+        bc = tuple(bc) + (T7_BC_PERIODIC,) * (4 - len(bc))
+        g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y)
+        self.grid = g
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.t7_create(ctypes.byref(g), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != T7_OK:
+            raise T7Error(st, "t7_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.t7_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != T7_OK:
+            raise T7Error(st, f"{what}: {self.lib.t7_last_error(self.h).decode()}")
+
+    def _dev(self, t):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous CUDA tensor of dtype {self.dtype}")
+        return t
+
+    # ------------------------------------------------------------ the ABI --
+    def teno7_reconstruct(self, v_padded, sign: int, eps: float, want_bits: bool = False):
+        torch = self._torch
+        v = self._dev(v_padded)
+        n = v.numel() - 8
+        fhat = torch.empty(n + 1, dtype=self.dtype, device=v.device)
+        d3 = torch.empty(n + 3, dtype=torch.uint8, device=v.device) if want_bits else None
+        D5 = torch.empty(n + 1, dtype=torch.uint8, device=v.device) if want_bits else None
+        self._check(self.lib.t7_teno7_reconstruct(self.h, _ptr(v), n, sign, eps, _ptr(fhat), _ptr(d3), _ptr(D5)),
+                    "t7_teno7_reconstruct")
+        return fhat, d3, D5
+
+    def euler_rhs(self, U, want_masks: bool = False, out=None):
+        torch = self._torch
+        U = self._dev(U)
+        out = torch.empty_like(U) if out is None else self._dev(out)
+        masks = torch.empty((2, self.m, self.nx + 1), dtype=torch.uint8, device=U.device) if want_masks else None
+        self._check(self.lib.t7_euler_rhs(self.h, _ptr(U), _ptr(out), _ptr(masks)), "t7_euler_rhs")
+        return out, masks
+
+    def cfl_dt(self, U, cfl: float) -> float:
+        dt = ctypes.c_double()
+        self._check(self.lib.t7_cfl_dt(self.h, _ptr(self._dev(U)), cfl, ctypes.byref(dt)), "t7_cfl_dt")
+        return dt.value
+
+    def rk3_step(self, U, dt: float):
+        self._check(self.lib.t7_rk3_step(self.h, _ptr(self._dev(U)), dt), "t7_rk3_step")
+        return U
+
+    def run(self, U, cfl: float, t_end: float = math.inf, max_steps: int = 2**31 - 1):
+        steps, t = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.t7_run(self.h, _ptr(self._dev(U)), cfl, t_end, max_steps, ctypes.byref(steps),
+                                    ctypes.byref(t)), "t7_run")
+        return steps.value, t.value
+
+    def run_host(self, U_host, cfl: float, t_end: float = math.inf, max_steps: int = 2**31 - 1):
+        """U_host: a C-contiguous numpy array or a (preferably pinned) CPU torch
+        tensor of the context's dtype, [m][nx]; advanced in place."""
+        torch = self._torch
+        if isinstance(U_host, torch.Tensor):
+            if U_host.is_cuda or U_host.dtype != self.dtype or not U_host.is_contiguous():
+                raise ValueError(f"expected a contiguous CPU tensor of dtype {self.dtype}")
+            ptr = ctypes.c_void_p(U_host.data_ptr())
+        else:
+            if not (U_host.dtype == self.np_dtype and U_host.flags.c_contiguous):
+                raise ValueError(f"expected a C-contiguous {self.np_dtype} array")
+            ptr = U_host.ctypes.data_as(ctypes.c_void_p)
+        steps, t = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.t7_run_host(self.h, ptr, cfl, t_end, max_steps, ctypes.byref(steps), ctypes.byref(t)),
+                    "t7_run_host")
+        return steps.value, t.value
+
+    def sync(self):
+        self._check(self.lib.t7_sync(self.h), "t7_sync")

@@ -1,0 +1,336 @@
+// teno7_api.cu -- the C ABI of libteno7 (declared in include/teno7.h): context
+// and workspace management, argument validation, the SSP-RK3 stage sequence
+// and the device-side CFL time stepping.  All compute is in the kernels of
+// teno7_kernels.cuh; this file only validates, allocates and launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "teno7.h"
+#include "teno7_internal.h"
+
+struct t7_ctx {
+    t7_grid g;
+    int m;                 // conserved variables
+    size_t esize;          // bytes per element (8 or 4)
+    size_t ncell;          // nx * ny
+    cudaStream_t stream;
+    int device;
+    void *U1, *U2;         // RK stage buffers
+    void *Uhost;           // device state for the host-array entry point
+    t7::DevCtl *ctl;       // device control block
+    t7::DevCtl *ctl_host;  // pinned mirror for status reads
+    char err[512];
+};
+
+namespace {
+
+t7_status fail(t7_ctx *c, t7_status st, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+t7_status cuda_fail(t7_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, T7_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int nvars(int sys) { return sys == T7_EULER1D ? 3 : (sys == T7_EULER2D ? 4 : 1); }
+
+bool is_1d(int sys) { return sys == T7_SCALAR_ADVECTION || sys == T7_EULER1D || sys == T7_BURGERS; }
+
+double eps_of(double eps, double d) { return eps < 0.0 ? d * d * d : eps; }
+
+__global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, int max_steps) {
+    for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = 0ull;
+    ctl->t = 0.0;
+    ctl->dt = 0.0;
+    ctl->t_end = t_end;
+    ctl->cfl = cfl;
+    ctl->steps = 0;
+    ctl->max_steps = max_steps;
+    ctl->active = 1;
+}
+
+t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
+    t7::Stage1D p;
+    memset(&p, 0, sizeof(p));
+    p.Us = Us;
+    p.U0 = U0;
+    p.out = out;
+    p.n = c->g.nx;
+    p.sys = c->g.sys;
+    p.bc_lo = c->g.bc[0];
+    p.bc_hi = c->g.bc[1];
+    p.dx = c->g.dx;
+    p.eps = eps_of(c->g.eps_x, c->g.dx);
+    p.CT = c->g.CT;
+    p.gamma = c->g.gamma;
+    p.a = c->g.adv_speed;
+    p.ctl = c->ctl;
+    return p;
+}
+
+cudaError_t stage(t7_ctx *c, const t7::Stage1D &p) {
+    return c->g.prec == T7_F64 ? t7::launch_stage1d_f64(p, c->stream) : t7::launch_stage1d_f32(p, c->stream);
+}
+
+// alpha(U) into slot 0 after clearing all slots
+cudaError_t alpha_init(t7_ctx *c, const void *U) {
+    cudaError_t e = cudaMemsetAsync(c->ctl->amax, 0, sizeof(c->ctl->amax), c->stream);
+    if (e != cudaSuccess) return e;
+    t7::Alpha1D a;
+    a.U = U;
+    a.n = c->g.nx;
+    a.sys = c->g.sys;
+    a.gamma = c->g.gamma;
+    a.a = c->g.adv_speed;
+    a.ctl = c->ctl;
+    a.slot = 0;
+    return c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+}
+
+// three stage launches; dt_fixed > 0 fixes the step, otherwise CFL on device
+cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed) {
+    void *bufs_in[3] = {U, c->U1, c->U2};
+    void *bufs_out[3] = {c->U1, c->U2, U};
+    for (int k = 0; k < 3; k++) {
+        t7::Stage1D p = stage_params(c, bufs_in[k], k == 0 ? nullptr : U, bufs_out[k]);
+        p.rhs_mode = 0;
+        p.stage = k;
+        p.dt_fixed = dt_fixed;
+        p.slot_in = k;
+        cudaError_t e = stage(c, p);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// read and clear the latched device error; stream must be idle
+t7_status collect(t7_ctx *c) {
+    cudaError_t e = cudaMemcpy(c->ctl_host, c->ctl, sizeof(t7::DevCtl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the control block");
+    int err = c->ctl_host->err, idx = c->ctl_host->err_index;
+    if (err) {
+        int zero = 0, big = 0x7fffffff;
+        cudaMemcpy(&c->ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(&c->ctl->err_index, &big, sizeof(int), cudaMemcpyHostToDevice);
+        if (err & t7::ERR_NONPHYSICAL)
+            return fail(c, T7_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or c^2 <= 0) near index %d", idx);
+        return fail(c, T7_ENONFINITE, "non-finite state or unreachable stencil pattern near index %d", idx);
+    }
+    return T7_OK;
+}
+
+t7_status check_1d(t7_ctx *c) {
+    if (!c) return T7_EINVAL;
+    if (!is_1d(c->g.sys)) return fail(c, T7_EINVAL, "this entry point takes a 1D system");
+    return T7_OK;
+}
+
+}  // namespace
+
+namespace t7 {
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, int max_steps, cudaStream_t s) {
+    ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, t_end, cfl, max_steps);
+    return cudaGetLastError();
+}
+}  // namespace t7
+
+extern "C" {
+
+t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
+    if (!g || !out) return T7_EINVAL;
+    *out = nullptr;
+    if (g->sys != T7_SCALAR_ADVECTION && g->sys != T7_EULER1D && g->sys != T7_BURGERS && g->sys != T7_EULER2D)
+        return T7_EINVAL;
+    if (g->prec != T7_F64 && g->prec != T7_F32) return T7_EINVAL;
+    if (g->nx < 1 || g->ny < 1 || (is_1d(g->sys) && g->ny != 1)) return T7_EINVAL;
+    if (!(g->dx > 0.0) || (g->sys == T7_EULER2D && !(g->dy > 0.0))) return T7_EINVAL;
+    for (int b = 0; b < 4; b++)
+        if (g->bc[b] != T7_BC_PERIODIC && g->bc[b] != T7_BC_ZERO_GRADIENT) return T7_EINVAL;
+    if ((double)g->nx * (double)g->ny * nvars(g->sys) > 2147483647.0) return T7_EINVAL;
+    if (!(g->CT > 0.0 && g->CT < 1.0)) return T7_EINVAL;
+    t7_ctx *c = new (std::nothrow) t7_ctx;
+    if (!c) return T7_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->g = *g;
+    c->m = nvars(g->sys);
+    c->esize = g->prec == T7_F64 ? 8 : 4;
+    c->ncell = (size_t)g->nx * g->ny;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    size_t bytes = c->ncell * c->m * c->esize;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->U1, bytes)) != cudaSuccess || (e = cudaMalloc(&c->U2, bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->Uhost, bytes)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->ctl, sizeof(t7::DevCtl))) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&c->ctl_host, sizeof(t7::DevCtl))) != cudaSuccess) {
+        t7_destroy(c);
+        cudaGetLastError();
+        return T7_ENOMEM;
+    }
+    t7::DevCtl init;
+    memset(&init, 0, sizeof(init));
+    init.err_index = 0x7fffffff;
+    init.max_steps = 0;
+    if ((e = cudaMemcpy(c->ctl, &init, sizeof(init), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        t7_destroy(c);
+        return T7_ECUDA;
+    }
+    snprintf(c->err, sizeof(c->err), "no error");
+    *out = c;
+    return T7_OK;
+}
+
+t7_status t7_destroy(t7_ctx *c) {
+    if (!c) return T7_EINVAL;
+    if (c->U1) cudaFree(c->U1);
+    if (c->U2) cudaFree(c->U2);
+    if (c->Uhost) cudaFree(c->Uhost);
+    if (c->ctl) cudaFree(c->ctl);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    delete c;
+    return T7_OK;
+}
+
+t7_status t7_set_stream(t7_ctx *c, void *stream) {
+    if (!c) return T7_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return T7_OK;
+}
+
+const char *t7_last_error(const t7_ctx *c) { return c ? c->err : "null context"; }
+
+t7_status t7_sync(t7_ctx *c) {
+    if (!c) return T7_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    return collect(c);
+}
+
+t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double eps, void *fhat, uint8_t *d3,
+                               uint8_t *D5) {
+    if (!c) return T7_EINVAL;
+    if (!v || !fhat || n < 1 || (sign != 1 && sign != -1) || !(eps > 0.0))
+        return fail(c, T7_EINVAL, "t7_teno7_reconstruct: bad argument");
+    t7::Recon p;
+    p.v = v;
+    p.fhat = fhat;
+    p.d3 = d3;
+    p.D5 = D5;
+    p.n = n;
+    p.sign = sign;
+    p.eps = eps;
+    p.CT = c->g.CT;
+    p.ctl = c->ctl;
+    cudaError_t e = c->g.prec == T7_F64 ? t7::launch_recon_f64(p, c->stream) : t7::launch_recon_f32(p, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reconstruct launch");
+    return T7_OK;
+}
+
+t7_status t7_euler_rhs(t7_ctx *c, const void *U, void *dUdt, uint8_t *masks) {
+    t7_status st = check_1d(c);
+    if (st) return st;
+    if (!U || !dUdt) return fail(c, T7_EINVAL, "t7_euler_rhs: null array");
+    cudaError_t e = alpha_init(c, U);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
+    t7::Stage1D p = stage_params(c, U, nullptr, dUdt);
+    p.rhs_mode = 1;
+    p.masks = masks;
+    p.slot_in = 0;
+    e = stage(c, p);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rhs launch");
+    return T7_OK;
+}
+
+t7_status t7_cfl_dt(t7_ctx *c, const void *U, double cfl, double *dt_out) {
+    t7_status st = check_1d(c);
+    if (st) return st;
+    if (!U || !dt_out || !(cfl > 0.0)) return fail(c, T7_EINVAL, "t7_cfl_dt: bad argument");
+    cudaError_t e = alpha_init(c, U);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    if ((st = collect(c))) return st;
+    double alpha = 0.0;
+    unsigned long long bits = c->ctl_host->amax[0][0];
+    memcpy(&alpha, &bits, sizeof(alpha));
+    *dt_out = (cfl * c->g.dx) / alpha;
+    return T7_OK;
+}
+
+t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
+    t7_status st = check_1d(c);
+    if (st) return st;
+    if (!U || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step: bad argument");
+    cudaError_t e = alpha_init(c, U);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
+    if ((e = rk3(c, U, dt)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+    return T7_OK;
+}
+
+t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out) {
+    t7_status st = check_1d(c);
+    if (st) return st;
+    if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
+    cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, max_steps, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ctl");
+    t7::Alpha1D a;
+    a.U = U;
+    a.n = c->g.nx;
+    a.sys = c->g.sys;
+    a.gamma = c->g.gamma;
+    a.a = c->g.adv_speed;
+    a.ctl = c->ctl;
+    a.slot = 0;
+    e = c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
+    // Steps are launched in chunks; between chunks the host polls whether the
+    // device-side clock has reached t_end (a step past it is a no-op anyway).
+    const int chunk = 64;
+    int launched = 0;
+    while (launched < max_steps) {
+        int k = max_steps - launched < chunk ? max_steps - launched : chunk;
+        for (int q = 0; q < k; q++)
+            if ((e = rk3(c, U, -1.0)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+        launched += k;
+        if (isfinite(t_end)) {
+            if ((e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(t7::DevCtl), cudaMemcpyDeviceToHost, c->stream)) !=
+                cudaSuccess)
+                return cuda_fail(c, e, "poll");
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+            if (!c->ctl_host->active || c->ctl_host->err || !(c->ctl_host->t < t_end)) break;
+        }
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    st = collect(c);
+    if (steps_out) *steps_out = c->ctl_host->steps;
+    if (t_out) *t_out = c->ctl_host->t;
+    return st;
+}
+
+t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
+                      double *t_out) {
+    t7_status st = check_1d(c);
+    if (st) return st;
+    if (!U_host) return fail(c, T7_EINVAL, "t7_run_host: null array");
+    size_t bytes = c->ncell * c->m * c->esize;
+    cudaError_t e = cudaMemcpyAsync(c->Uhost, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "H2D copy");
+    st = t7_run(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out);
+    if (st != T7_OK && st != T7_ENONPHYSICAL && st != T7_ENONFINITE) return st;
+    e = cudaMemcpyAsync(U_host, c->Uhost, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "D2H copy");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Internal declarations shared by the translation units of libteno7 (the
+// precision-specific kernel files and the C-ABI file).  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace t7 {
+
+enum { SYS_ADV = 0, SYS_EULER1D = 1, SYS_EULER2D = 2, SYS_BURGERS = 3 };
+enum { BC_PERIODIC = 0, BC_ZG = 1 };
+enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4 };
+
+// Device-resident control block of a context.  amax[slot][dir] holds the bit
+// pattern of a non-negative double (max characteristic speed) so that it can
+// be reduced with atomicMax on unsigned 64-bit integers.
+struct DevCtl {
+    unsigned long long amax[3][2];
+    double t, dt, t_end, cfl;
+    int steps, max_steps, active, err;
+    int err_index, pad0;
+};
+
+// One launch of the fused 1D stage kernel.
+struct Stage1D {
+    const void *Us;  // stage input state [m][n] (stencil reads)
+    const void *U0;  // U^n (pointwise reads; stages 1 and 2 only)
+    void *out;       // RK mode: stage output; RHS mode: dU/dt
+    uint8_t *masks;  // RHS mode, nullable: [2][m][n+1]
+    int n, sys, bc_lo, bc_hi;
+    double dx, eps, CT, gamma, a;
+    int rhs_mode;    // 1: write L(U) (and masks); 0: RK stage
+    int stage;       // 0, 1, 2 (RK mode)
+    double dt_fixed; // > 0: use it; otherwise the control block's dt
+    DevCtl *ctl;
+    int slot_in;     // alpha of Us
+};
+
+struct Alpha1D {
+    const void *U;
+    int n, sys;
+    double gamma, a;
+    DevCtl *ctl;
+    int slot;
+};
+
+struct Recon {
+    const void *v;  // n + 8 values
+    void *fhat;     // n + 1
+    uint8_t *d3, *D5;
+    int n, sign;
+    double eps, CT;
+    DevCtl *ctl;
+};
+
+cudaError_t launch_stage1d_f64(const Stage1D &p, cudaStream_t s);
+cudaError_t launch_stage1d_f32(const Stage1D &p, cudaStream_t s);
+cudaError_t launch_alpha1d_f64(const Alpha1D &p, cudaStream_t s);
+cudaError_t launch_alpha1d_f32(const Alpha1D &p, cudaStream_t s);
+cudaError_t launch_recon_f64(const Recon &p, cudaStream_t s);
+cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s);
+
+// Control-block helpers (teno7_api.cu).
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, int max_steps, cudaStream_t s);
+
+}  // namespace t7

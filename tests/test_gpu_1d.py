@@ -1,0 +1,264 @@
+"""GPU parity of the 1D CUDA path (through the C ABI) against the CPU oracle.
+
+FP64: the kernels evaluate every expression in the oracle's operation order
+without FMA contraction, so face values, masks, right-hand sides and whole runs
+are compared bit for bit (any difference is a bug).  FP32: masks are decided in
+FP32 (the kernel's precision); errors are measured against the FP64 oracle with
+the tolerance the accuracy target states (<= 1e-5 relative L1 on smooth cases),
+and the mask-flip fraction is bounded.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import riemann
+from paper_1808_00037_gb300 import binding as B
+from paper_1808_00037_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SYSMAP = {oracle.SYS_ADVECTION: B.T7_SCALAR_ADVECTION, oracle.SYS_EULER1D: B.T7_EULER1D,
+          oracle.SYS_BURGERS: B.T7_BURGERS}
+
+
+def ctx(sys, n, dx, prec=B.T7_F64, bc=(0, 0), a=1.0):
+    return B.Context(SYSMAP[sys], n, dx, prec=prec, bc=(bc[0], bc[1], 0, 0), adv_speed=a)
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def rel_l1(a, b):
+    return np.abs(a - b).sum() / np.abs(b).sum()
+
+
+# ------------------------------------------------------------ reconstruction --
+@pytest.mark.parametrize("n", [1, 2, 7, 252, 253, 254, 506, 1000])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_reconstruct_f64_bitexact(n, sign):
+    rng = np.random.default_rng(n * 7 + sign)
+    v = np.cumsum(rng.normal(size=n + 8)) * 0.3
+    v[(n + 8) // 3:] += 4.0  # a jump somewhere inside
+    v[(2 * (n + 8)) // 3:] *= -0.5
+    eps = 1e-4
+    fo, d3o, D5o = oracle.teno7_reconstruct(v, sign, eps)
+    c = ctx(oracle.SYS_ADVECTION, max(n, 1), 0.1)
+    fg, d3g, D5g = c.teno7_reconstruct(dev(v), sign, eps, want_bits=True)
+    c.sync()
+    assert np.array_equal(host(fg), fo)
+    assert np.array_equal(d3g.cpu().numpy(), d3o)
+    assert np.array_equal(D5g.cpu().numpy(), D5o)
+
+
+def test_reconstruct_every_pattern_and_coefficient():
+    """I.i.d. values drawn from magnitudes spread over five decades (4M values,
+    seed 12) reach all 28 attainable Delta patterns: the GPU selection and its
+    Table co2 row agree with the oracle bit for bit on every face."""
+    rng = np.random.default_rng(12)
+    N = 4_000_000
+    levels = np.array([0, 0.001, 0.01, 0.1, 0.3, 1, 3, 10, 100])
+    v = rng.choice(levels, size=N) * rng.choice([-1, 1], size=N) + rng.normal(size=N) * rng.choice(
+        [0, 1e-3, 1e-1], size=N)
+    n = N - 8
+    c = ctx(oracle.SYS_ADVECTION, n, 0.1)
+    for sign in (1, -1):
+        fo, d3o, D5o = oracle.teno7_reconstruct(v, sign, 1e-6)
+        assert len(np.unique(D5o)) == 28
+        fg, d3g, D5g = c.teno7_reconstruct(dev(v), sign, 1e-6, want_bits=True)
+        c.sync()
+        assert np.array_equal(D5g.cpu().numpy(), D5o)
+        assert np.array_equal(d3g.cpu().numpy(), d3o)
+        assert np.array_equal(host(fg), fo)
+
+
+def test_reconstruct_f32_masks_and_values():
+    rng = np.random.default_rng(1)
+    n = 2000
+    x = np.arange(n + 8) / n
+    v = np.sin(6 * np.pi * x) + np.where(x > 0.5, 1.0, 0.0) + 0.001 * rng.normal(size=n + 8)
+    fo, _, D5o = oracle.teno7_reconstruct(v, 1, 1e-6)
+    c = ctx(oracle.SYS_ADVECTION, n, 0.1, prec=B.T7_F32)
+    fg, _, D5g = c.teno7_reconstruct(dev(v, torch.float32), 1, 1e-6, want_bits=True)
+    c.sync()
+    same = D5g.cpu().numpy() == D5o
+    assert same.mean() > 0.99
+    assert np.max(np.abs(host(fg)[same] - fo[same])) < 1e-5 * np.max(np.abs(fo))
+
+
+# ------------------------------------------------------------------ RHS -------
+CASES = [
+    ("adv-sine", oracle.SYS_ADVECTION, lambda n: I.advection_sine(n)[:2], (0, 0), 1.0),
+    ("adv-neg", oracle.SYS_ADVECTION, lambda n: I.random_smooth_1d(3, n)[:2], (0, 0), -0.7),
+    ("burgers", oracle.SYS_BURGERS, lambda n: I.burgers_sine(n)[:2], (0, 0), 1.0),
+    ("sod", oracle.SYS_EULER1D, lambda n: I.riemann_tube(n, *I.SOD)[:2], (1, 1), 1.0),
+    ("lax", oracle.SYS_EULER1D, lambda n: I.riemann_tube(n, *I.LAX)[:2], (1, 1), 1.0),
+    ("shu-osher", oracle.SYS_EULER1D, lambda n: I.shu_osher(n), (1, 1), 1.0),
+    ("euler-periodic", oracle.SYS_EULER1D, lambda n: I.random_euler_smooth(5, n)[:2], (0, 0), 1.0),
+]
+
+
+@pytest.mark.parametrize("name,sys,gen,bc,a", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("n", [3, 200, 759, 1600])
+def test_rhs_f64_bitexact(name, sys, gen, bc, a, n):
+    U, dx = gen(n)
+    ro, alpha, mo = oracle.rhs_1d(sys, U, dx, a=a, bc=bc, want_masks=True)
+    c = ctx(sys, n, dx, bc=bc, a=a)
+    rg, mg = c.euler_rhs(dev(U), want_masks=True)
+    c.sync()
+    assert np.array_equal(mg.cpu().numpy(), mo)
+    assert np.array_equal(host(rg), ro)
+
+
+@pytest.mark.parametrize("name,sys,gen,bc,a", CASES, ids=[c[0] for c in CASES])
+def test_rk3_step_f64_bitexact(name, sys, gen, bc, a):
+    n = 1600
+    U, dx = gen(n)
+    dt = 0.5 * oracle.cfl_dt_1d(sys, U, dx, 1.0, a=a)
+    Uo = oracle.rk3_step_1d(sys, U, dx, dt, a=a, bc=bc)
+    c = ctx(sys, n, dx, bc=bc, a=a)
+    Ug = dev(U)
+    c.rk3_step(Ug, dt)
+    c.sync()
+    assert np.array_equal(host(Ug), Uo)
+    assert c.cfl_dt(dev(U), 0.5) == oracle.cfl_dt_1d(sys, U, dx, 0.5, a=a)
+
+
+# ------------------------------------------------------------- whole runs -----
+def test_advection_config_run_f64_bitexact():
+    """sin(pi x) on [-1, 1], N = 200, CFL 0.2 to t = 2: identical to the oracle."""
+    U, dx, x = I.advection_sine(200)
+    Uo, so, to, _ = oracle.run_1d(oracle.SYS_ADVECTION, U, dx, t_end=2.0, cfl=0.2)
+    c = ctx(oracle.SYS_ADVECTION, 200, dx)
+    Ug = dev(U)
+    sg, tg = c.run(Ug, 0.2, t_end=2.0)
+    assert (sg, tg) == (so, to)
+    assert np.array_equal(host(Ug), Uo)
+    assert np.max(np.abs(host(Ug)[0] - np.sin(np.pi * x))) < 2e-7
+
+
+def test_shu_osher_config_run_f64_bitexact():
+    """Shu-Osher, N = 1600 on [-5, 5], CFL 0.5 to t = 1.8, zero-gradient ends."""
+    U, dx = I.shu_osher(1600)
+    Uo, so, to, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=1.8, cfl=0.5, bc=(1, 1))
+    c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1))
+    Ug = dev(U)
+    sg, tg = c.run(Ug, 0.5, t_end=1.8)
+    assert (sg, tg) == (so, to)
+    assert np.array_equal(host(Ug), Uo)
+
+
+def test_shu_osher_config_run_f32():
+    U, dx = I.shu_osher(1600)
+    Uo, so, to, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=1.8, cfl=0.5, bc=(1, 1))
+    c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1), prec=B.T7_F32)
+    Ug = dev(U, torch.float32)
+    sg, tg = c.run(Ug, 0.5, t_end=1.8)
+    assert tg == pytest.approx(1.8, abs=1e-12)
+    err = rel_l1(host(Ug)[0], Uo[0])
+    # shock case: FP32 masks may flip near the shocks; the density stays close
+    assert err < 2e-3, err
+
+
+def test_f32_smooth_case_tolerance():
+    """Smooth cases: FP32 within 1e-5 relative L1 of the FP64 oracle."""
+    U, dx, x = I.advection_sine(200)
+    Uo, _, _, _ = oracle.run_1d(oracle.SYS_ADVECTION, U, dx, t_end=2.0, cfl=0.2)
+    c = ctx(oracle.SYS_ADVECTION, 200, dx, prec=B.T7_F32)
+    Ug = dev(U, torch.float32)
+    c.run(Ug, 0.2, t_end=2.0)
+    assert rel_l1(host(Ug)[0], Uo[0]) < 1e-5
+    U, dx, x = I.random_euler_smooth(7, 512)
+    Uo, _, to, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=0.2, cfl=0.5)
+    c = ctx(oracle.SYS_EULER1D, 512, dx, prec=B.T7_F32)
+    Ug = dev(U, torch.float32)
+    c.run(Ug, 0.5, t_end=0.2)
+    for k in range(3):
+        assert rel_l1(host(Ug)[k], Uo[k]) < 1e-5
+
+
+def test_sod_gpu_against_exact_riemann():
+    U, dx, x = I.riemann_tube(200, *I.SOD)
+    for prec, dtype in ((B.T7_F64, torch.float64), (B.T7_F32, torch.float32)):
+        c = ctx(oracle.SYS_EULER1D, 200, dx, bc=(1, 1), prec=prec)
+        Ug = dev(U, dtype)
+        c.run(Ug, 0.6, t_end=0.2)
+        rho, _, _ = riemann.sample(*I.SOD, (x - 0.5) / 0.2)
+        assert np.mean(np.abs(host(Ug)[0] - rho)) < 5e-3
+
+
+def test_run_host_matches_device_run():
+    U, dx = I.shu_osher(1600)
+    c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1))
+    Ud = dev(U)
+    sd, td = c.run(Ud, 0.5, max_steps=37)
+    Uh = np.ascontiguousarray(U)
+    sh, th = c.run_host(Uh, 0.5, max_steps=37)
+    assert (sd, td) == (sh, th) and sd == 37
+    assert np.array_equal(host(Ud), Uh)
+
+
+# --------------------------------------------------------- full-size checks ---
+NBIG = 1600 * 10486  # Shu-Osher profile tiled: 16,777,600 cells, dx = 1/160
+
+
+def test_full_size_rhs_sampled_f64():
+    """The benchmark's workload size: RHS of the tiled Shu-Osher profile, checked
+    on sampled cells against the oracle evaluated on windows around them (the RHS
+    at cell i depends only on cells i-4 .. i+4 and the global alpha)."""
+    U, dx = I.shu_osher(1600, tiles=NBIG // 1600)
+    n = U.shape[1]
+    alpha = oracle.alpha_1d(oracle.SYS_EULER1D, U)
+    c = ctx(oracle.SYS_EULER1D, n, dx, bc=(1, 1))
+    Ug = dev(U)
+    rg, mg = c.euler_rhs(Ug, want_masks=True)
+    c.sync()
+    rng = np.random.default_rng(9)
+    idx = np.concatenate([[0, 1, 2, 3, 252, 253, n - 1, n - 2, n - 5], rng.integers(0, n, 200)])
+    W = 12
+    for i in idx:
+        lo, hi = max(0, i - W), min(n, i + W + 1)
+        win = U[:, lo:hi]
+        ro, _, mo = oracle.rhs_1d(oracle.SYS_EULER1D, win, dx, bc=(1, 1), alpha=alpha, want_masks=True)
+        k = i - lo
+        if (lo > 0 and k < 6) or (hi < n and (hi - lo) - k < 7):
+            continue
+        assert np.array_equal(host(rg[:, i:i + 1])[:, 0], ro[:, k]), i
+        assert np.array_equal(mg[:, :, i].cpu().numpy(), mo[:, :, k]), i
+
+
+@pytest.mark.parametrize("prec,dtype", [(B.T7_F64, torch.float64), (B.T7_F32, torch.float32)])
+def test_full_size_periodic_conservation(prec, dtype):
+    """At the benchmark size with periodic ends, three SSP-RK3 steps conserve
+    every domain sum to round-off (a property that holds at any size)."""
+    U, dx = I.shu_osher(1600, tiles=NBIG // 1600)
+    c = ctx(oracle.SYS_EULER1D, U.shape[1], dx, bc=(0, 0), prec=prec)
+    Ug = dev(U, dtype)
+    s0 = Ug.double().sum(dim=1)
+    steps, t = c.run(Ug, 0.5, max_steps=3)
+    assert steps == 3
+    s1 = Ug.double().sum(dim=1)
+    tol = 1e-12 if prec == B.T7_F64 else 2e-6
+    assert torch.all(torch.abs(s1 - s0) <= tol * torch.abs(Ug.double()).sum(dim=1)), (s0, s1)
+
+
+def test_nonphysical_state_is_reported():
+    U, dx = I.shu_osher(1600)
+    U = U.copy()
+    U[2, 800] = -1.0  # negative energy -> negative pressure
+    c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1))
+    with pytest.raises(B.T7Error) as ei:
+        c.run(dev(U), 0.5, max_steps=2)
+    assert ei.value.status == B.T7_ENONPHYSICAL
+    # the context stays usable after the error
+    U2, _ = I.shu_osher(1600)
+    steps, _ = c.run(dev(U2), 0.5, max_steps=2)
+    assert steps == 2
