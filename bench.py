@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--only", choices=["f32", "f64"], default=None, help="time one precision (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
@@ -223,6 +225,8 @@ def main():
     hbm_peak, peak_kind = peaks()
     res = {}
     for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        if args.only and name != args.only:
+            continue
         steps = args.steps if name == "f32" or args.f64_steps is None else args.f64_steps
         ctx = B.Context(B.T7_EULER1D, n, dx, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
         U = torch.tensor(U0, dtype=dtype, device="cuda")
@@ -263,24 +267,30 @@ def main():
         del U
         torch.cuda.empty_cache()
 
+    if args.only:
+        if rank == 0:
+            print(json.dumps({"only": args.only, **res[args.only]}), flush=True)
+        return 0
     # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
     acc = {}
     Ua, dxa = I.shu_osher(N1)
     outs = {}
-    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+    for name, prec, dtype in (() if args.no_accuracy else
+                              (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64))):
         c = B.Context(B.T7_EULER1D, N1, dxa, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
         Ug = torch.tensor(Ua, dtype=dtype, device="cuda")
         c.run(Ug, CFL, t_end=1.8)
         outs[name] = (c, Ug)
-    f32 = outs["f32"][1].double().cpu().numpy()
-    f64 = outs["f64"][1].double().cpu().numpy()
-    acc["f32_vs_f64_rel_l1_rho"] = float(np.abs(f32[0] - f64[0]).sum() / np.abs(f64[0]).sum())
-    # stencil-selection flips: both precisions evaluate L(U) on the same FP64 end state
-    _, m64 = outs["f64"][0].euler_rhs(outs["f64"][1], want_masks=True)
-    _, m32 = outs["f32"][0].euler_rhs(outs["f64"][1].float(), want_masks=True)
-    torch.cuda.synchronize()
-    acc["mask_flip_fraction"] = float((m64 != m32).double().mean().item())
-    acc["case"] = "Shu-Osher N=1600, CFL 0.5, t=1.8"
+    if outs:
+        f32 = outs["f32"][1].double().cpu().numpy()
+        f64 = outs["f64"][1].double().cpu().numpy()
+        acc["f32_vs_f64_rel_l1_rho"] = float(np.abs(f32[0] - f64[0]).sum() / np.abs(f64[0]).sum())
+        # stencil-selection flips: both precisions evaluate L(U) on the same FP64 end state
+        _, m64 = outs["f64"][0].euler_rhs(outs["f64"][1], want_masks=True)
+        _, m32 = outs["f32"][0].euler_rhs(outs["f64"][1].float(), want_masks=True)
+        torch.cuda.synchronize()
+        acc["mask_flip_fraction"] = float((m64 != m32).double().mean().item())
+        acc["case"] = "Shu-Osher N=1600, CFL 0.5, t=1.8"
 
     if rank != 0:
         return 0

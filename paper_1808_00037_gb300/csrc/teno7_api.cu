@@ -49,15 +49,17 @@ bool is_1d(int sys) { return sys == T7_SCALAR_ADVECTION || sys == T7_EULER1D || 
 
 double eps_of(double eps, double d) { return eps < 0.0 ? d * d * d : eps; }
 
-__global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, int max_steps) {
+__global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, double dx, int max_steps) {
     for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = 0ull;
     ctl->t = 0.0;
     ctl->dt = 0.0;
     ctl->t_end = t_end;
     ctl->cfl = cfl;
+    ctl->dx = dx;
     ctl->steps = 0;
     ctl->max_steps = max_steps;
     ctl->active = 1;
+    ctl->blocks_done = 0u;
 }
 
 t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
@@ -76,6 +78,12 @@ t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
     p.gamma = c->g.gamma;
     p.a = c->g.adv_speed;
     p.ctl = c->ctl;
+    p.f_dx = (float)p.dx;
+    p.f_eps = (float)p.eps;
+    p.f_CT = (float)p.CT;
+    p.f_gamma = (float)p.gamma;
+    p.f_gm1 = (float)(p.gamma - 1.0);
+    p.f_a = (float)p.a;
     return p;
 }
 
@@ -107,6 +115,7 @@ cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed) {
         p.rhs_mode = 0;
         p.stage = k;
         p.dt_fixed = dt_fixed;
+        p.f_dt_fixed = (float)dt_fixed;
         p.slot_in = k;
         cudaError_t e = stage(c, p);
         if (e != cudaSuccess) return e;
@@ -139,8 +148,8 @@ t7_status check_1d(t7_ctx *c) {
 }  // namespace
 
 namespace t7 {
-cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, int max_steps, cudaStream_t s) {
-    ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, t_end, cfl, max_steps);
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, int max_steps, cudaStream_t s) {
+    ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, t_end, cfl, dx, max_steps);
     return cudaGetLastError();
 }
 }  // namespace t7
@@ -281,7 +290,7 @@ t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, in
     t7_status st = check_1d(c);
     if (st) return st;
     if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
-    cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, max_steps, c->stream);
+    cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, c->g.dx, max_steps, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ctl");
     t7::Alpha1D a;
     a.U = U;

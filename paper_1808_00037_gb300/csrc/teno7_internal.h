@@ -13,11 +13,19 @@ enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4 };
 // Device-resident control block of a context.  amax[slot][dir] holds the bit
 // pattern of a non-negative double (max characteristic speed) so that it can
 // be reduced with atomicMax on unsigned 64-bit integers.
+//
+// The last CTA of every stage launch (and of the alpha kernel) finalizes the
+// launch: it converts the freshly reduced alpha to float (alpha_f), clears the
+// slot the next launch accumulates into, and at the end of an RK step advances
+// t and computes the next CFL step, so that no CTA ever divides in FP64.
 struct DevCtl {
     unsigned long long amax[3][2];
-    double t, dt, t_end, cfl;
+    double t, dt, t_end, cfl, dx;
+    float alpha_f[3][2];
+    float dt_f, pad_f;
     int steps, max_steps, active, err;
-    int err_index, pad0;
+    int err_index;
+    unsigned blocks_done;
 };
 
 // One launch of the fused 1D stage kernel.
@@ -33,6 +41,8 @@ struct Stage1D {
     double dt_fixed; // > 0: use it; otherwise the control block's dt
     DevCtl *ctl;
     int slot_in;     // alpha of Us
+    // the same parameters rounded to float, for the FP32 kernels
+    float f_dx, f_eps, f_CT, f_gamma, f_gm1, f_a, f_dt_fixed;
 };
 
 struct Alpha1D {
@@ -42,6 +52,9 @@ struct Alpha1D {
     DevCtl *ctl;
     int slot;
 };
+
+// Finalization done by the last CTA of a launch (see DevCtl).
+enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_STEP = 2 };
 
 struct Recon {
     const void *v;  // n + 8 values
@@ -60,6 +73,6 @@ cudaError_t launch_recon_f64(const Recon &p, cudaStream_t s);
 cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s);
 
 // Control-block helpers (teno7_api.cu).
-cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, int max_steps, cudaStream_t s);
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, int max_steps, cudaStream_t s);
 
 }  // namespace t7

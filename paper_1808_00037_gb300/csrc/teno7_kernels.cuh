@@ -61,38 +61,39 @@ __device__ __forceinline__ int pack_delta(unsigned dm, unsigned d0, unsigned dp)
                  ((dp >> 2) & 1u));
 }
 
-// Table co2, coefficients on f_{i-3} .. f_{i+3}; each entry is the nearest
-// double to the printed rational.
-__device__ __forceinline__ double coef_f64(int idx) {
+// Table co2, coefficients on f_{i-3} .. f_{i+3}; each FP64 entry is the nearest
+// double to the printed rational (FP32: that double rounded to float).
+template <typename T>
+__device__ __forceinline__ T coef(int idx) {
     switch (idx) {
         // clang-format off
-        case 0: return -1.0/140.0; case 1: return 5.0/84.0; case 2: return -101.0/420.0; case 3: return 319.0/420.0;
-        case 4: return 107.0/210.0; case 5: return -19.0/210.0; case 6: return 1.0/105.0;
-        case 7: return 0.0; case 8: return 1.0/60.0; case 9: return -2.0/15.0; case 10: return 37.0/60.0;
-        case 11: return 37.0/60.0; case 12: return -2.0/15.0; case 13: return 1.0/60.0;
-        case 14: return -1.0/60.0; case 15: return 7.0/60.0; case 16: return -23.0/60.0; case 17: return 19.0/20.0;
-        case 18: return 11.0/30.0; case 19: return -1.0/30.0; case 20: return 0.0;
-        case 21: return 0.0; case 22: return 0.0; case 23: return -1.0/20.0; case 24: return 9.0/20.0;
-        case 25: return 47.0/60.0; case 26: return -13.0/60.0; case 27: return 1.0/30.0;
-        case 28: return 0.0; case 29: return 1.0/30.0; case 30: return -13.0/60.0; case 31: return 47.0/60.0;
-        case 32: return 9.0/20.0; case 33: return -1.0/20.0; case 34: return 0.0;
-        case 35: return -1.0/20.0; case 36: return 17.0/60.0; case 37: return -43.0/60.0; case 38: return 77.0/60.0;
-        case 39: return 1.0/5.0; case 40: return 0.0; case 41: return 0.0;
-        case 42: return 0.0; case 43: return 0.0; case 44: return 0.0; case 45: return 1.0/4.0;
-        case 46: return 13.0/12.0; case 47: return -5.0/12.0; case 48: return 1.0/12.0;
-        case 49: return 0.0; case 50: return 0.0; case 51: return -1.0/12.0; case 52: return 7.0/12.0;
-        case 53: return 7.0/12.0; case 54: return -1.0/12.0; case 55: return 0.0;
-        case 56: return 0.0; case 57: return 1.0/12.0; case 58: return -5.0/12.0; case 59: return 13.0/12.0;
-        case 60: return 1.0/4.0; case 61: return 0.0; case 62: return 0.0;
-        case 63: return -1.0/4.0; case 64: return 13.0/12.0; case 65: return -23.0/12.0; case 66: return 25.0/12.0;
-        case 67: return 0.0; case 68: return 0.0; case 69: return 0.0;
-        case 70: return 0.0; case 71: return 0.0; case 72: return 0.0; case 73: return 1.0/3.0;
-        case 74: return 5.0/6.0; case 75: return -1.0/6.0; case 76: return 0.0;
-        case 77: return 0.0; case 78: return 0.0; case 79: return -1.0/6.0; case 80: return 5.0/6.0;
-        case 81: return 1.0/3.0; case 82: return 0.0; case 83: return 0.0;
-        case 84: return 0.0; case 85: return 1.0/3.0; case 86: return -7.0/6.0; case 87: return 11.0/6.0;
-        case 88: return 0.0; case 89: return 0.0; case 90: return 0.0;
-        default: return 0.0;
+        case 0: return T(-1.0/140.0); case 1: return T(5.0/84.0); case 2: return T(-101.0/420.0); case 3: return T(319.0/420.0);
+        case 4: return T(107.0/210.0); case 5: return T(-19.0/210.0); case 6: return T(1.0/105.0);
+        case 7: return T(0); case 8: return T(1.0/60.0); case 9: return T(-2.0/15.0); case 10: return T(37.0/60.0);
+        case 11: return T(37.0/60.0); case 12: return T(-2.0/15.0); case 13: return T(1.0/60.0);
+        case 14: return T(-1.0/60.0); case 15: return T(7.0/60.0); case 16: return T(-23.0/60.0); case 17: return T(19.0/20.0);
+        case 18: return T(11.0/30.0); case 19: return T(-1.0/30.0); case 20: return T(0);
+        case 21: return T(0); case 22: return T(0); case 23: return T(-1.0/20.0); case 24: return T(9.0/20.0);
+        case 25: return T(47.0/60.0); case 26: return T(-13.0/60.0); case 27: return T(1.0/30.0);
+        case 28: return T(0); case 29: return T(1.0/30.0); case 30: return T(-13.0/60.0); case 31: return T(47.0/60.0);
+        case 32: return T(9.0/20.0); case 33: return T(-1.0/20.0); case 34: return T(0);
+        case 35: return T(-1.0/20.0); case 36: return T(17.0/60.0); case 37: return T(-43.0/60.0); case 38: return T(77.0/60.0);
+        case 39: return T(1.0/5.0); case 40: return T(0); case 41: return T(0);
+        case 42: return T(0); case 43: return T(0); case 44: return T(0); case 45: return T(1.0/4.0);
+        case 46: return T(13.0/12.0); case 47: return T(-5.0/12.0); case 48: return T(1.0/12.0);
+        case 49: return T(0); case 50: return T(0); case 51: return T(-1.0/12.0); case 52: return T(7.0/12.0);
+        case 53: return T(7.0/12.0); case 54: return T(-1.0/12.0); case 55: return T(0);
+        case 56: return T(0); case 57: return T(1.0/12.0); case 58: return T(-5.0/12.0); case 59: return T(13.0/12.0);
+        case 60: return T(1.0/4.0); case 61: return T(0); case 62: return T(0);
+        case 63: return T(-1.0/4.0); case 64: return T(13.0/12.0); case 65: return T(-23.0/12.0); case 66: return T(25.0/12.0);
+        case 67: return T(0); case 68: return T(0); case 69: return T(0);
+        case 70: return T(0); case 71: return T(0); case 72: return T(0); case 73: return T(1.0/3.0);
+        case 74: return T(5.0/6.0); case 75: return T(-1.0/6.0); case 76: return T(0);
+        case 77: return T(0); case 78: return T(0); case 79: return T(-1.0/6.0); case 80: return T(5.0/6.0);
+        case 81: return T(1.0/3.0); case 82: return T(0); case 83: return T(0);
+        case 84: return T(0); case 85: return T(1.0/3.0); case 86: return T(-7.0/6.0); case 87: return T(11.0/6.0);
+        case 88: return T(0); case 89: return T(0); case 90: return T(0);
+        default: return T(0);
         // clang-format on
     }
 }
@@ -200,13 +201,15 @@ __device__ __forceinline__ void latch_error(DevCtl *ctl, int flag, int index) {
     atomicMin(&ctl->err_index, index);
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
 // Largest characteristic speed of one cell (1D systems) and its validity.
+// FP64 follows the oracle's expression order; FP32 uses fast reciprocals.
 template <typename T, int SYS>
 __device__ __forceinline__ T wavespeed1d(const T *Uc, T gm1, T gamma, T a, int *flag) {
     if (SYS == SYS_ADV) return absval(a);
@@ -214,154 +217,262 @@ __device__ __forceinline__ T wavespeed1d(const T *Uc, T gm1, T gamma, T a, int *
         if (!isfinite(Uc[0])) *flag |= ERR_NONFINITE;
         return absval(Uc[0]);
     }
-    T u = Uc[1] / Uc[0];
-    T p = gm1 * (Uc[2] - T(0.5) * Uc[1] * u);
-    T c = sq_root(gamma * p / Uc[0]);
+    T u, p, c;
+    if constexpr (sizeof(T) == 8) {
+        u = Uc[1] / Uc[0];
+        p = gm1 * (Uc[2] - T(0.5) * Uc[1] * u);
+        c = sq_root(gamma * p / Uc[0]);
+    } else {
+        const float ri = __frcp_rn(Uc[0]);
+        u = Uc[1] * ri;
+        p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
+        c = __fsqrt_rn(gamma * p * ri);
+    }
     if (!(Uc[0] > T(0)) || !(p > T(0))) *flag |= ERR_NONPHYSICAL;
     if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2])) *flag |= ERR_NONFINITE;
     return absval(u) + c;
 }
 
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f) {
+    if constexpr (sizeof(T) == 8) {
+        return d;
+    } else {
+        return f;
+    }
+}
+
+// Table co2 row 0 (the seventh-order polynomial) as immediates: the common
+// smooth case avoids the shared-memory coefficient table.  Same values and
+// summation order as the table path.
+template <typename T>
+__device__ __forceinline__ T poly_f0(T v0, T v1, T v2, T v3, T v4, T v5, T v6) {
+    T s = T(-1.0 / 140.0) * v0;
+    s = s + T(5.0 / 84.0) * v1;
+    s = s + T(-101.0 / 420.0) * v2;
+    s = s + T(319.0 / 420.0) * v3;
+    s = s + T(107.0 / 210.0) * v4;
+    s = s + T(-19.0 / 210.0) * v5;
+    s = s + T(1.0 / 105.0) * v6;
+    return s;
+}
+
+// --------------------------------------------------------------------------
+// Last-CTA finalization of a launch (see DevCtl).  Called by thread 0 of every
+// CTA after its atomicMax into amax[slot_out].
+//   zero_slot    the slot the next launch accumulates into (cleared here)
+//   end_of_step  advance t and steps by the step just taken
+//   plan_step    compute active and the CFL step dt for the next RK step from
+//                alpha(U^n) = amax[slot_out] (oracle's expression order)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zero_slot, bool end_of_step,
+                                              bool plan_step) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
+    if (prev != gridDim.x - 1) return;
+    __threadfence();
+    const double a = __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][0], 0ull));
+    ctl->alpha_f[slot_out][0] = (float)a;
+    ctl->amax[zero_slot][0] = 0ull;
+    if (end_of_step) {
+        ctl->t = ctl->t + ctl->dt;
+        ctl->steps = ctl->steps + 1;
+    }
+    if (plan_step) {
+        const double t = ctl->t, t_end = ctl->t_end;
+        const int active = (ctl->steps < ctl->max_steps) && (t < t_end);
+        double dt = (ctl->cfl * ctl->dx) / a;
+        if (t + dt > t_end) dt = t_end - t;
+        ctl->active = active;
+        ctl->dt = dt;
+        ctl->dt_f = (float)dt;
+    }
+    ctl->blocks_done = 0u;
+}
+
 // ==========================================================================
 // Fused 1D stage kernel.  SYS in {SYS_ADV, SYS_BURGERS, SYS_EULER1D}.
+//
+// Warp tiles: warp tile w updates the WT = 29 cells c0 = 29 w .. c0 + 28.
+// Lane l owns the face j+1/2 with j = c0 - 2 + l (faces c0-2 .. c0+29) and
+// stages cells c0-5+l (and c0+27+l for l < 7) in warp-private shared memory.
+// Neighbouring faces' cutoff words and face fluxes travel by __shfl, so the
+// hot loop has no CTA-wide barrier; lanes 1..30 produce face fluxes and
+// lanes 2..30 update cells.  Warps loop over tiles with a grid stride.
 // ==========================================================================
+constexpr int WT = 29;   // cells updated per warp tile
+constexpr int WS = 39;   // cells staged per warp tile
+constexpr int WC = 40;   // padded row length
+constexpr int WPB = 8;   // warps per CTA
+
 template <typename T, int SYS>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
+__global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;  // u, H, sqrt(rho)
-    __shared__ T s_U[M][NCP];
-    __shared__ T s_gp[M][NCP];
-    __shared__ T s_gm[M][NCP];
-    __shared__ T s_pr[NP][NCP];
-    __shared__ T s_coef[91];
-    __shared__ unsigned s_bits[NT];
-    __shared__ T s_fh[M][NT];
-    __shared__ double s_red[NT / 32];
+    constexpr bool F64 = sizeof(T) == 8;
+    __shared__ T s_U[WPB][M][WC];
+    __shared__ T s_gp[WPB][M][WC];
+    __shared__ T s_gm[WPB][M][WC];
+    __shared__ T s_pr[WPB][NP][WC];
+    __shared__ T s_coef[WPB][92];
+    __shared__ T s_red[WPB];
 
     DevCtl *ctl = p.ctl;
-    const int tid = threadIdx.x;
-    const int n = p.n;
-    const int s = blockIdx.x * TILE;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
 
-    // ---- time step of this stage -----------------------------------------
-    const double alpha_d = __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
-    double dt = 0.0;
-    if (!p.rhs_mode) {
-        if (p.dt_fixed > 0.0) {
-            dt = p.dt_fixed;
-        } else if (p.stage == 0) {
-            const double t = ctl->t, t_end = ctl->t_end;
-            const bool active = (ctl->steps < ctl->max_steps) && (t < t_end);
-            dt = (ctl->cfl * p.dx) / alpha_d;
-            if (t + dt > t_end) dt = t_end - t;
-            if (blockIdx.x == 0 && tid == 0) {
-                ctl->dt = dt;
-                ctl->active = active ? 1 : 0;
-            }
-            if (!active) return;
-        } else {
-            if (!ctl->active) return;
-            dt = ctl->dt;
-        }
-        if (blockIdx.x == 0 && tid == 0) ctl->amax[(p.stage + 2) % 3][0] = 0ull;
+    T alpha, dtT;
+    if constexpr (F64) {
+        alpha = __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
+        dtT = fixed ? p.dt_fixed : ctl->dt;
+    } else {
+        alpha = ctl->alpha_f[p.slot_in][0];
+        dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
     }
-
-    const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0), a = T(p.a);
-    const T alpha = T(alpha_d), eps = T(p.eps), CT = T(p.CT);
+    const T gamma = pick<T>(p.gamma, p.f_gamma), gm1 = pick<T>(p.gamma - 1.0, p.f_gm1), a = pick<T>(p.a, p.f_a);
+    const T eps = pick<T>(p.eps, p.f_eps), CT = pick<T>(p.CT, p.f_CT);
     const T *Us = static_cast<const T *>(p.Us);
+    const T *U0 = static_cast<const T *>(p.U0);
+    T *out = static_cast<T *>(p.out);
+    const int n = p.n;
+    const int ntiles = (n + WT - 1) / WT;
+    T (*sU)[WC] = s_U[warp];
+    T (*sgp)[WC] = s_gp[warp];
+    T (*sgm)[WC] = s_gm[warp];
+    T (*spr)[WC] = s_pr[warp];
+    const T *scoef = s_coef[warp];
+    T wsmax = T(0);
+    __syncwarp();
 
-    for (int q = tid; q < 91; q += NT) s_coef[q] = T(coef_f64(q));
-
-    // ---- stage per-cell data: cells s-5 .. s+257 ---------------------------
-    for (int c = tid; c < NCELL; c += NT) {
-        const int gi = ghost_map(s - HALO + c, n, p.bc_lo, p.bc_hi);
-        T U[M], F[M];
+    for (int tile = blockIdx.x * WPB + warp; tile < ntiles; tile += gridDim.x * WPB) {
+        const int c0 = tile * WT;
+        // ---- stage cells c0-5 .. c0+33 -----------------------------------
+        for (int c = lane; c < WS; c += 32) {
+            int gi = c0 - 5 + c;
+            if (gi < 0 || gi >= n) gi = ghost_map(gi, n, p.bc_lo, p.bc_hi);
+            T U[M], F[M];
 #pragma unroll
-        for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * n + gi];
-        if (SYS == SYS_ADV) {
-            F[0] = a * U[0];
-        } else if (SYS == SYS_BURGERS) {
-            F[0] = T(0.5) * U[0] * U[0];
-        } else {
-            T u = U[1] / U[0];
-            T pr = gm1 * (U[2] - T(0.5) * U[1] * u);
-            F[0] = U[1];
-            F[1] = U[1] * u + pr;
-            F[2] = u * (U[2] + pr);
-            s_pr[0][c] = u;
-            s_pr[NP > 1 ? 1 : 0][c] = (U[2] + pr) / U[0];
-            s_pr[NP > 2 ? 2 : 0][c] = sq_root(U[0]);
+            for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * n + gi];
+            if (SYS == SYS_ADV) {
+                F[0] = a * U[0];
+            } else if (SYS == SYS_BURGERS) {
+                F[0] = T(0.5) * U[0] * U[0];
+            } else {
+                if constexpr (F64) {
+                    T u = U[1] / U[0];
+                    T pr = gm1 * (U[2] - T(0.5) * U[1] * u);
+                    F[0] = U[1];
+                    F[1] = U[1] * u + pr;
+                    F[2] = u * (U[2] + pr);
+                    spr[0][c] = u;
+                    spr[NP > 1 ? 1 : 0][c] = (U[2] + pr) / U[0];
+                    spr[NP > 2 ? 2 : 0][c] = sq_root(U[0]);
+                } else {
+                    const float ri = __frcp_rn(U[0]);
+                    const float u = U[1] * ri;
+                    const float pr = gm1 * (U[2] - 0.5f * U[1] * u);
+                    F[0] = U[1];
+                    F[1] = U[1] * u + pr;
+                    F[2] = u * (U[2] + pr);
+                    spr[0][c] = u;
+                    spr[NP > 1 ? 1 : 0][c] = (U[2] + pr) * ri;
+                    spr[NP > 2 ? 2 : 0][c] = __fsqrt_rn(U[0]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                sU[k][c] = U[k];
+                sgp[k][c] = T(0.5) * (F[k] + alpha * U[k]);
+                sgm[k][c] = T(0.5) * (F[k] - alpha * U[k]);
+            }
         }
+        __syncwarp();
+
+        // ---- face j+1/2: frame, projection, cutoff bits --------------------
+        const int j = c0 - 2 + lane;
+        T L[M][M];
+        T ut = T(0), cc = T(0), Ht = T(0);
+        int flag = 0;
+        if (SYS == SYS_EULER1D) {
+            const T ul = spr[0][lane + 3], ur = spr[0][lane + 4];
+            const T Hl = spr[NP > 1 ? 1 : 0][lane + 3], Hr = spr[NP > 1 ? 1 : 0][lane + 4];
+            const T sl = spr[NP > 2 ? 2 : 0][lane + 3], sr = spr[NP > 2 ? 2 : 0][lane + 4];
+            if constexpr (F64) {
+                // Roe average and eigenvectors in the oracle's operation order
+                ut = (sl * ul + sr * ur) / (sl + sr);
+                Ht = (sl * Hl + sr * Hr) / (sl + sr);
+                const T c2 = gm1 * (Ht - T(0.5) * ut * ut);
+                cc = sq_root(c2);
+                const T b1 = gm1 / c2;
+                const T b2 = T(0.5) * ut * ut * b1;
+                L[0][0] = T(0.5) * (b2 + ut / cc);
+                L[0][1 % M] = T(-0.5) * (b1 * ut + T(1) / cc);
+                L[0][2 % M] = T(0.5) * b1;
+                L[1 % M][0] = T(1) - b2;
+                L[1 % M][1 % M] = b1 * ut;
+                L[1 % M][2 % M] = -b1;
+                L[2 % M][0] = T(0.5) * (b2 - ut / cc);
+                L[2 % M][1 % M] = T(-0.5) * (b1 * ut - T(1) / cc);
+                L[2 % M][2 % M] = T(0.5) * b1;
+                if (!(c2 > T(0))) flag |= ERR_NONPHYSICAL;
+            } else {
+                const float w = __frcp_rn(sl + sr);
+                ut = (sl * ul + sr * ur) * w;
+                Ht = (sl * Hl + sr * Hr) * w;
+                const float c2 = gm1 * (Ht - 0.5f * ut * ut);
+                const float rc = rsqrtf(c2);  // 1/c
+                cc = c2 * rc;
+                const float b1 = gm1 * (rc * rc);
+                const float b2 = 0.5f * ut * ut * b1;
+                const float uc = ut * rc;
+                L[0][0] = 0.5f * (b2 + uc);
+                L[0][1 % M] = -0.5f * (b1 * ut + rc);
+                L[0][2 % M] = 0.5f * b1;
+                L[1 % M][0] = 1.f - b2;
+                L[1 % M][1 % M] = b1 * ut;
+                L[1 % M][2 % M] = -b1;
+                L[2 % M][0] = 0.5f * (b2 - uc);
+                L[2 % M][1 % M] = -0.5f * (b1 * ut - rc);
+                L[2 % M][2 % M] = 0.5f * b1;
+                if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+            }
+        } else {
+            L[0][0] = T(1);
+        }
+
+        T qp[M][7], qm[M][7];
+        unsigned word = 0;
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            s_U[k][c] = U[k];
-            s_gp[k][c] = T(0.5) * (F[k] + alpha * U[k]);
-            s_gm[k][c] = T(0.5) * (F[k] - alpha * U[k]);
-        }
-    }
-    __syncthreads();
-
-    // ---- face j+1/2, j = s-2+tid: frame, projection, cutoff bits ------------
-    T L[M][M];
-    T ut = T(0), cc = T(0), Ht = T(0);
-    int flag = 0;
-    if (SYS == SYS_EULER1D) {
-        const T ul = s_pr[0][tid + 3], ur = s_pr[0][tid + 4];
-        const T Hl = s_pr[NP > 1 ? 1 : 0][tid + 3], Hr = s_pr[NP > 1 ? 1 : 0][tid + 4];
-        const T sl = s_pr[NP > 2 ? 2 : 0][tid + 3], sr = s_pr[NP > 2 ? 2 : 0][tid + 4];
-        ut = (sl * ul + sr * ur) / (sl + sr);
-        Ht = (sl * Hl + sr * Hr) / (sl + sr);
-        const T c2 = gm1 * (Ht - T(0.5) * ut * ut);
-        cc = sq_root(c2);
-        const T b1 = gm1 / c2;
-        const T b2 = T(0.5) * ut * ut * b1;
-        L[0][0] = T(0.5) * (b2 + ut / cc);
-        L[0][1 % M] = T(-0.5) * (b1 * ut + T(1) / cc);
-        L[0][2 % M] = T(0.5) * b1;
-        L[1 % M][0] = T(1) - b2;
-        L[1 % M][1 % M] = b1 * ut;
-        L[1 % M][2 % M] = -b1;
-        L[2 % M][0] = T(0.5) * (b2 - ut / cc);
-        L[2 % M][1 % M] = T(-0.5) * (b1 * ut - T(1) / cc);
-        L[2 % M][2 % M] = T(0.5) * b1;
-        if (!(c2 > T(0))) flag |= ERR_NONPHYSICAL;
-    } else {
-        L[0][0] = T(1);
-    }
-
-    T qp[M][7], qm[M][7];
-    unsigned word = 0;
 #pragma unroll
-    for (int k = 0; k < M; k++) {
+            for (int t = 0; t < 7; t++) {
+                if (M == 1) {
+                    qp[k][t] = sgp[0][lane + t];
+                    qm[k][t] = sgm[0][lane + 1 + t];
+                } else {
+                    T sp = L[k][0] * sgp[0][lane + t];
+                    T sm = L[k][0] * sgm[0][lane + 1 + t];
 #pragma unroll
-        for (int t = 0; t < 7; t++) {
-            if (M == 1) {
-                qp[k][t] = s_gp[0][tid + t];
-                qm[k][t] = s_gm[0][tid + 1 + t];
-            } else {
-                T sp = L[k][0] * s_gp[0][tid + t];
-                T sm = L[k][0] * s_gm[0][tid + 1 + t];
-#pragma unroll
-                for (int c = 1; c < M; c++) {
-                    sp = sp + L[k][c] * s_gp[c][tid + t];
-                    sm = sm + L[k][c] * s_gm[c][tid + 1 + t];
+                    for (int c = 1; c < M; c++) {
+                        sp = sp + L[k][c] * sgp[c][lane + t];
+                        sm = sm + L[k][c] * sgm[c][lane + 1 + t];
+                    }
+                    qp[k][t] = sp;
+                    qm[k][t] = sm;
                 }
-                qp[k][t] = sp;
-                qm[k][t] = sm;
             }
+            const unsigned bp = cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT);
+            const unsigned bm = cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT);
+            word |= bp << (3 * k);
+            word |= bm << (3 * (M + k));
         }
-        const unsigned bp = cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT);
-        const unsigned bm = cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT);
-        word |= bp << (3 * k);
-        word |= bm << (3 * (M + k));
-    }
-    s_bits[tid] = word;
-    __syncthreads();
+        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
+        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
 
-    // ---- selection, polynomial, back-projection ----------------------------
-    const int j = s - 2 + tid;  // this thread's face is j+1/2
-    if (tid >= 1 && tid <= NT - 2) {
-        const unsigned wl = s_bits[tid - 1], wr = s_bits[tid + 1];
+        // ---- selection, polynomial, back-projection ------------------------
+        const bool face_out = lane >= 1 && lane <= 30;
         T f[M];
 #pragma unroll
         for (int k = 0; k < M; k++) {
@@ -370,104 +481,456 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(c
             int mp = lut_select(Dp), mm = lut_select(Dm);
             if (mp == 15) {
                 mp = 11;
-                flag |= ERR_NOEXIST;
+                if (face_out) flag |= ERR_NOEXIST;
             }
             if (mm == 15) {
                 mm = 11;
-                flag |= ERR_NOEXIST;
+                if (face_out) flag |= ERR_NOEXIST;
             }
-            const T fp = poly7(s_coef + 7 * mp, qp[k][0], qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], qp[k][6]);
-            const T fm = poly7(s_coef + 7 * mm, qm[k][6], qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], qm[k][0]);
+            T fp, fm;
+            if (mp == 0)
+                fp = poly_f0(qp[k][0], qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], qp[k][6]);
+            else
+                fp = poly7(scoef + 7 * mp, qp[k][0], qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], qp[k][6]);
+            if (mm == 0)
+                fm = poly_f0(qm[k][6], qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], qm[k][0]);
+            else
+                fm = poly7(scoef + 7 * mm, qm[k][6], qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], qm[k][0]);
             f[k] = fp + fm;
-            if (p.rhs_mode && p.masks && j >= -1 && j <= n - 1) {
+            if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= n - 1) {
                 p.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dp;
                 p.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dm;
             }
         }
+        T fh[M];
         if (SYS == SYS_EULER1D) {
             // R columns: eigenvectors of u-c, u, u+c at the Roe state
             const T R20 = Ht - ut * cc, R21 = T(0.5) * ut * ut, R22 = Ht + ut * cc;
-            s_fh[0][tid] = f[0] + f[1 % M] + f[2 % M];
-            s_fh[1 % M][tid] = (ut - cc) * f[0] + ut * f[1 % M] + (ut + cc) * f[2 % M];
-            s_fh[2 % M][tid] = R20 * f[0] + R21 * f[1 % M] + R22 * f[2 % M];
+            fh[0] = f[0] + f[1 % M] + f[2 % M];
+            fh[1 % M] = (ut - cc) * f[0] + ut * f[1 % M] + (ut + cc) * f[2 % M];
+            fh[2 % M] = R20 * f[0] + R21 * f[1 % M] + R22 * f[2 % M];
         } else {
-            s_fh[0][tid] = f[0];
+            fh[0] = f[0];
         }
-    }
-    if (flag && j >= -2 && j <= n) latch_error(ctl, (flag & ERR_NONPHYSICAL) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), j);
-    __syncthreads();
+        if (flag && face_out && j >= -2 && j <= n)
+            latch_error(ctl, (flag & ERR_NONPHYSICAL) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), j);
 
-    // ---- flux difference and RK stage ---------------------------------------
-    const int i = j;  // cell i = j: faces i-1/2 (tid-1) and i+1/2 (tid)
-    double ws = 0.0;
-    if (tid >= 2 && tid <= NT - 2 && i < n) {
-        T r[M];
-        const T dxT = T(p.dx);
+        // ---- flux difference and RK stage ----------------------------------
+        T fprev[M];
 #pragma unroll
-        for (int k = 0; k < M; k++) r[k] = (s_fh[k][tid - 1] - s_fh[k][tid]) / dxT;
-        T *out = static_cast<T *>(p.out);
-        if (p.rhs_mode) {
+        for (int k = 0; k < M; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
+        const int i = j;  // cell i: faces i-1/2 (lane-1) and i+1/2 (this lane)
+        if (lane >= 2 && lane <= 30 && i < n) {
+            T r[M];
+            if constexpr (F64) {
 #pragma unroll
-            for (int k = 0; k < M; k++) out[(size_t)k * n + i] = r[k];
-        } else {
-            const T dtT = T(dt);
-            const T *U0 = static_cast<const T *>(p.U0);
-            T o[M];
+                for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) / p.dx;
+            } else {
+                const float idx = __frcp_rn(p.f_dx);
 #pragma unroll
-            for (int k = 0; k < M; k++) {
-                const T us = s_U[k][tid + 3];
-                if (p.stage == 0) {
-                    o[k] = us + dtT * r[k];
-                } else if (p.stage == 1) {
-                    o[k] = T(0.75) * U0[(size_t)k * n + i] + T(0.25) * (us + dtT * r[k]);
-                } else {
-                    if constexpr (sizeof(T) == 8) {
-                        o[k] = T(1.0 / 3.0) * U0[(size_t)k * n + i] + T(2.0 / 3.0) * (us + dtT * r[k]);
-                    } else {
-                        // in FP32, float(1/3) + float(2/3) = 1 + 6e-8 would grow the
-                        // solution by that factor every step: use u0 + 2/3 (v - u0)
-                        const T u0 = U0[(size_t)k * n + i];
-                        o[k] = fmaf(2.0f / 3.0f, (us + dtT * r[k]) - u0, u0);
-                    }
-                }
-                out[(size_t)k * n + i] = o[k];
+                for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
             }
-            int wflag = 0;
-            ws = (double)wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag);
-            if (wflag) latch_error(ctl, wflag, i);
+            if (p.rhs_mode) {
+#pragma unroll
+                for (int k = 0; k < M; k++) out[(size_t)k * n + i] = r[k];
+            } else {
+                T o[M];
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    const T us = sU[k][lane + 3];
+                    if (p.stage == 0) {
+                        o[k] = us + dtT * r[k];
+                    } else if (p.stage == 1) {
+                        o[k] = T(0.75) * U0[(size_t)k * n + i] + T(0.25) * (us + dtT * r[k]);
+                    } else {
+                        if constexpr (F64) {
+                            o[k] = T(1.0 / 3.0) * U0[(size_t)k * n + i] + T(2.0 / 3.0) * (us + dtT * r[k]);
+                        } else {
+                            // in FP32, float(1/3) + float(2/3) = 1 + 6e-8 would grow the
+                            // solution by that factor every step: use u0 + 2/3 (v - u0)
+                            const T u0 = U0[(size_t)k * n + i];
+                            o[k] = fmaf(2.0f / 3.0f, (us + dtT * r[k]) - u0, u0);
+                        }
+                    }
+                    out[(size_t)k * n + i] = o[k];
+                }
+                int wflag = 0;
+                wsmax = fmax(wsmax, wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag));
+                if (wflag) latch_error(ctl, wflag, i);
+            }
         }
+        __syncwarp();  // the next tile overwrites this warp's staging rows
     }
+
     if (!p.rhs_mode) {
-        ws = warp_max(ws);
-        if ((tid & 31) == 0) s_red[tid >> 5] = ws;
+        wsmax = warp_max(wsmax);
+        if (lane == 0) s_red[warp] = wsmax;
         __syncthreads();
-        if (tid < 32) {
-            double v = tid < NT / 32 ? s_red[tid] : 0.0;
-            v = warp_max(v);
-            if (tid == 0) atomicMax(&ctl->amax[(p.stage + 1) % 3][0], (unsigned long long)__double_as_longlong(v));
-        }
-        if (p.stage == 2 && p.dt_fixed <= 0.0 && blockIdx.x == 0 && tid == 0) {
-            ctl->t = ctl->t + dt;
-            ctl->steps = ctl->steps + 1;
+        if (threadIdx.x == 0) {
+            T v = s_red[0];
+#pragma unroll
+            for (int w = 1; w < WPB; w++) v = fmax(v, s_red[w]);
+            const int so = (p.stage + 1) % 3;
+            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed);
         }
     }
 }
 
-// alpha of a 1D state into ctl->amax[slot][0]; grid-stride, one atomic per CTA.
+// ==========================================================================
+// FP32 stage kernel with paired splits.  The '+' split at cell j-3+t and the
+// '-' split at cell j+4-t share one float2 lane pair, P[t] = (q+_{j-3+t},
+// q-_{j+4-t}), t = 0..6.  With this mirror pairing the '-' window and the '-'
+// polynomial are element-wise aligned with the '+' ones, so the projection,
+// the smoothness measure and the polynomial run as packed f32x2 operations.
+// Cutoff codes of the six (split, field) groups sit in 5-bit slots of one
+// word (code bits 3..1 = d0, d1, d2; bits 4 and 0 receive the neighbours'
+// bits), so all six Delta_i come out of three whole-word bit operations and
+// index a Delta-addressed coefficient table directly.
+// ==========================================================================
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Cutoff codes of a '+' window (.x) and a '-' window (.y), w0..w4 in upwind
+// order.  beta is scaled by 12 (3 a^2 + 13 b^2) with eps12 = 12 eps, which
+// leaves gamma unchanged; chi_k is evaluated as x_k^6 / sum x^6 with
+// x = g / g_max in (0, 1] so that nothing overflows.  Returns the codes
+// d0<<2 | d1<<1 | d2 of both splits.
+__device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps12, float CT,
+                                        unsigned &cp, unsigned &cm) {
+    const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
+    const float2 s0b = __fadd2_rn(__ffma2_rn(f2(-2.f), w1, w0), w2);
+    const float2 s1a = __ffma2_rn(f2(-1.f), w3, w1);
+    const float2 s1b = __fadd2_rn(__ffma2_rn(f2(-2.f), w2, w1), w3);
+    const float2 s2a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w3, w4));
+    const float2 s2b = __fadd2_rn(__ffma2_rn(f2(-2.f), w3, w2), w4);
+    const float2 b0 = __ffma2_rn(f2(3.f), __fmul2_rn(s0a, s0a), __fmul2_rn(f2(13.f), __fmul2_rn(s0b, s0b)));
+    const float2 b1 = __ffma2_rn(f2(3.f), __fmul2_rn(s1a, s1a), __fmul2_rn(f2(13.f), __fmul2_rn(s1b, s1b)));
+    const float2 b2 = __ffma2_rn(f2(3.f), __fmul2_rn(s2a, s2a), __fmul2_rn(f2(13.f), __fmul2_rn(s2b, s2b)));
+    const float2 td = __ffma2_rn(f2(-1.f), b2, b0);
+    const float2 tau = make_float2(fabsf(td.x), fabsf(td.y));
+    const float2 d0 = __fadd2_rn(b0, f2(eps12)), d1 = __fadd2_rn(b1, f2(eps12)), d2 = __fadd2_rn(b2, f2(eps12));
+    const float2 g0 = __ffma2_rn(tau, make_float2(rcp_approx(d0.x), rcp_approx(d0.y)), f2(1.f));
+    const float2 g1 = __ffma2_rn(tau, make_float2(rcp_approx(d1.x), rcp_approx(d1.y)), f2(1.f));
+    const float2 g2 = __ffma2_rn(tau, make_float2(rcp_approx(d2.x), rcp_approx(d2.y)), f2(1.f));
+    const float2 rg = make_float2(rcp_approx(fmaxf(fmaxf(g0.x, g1.x), g2.x)), rcp_approx(fmaxf(fmaxf(g0.y, g1.y), g2.y)));
+    float2 x0 = __fmul2_rn(g0, rg), x1 = __fmul2_rn(g1, rg), x2 = __fmul2_rn(g2, rg);
+    x0 = __fmul2_rn(x0, x0);
+    x1 = __fmul2_rn(x1, x1);
+    x2 = __fmul2_rn(x2, x2);
+    const float2 y0 = __fmul2_rn(__fmul2_rn(x0, x0), x0);
+    const float2 y1 = __fmul2_rn(__fmul2_rn(x1, x1), x1);
+    const float2 y2 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
+    const float2 thr = __fmul2_rn(f2(CT), __fadd2_rn(__fadd2_rn(y0, y1), y2));
+    cp = ((y0.x < thr.x) ? 0u : 4u) | ((y1.x < thr.x) ? 0u : 2u) | ((y2.x < thr.x) ? 0u : 1u);
+    cm = ((y0.y < thr.y) ? 0u : 4u) | ((y1.y < thr.y) ? 0u : 2u) | ((y2.y < thr.y) ? 0u : 1u);
+}
+
+// FP32 max characteristic speed with approximate reciprocal and square root
+// (it only sets alpha and dt); flags as wavespeed1d.
+template <int SYS>
+__device__ __forceinline__ float wavespeed1d_fast(const float *Uc, float gm1, float gamma, float a, int *flag) {
+    if (SYS == SYS_ADV) return fabsf(a);
+    if (SYS == SYS_BURGERS) {
+        if (!isfinite(Uc[0])) *flag |= ERR_NONFINITE;
+        return fabsf(Uc[0]);
+    }
+    const float ri = rcp_approx(Uc[0]);
+    const float u = Uc[1] * ri;
+    const float p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
+    const float c2 = gamma * p * ri;
+    const float c = c2 * rsqrtf(c2);
+    if (!(Uc[0] > 0.f) || !(p > 0.f)) *flag |= ERR_NONPHYSICAL;
+    if (!isfinite(Uc[0] + Uc[1] + Uc[2])) *flag |= ERR_NONFINITE;
+    return fabsf(u) + c;
+}
+
+// Slot masks of the 6 x 5-bit word (see above).
+constexpr unsigned SLOT_HI = 0x21084210u;   // bit 4 of every slot
+constexpr unsigned SLOT_MID = 0x1CE739CEu;  // bits 3..1 of every slot
+constexpr unsigned SLOT_LO = 0x02108421u;   // bit 0 of every slot
+constexpr unsigned SLOT_PLUS = 0x00007FFFu; // slots 0..2 ('+' split)
+
+#ifndef T7_F32_MINB
+#define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
+#endif
+
+template <int SYS>
+__global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(const Stage1D p) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    __shared__ float s_U[WPB][M][WC];
+    __shared__ float s_gp[WPB][M][WC];
+    __shared__ float s_gm[WPB][M][WC];
+    __shared__ float s_pr[WPB][NP][WC];
+    __shared__ __align__(16) float s_cf[32][8];  // row Delta: Table co2 row of Table co3's choice
+    __shared__ float s_red[WPB];
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
+        int m = lut_select(row);
+        if (m == 15) m = 11;
+        s_cf[row][t] = t < 7 ? coef<float>(7 * m + t) : 0.f;
+    }
+    const float alpha = ctl->alpha_f[p.slot_in][0];
+    const float dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
+    const float gamma = p.f_gamma, gm1 = p.f_gm1, a = p.f_a;
+    const float eps12 = 12.f * p.f_eps, CT = p.f_CT;
+    const float idx = 1.f / p.f_dx;
+    const float *Us = static_cast<const float *>(p.Us);
+    const float *U0 = static_cast<const float *>(p.U0);
+    float *out = static_cast<float *>(p.out);
+    const int n = p.n;
+    const int ntiles = (n + WT - 1) / WT;
+    float (*sU)[WC] = s_U[warp];
+    float (*sgp)[WC] = s_gp[warp];
+    float (*sgm)[WC] = s_gm[warp];
+    float (*spr)[WC] = s_pr[warp];
+    float wsmax = 0.f;
+    // Software pipelining: the raw state of a warp tile's staged cells (lane
+    // and lane + 32) is loaded one tile ahead, and U^n of the tile's own cells
+    // at the start of the tile, so DRAM latency overlaps the face work.
+    float ua[M], ub[M];
+    auto load_tile = [&](int tile) {
+        const int c0 = tile * WT;
+        int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
+        if (ga < 0 || ga >= n) ga = ghost_map(ga, n, p.bc_lo, p.bc_hi);
+        if (gb < 0 || gb >= n) gb = ghost_map(gb, n, p.bc_lo, p.bc_hi);
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            ua[k] = Us[(size_t)k * n + ga];
+            ub[k] = (lane < WS - 32) ? Us[(size_t)k * n + gb] : 0.f;
+        }
+    };
+    int tile = blockIdx.x * WPB + warp;
+    if (tile < ntiles) load_tile(tile);
+    __syncthreads();
+
+    for (; tile < ntiles; tile += gridDim.x * WPB) {
+        const int c0 = tile * WT;
+        const int jc = c0 - 2 + lane;  // this lane's cell (if it updates one)
+        float u0r[M];
+        if (!p.rhs_mode && p.stage > 0) {
+            const int ic = jc < n ? jc : n - 1;
+#pragma unroll
+            for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * n + (ic < 0 ? 0 : ic)];
+        }
+        float Ucur[2][M];
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            Ucur[0][k] = ua[k];
+            Ucur[1][k] = ub[k];
+        }
+        if (tile + gridDim.x * WPB < ntiles) load_tile(tile + gridDim.x * WPB);
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int c = lane + 32 * r;
+            if (c >= WS) break;
+            float U[M], F[M];
+#pragma unroll
+            for (int k = 0; k < M; k++) U[k] = Ucur[r][k];
+            if (SYS == SYS_ADV) {
+                F[0] = a * U[0];
+            } else if (SYS == SYS_BURGERS) {
+                F[0] = 0.5f * U[0] * U[0];
+            } else {
+                const float ri = rcp_approx(U[0]);
+                const float u = U[1] * ri;
+                const float pr = gm1 * (U[2] - 0.5f * U[1] * u);
+                F[0] = U[1];
+                F[1] = U[1] * u + pr;
+                F[2] = u * (U[2] + pr);
+                spr[0][c] = u;
+                spr[NP > 1 ? 1 : 0][c] = (U[2] + pr) * ri;
+                spr[NP > 2 ? 2 : 0][c] = U[0] * rsqrtf(U[0]);
+            }
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                sU[k][c] = U[k];
+                sgp[k][c] = 0.5f * fmaf(alpha, U[k], F[k]);
+                sgm[k][c] = 0.5f * fmaf(-alpha, U[k], F[k]);
+            }
+        }
+        __syncwarp();
+
+        const int j = c0 - 2 + lane;
+        float2 L2[M][M];
+        float ut = 0.f, cc = 0.f, Ht = 0.f;
+        int flag = 0;
+        if (SYS == SYS_EULER1D) {
+            const float ul = spr[0][lane + 3], ur = spr[0][lane + 4];
+            const float Hl = spr[NP > 1 ? 1 : 0][lane + 3], Hr = spr[NP > 1 ? 1 : 0][lane + 4];
+            const float sl = spr[NP > 2 ? 2 : 0][lane + 3], sr = spr[NP > 2 ? 2 : 0][lane + 4];
+            const float w = rcp_approx(sl + sr);
+            ut = (sl * ul + sr * ur) * w;
+            Ht = (sl * Hl + sr * Hr) * w;
+            const float c2 = gm1 * (Ht - 0.5f * ut * ut);
+            const float rc = rsqrtf(c2);
+            cc = c2 * rc;
+            const float b1 = gm1 * (rc * rc);
+            const float b2 = 0.5f * ut * ut * b1;
+            const float uc = ut * rc;
+            L2[0][0] = f2(0.5f * (b2 + uc));
+            L2[0][1 % M] = f2(-0.5f * (b1 * ut + rc));
+            L2[0][2 % M] = f2(0.5f * b1);
+            L2[1 % M][0] = f2(1.f - b2);
+            L2[1 % M][1 % M] = f2(b1 * ut);
+            L2[1 % M][2 % M] = f2(-b1);
+            L2[2 % M][0] = f2(0.5f * (b2 - uc));
+            L2[2 % M][1 % M] = f2(-0.5f * (b1 * ut - rc));
+            L2[2 % M][2 % M] = f2(0.5f * b1);
+            if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+        }
+
+        float2 P[M][7];
+#pragma unroll
+        for (int t = 0; t < 7; t++) {
+            float2 g[M];
+#pragma unroll
+            for (int c = 0; c < M; c++) g[c] = make_float2(sgp[c][lane + t], sgm[c][lane + 7 - t]);
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                if (M == 1) {
+                    P[k][t] = g[0];
+                } else {
+                    float2 q = __fmul2_rn(L2[k][0], g[0]);
+#pragma unroll
+                    for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
+                    P[k][t] = q;
+                }
+            }
+        }
+        unsigned word = 0;
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            unsigned cp, cm;
+            cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps12, CT, cp, cm);
+            word |= (cp << (5 * k + 1)) | (cm << (5 * (3 + k) + 1));
+        }
+        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
+        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
+        const unsigned Dp = ((wl << 1) & SLOT_HI) | (word & SLOT_MID) | ((wr >> 1) & SLOT_LO);
+        const unsigned Dm = ((wr << 1) & SLOT_HI) | (word & SLOT_MID) | ((wl >> 1) & SLOT_LO);
+        const unsigned D = (Dp & SLOT_PLUS) | (Dm & ~SLOT_PLUS);
+        const bool face_out = lane >= 1 && lane <= 30;
+
+        float f[M];
+        constexpr unsigned ALL_SMOOTH = (M == 3) ? 0x3FFFFFFFu : ((31u) | (31u << 15));
+        if ((D & ALL_SMOOTH) == ALL_SMOOTH) {
+            // every split of every field selects f0 (the seventh-order polynomial)
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                float2 s = __fmul2_rn(f2(-1.f / 140.f), P[k][0]);
+                s = __ffma2_rn(f2(5.f / 84.f), P[k][1], s);
+                s = __ffma2_rn(f2(-101.f / 420.f), P[k][2], s);
+                s = __ffma2_rn(f2(319.f / 420.f), P[k][3], s);
+                s = __ffma2_rn(f2(107.f / 210.f), P[k][4], s);
+                s = __ffma2_rn(f2(-19.f / 210.f), P[k][5], s);
+                s = __ffma2_rn(f2(1.f / 105.f), P[k][6], s);
+                f[k] = s.x + s.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const float *cp = s_cf[(D >> (5 * k)) & 31u];
+                const float *cm = s_cf[(D >> (5 * (3 + k))) & 31u];
+                float2 s = __fmul2_rn(make_float2(cp[0], cm[0]), P[k][0]);
+#pragma unroll
+                for (int t = 1; t < 7; t++) s = __ffma2_rn(make_float2(cp[t], cm[t]), P[k][t], s);
+                f[k] = s.x + s.y;
+            }
+        }
+        if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= n - 1) {
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                p.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * k)) & 31u);
+                p.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * (3 + k))) & 31u);
+            }
+        }
+        float fh[M];
+        if (SYS == SYS_EULER1D) {
+            fh[0] = f[0] + f[1 % M] + f[2 % M];
+            fh[1 % M] = (ut - cc) * f[0] + ut * f[1 % M] + (ut + cc) * f[2 % M];
+            fh[2 % M] = (Ht - ut * cc) * f[0] + 0.5f * ut * ut * f[1 % M] + (Ht + ut * cc) * f[2 % M];
+        } else {
+            fh[0] = f[0];
+        }
+        if (flag && face_out && j >= -2 && j <= n) latch_error(ctl, flag, j);
+
+        float fprev[M];
+#pragma unroll
+        for (int k = 0; k < M; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
+        const int i = j;
+        if (lane >= 2 && lane <= 30 && i < n) {
+            float r[M];
+#pragma unroll
+            for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
+            if (p.rhs_mode) {
+#pragma unroll
+                for (int k = 0; k < M; k++) out[(size_t)k * n + i] = r[k];
+            } else {
+                float o[M];
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    const float v = fmaf(dtT, r[k], sU[k][lane + 3]);
+                    if (p.stage == 0) {
+                        o[k] = v;
+                    } else if (p.stage == 1) {
+                        o[k] = fmaf(0.75f, u0r[k], 0.25f * v);
+                    } else {
+                        // u0 + 2/3 (v - u0): float(1/3) + float(2/3) != 1 would
+                        // grow the solution by 6e-8 every step
+                        o[k] = fmaf(2.0f / 3.0f, v - u0r[k], u0r[k]);
+                    }
+                    out[(size_t)k * n + i] = o[k];
+                }
+                int wflag = 0;
+                wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(o, gm1, gamma, a, &wflag));
+                if (wflag) latch_error(ctl, wflag, i);
+            }
+        }
+        __syncwarp();
+    }
+
+    if (!p.rhs_mode) {
+        wsmax = warp_max(wsmax);
+        if (lane == 0) s_red[warp] = wsmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = s_red[0];
+#pragma unroll
+            for (int w = 1; w < WPB; w++) v = fmaxf(v, s_red[w]);
+            const int so = (p.stage + 1) % 3;
+            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed);
+        }
+    }
+}
+
+// alpha of a 1D state into ctl->amax[slot][0]; grid-stride, one atomic per CTA;
+// the last CTA converts it and plans the first RK step (see finish_launch).
 template <typename T, int SYS>
 __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
-    __shared__ double s_red[8];
+    __shared__ T s_red[8];
     const T *U = static_cast<const T *>(p.U);
     const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0), a = T(p.a);
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
-    double m = 0.0;
+    T m = T(0);
     int flag = 0, first = 0x7fffffff;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
         T Uc[M];
 #pragma unroll
         for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * p.n + i];
         int f = 0;
-        double w = (double)wavespeed1d<T, SYS>(Uc, gm1, gamma, a, &f);
+        const T w = wavespeed1d<T, SYS>(Uc, gm1, gamma, a, &f);
         if (f) {
             flag |= f;
             first = min(first, i);
@@ -478,14 +941,16 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
     m = warp_max(m);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < 8 ? s_red[threadIdx.x] : 0.0;
-        v = warp_max(v);
-        if (threadIdx.x == 0) atomicMax(&p.ctl->amax[p.slot][0], (unsigned long long)__double_as_longlong(v));
+    if (threadIdx.x == 0) {
+        T v = s_red[0];
+        for (int w = 1; w < 8; w++) v = fmax(v, s_red[w]);
+        atomicMax(&p.ctl->amax[p.slot][0], (unsigned long long)__double_as_longlong((double)v));
+        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true);
     }
 }
 
 // Scalar reconstruction of caller-padded values (t7_teno7_reconstruct).
+// Tiles of NT faces per CTA with the cutoff words exchanged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(NT) recon_kernel(const Recon p) {
     __shared__ T s_v[NCP];
@@ -495,7 +960,7 @@ __global__ void __launch_bounds__(NT) recon_kernel(const Recon p) {
     const int s = blockIdx.x * TILE;
     const T *v = static_cast<const T *>(p.v);
     const T eps = T(p.eps), CT = T(p.CT);
-    for (int q = tid; q < 91; q += NT) s_coef[q] = T(coef_f64(q));
+    for (int q = tid; q < 91; q += NT) s_coef[q] = coef<T>(q);
     for (int c = tid; c < NCELL; c += NT) {
         int l = s - HALO + c + 4;  // index into v (cell -4 is v[0])
         l = l < 0 ? 0 : (l > n + 7 ? n + 7 : l);
@@ -540,13 +1005,36 @@ __global__ void __launch_bounds__(NT) recon_kernel(const Recon p) {
 }
 
 // ---------------------------------------------------------------- launchers --
+inline int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
 template <typename T>
 cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
-    const int grid = (p.n + TILE - 1) / TILE;
+    const int ntiles = (p.n + WT - 1) / WT;
+    const int resident = num_sms() * (sizeof(T) == 4 ? T7_F32_MINB : 1) * 4;  // a few waves of resident CTAs
+    int grid = (ntiles + WPB - 1) / WPB;
+    if (grid > resident) grid = resident;
+    if constexpr (sizeof(T) == 4) {
+        switch (p.sys) {
+            case SYS_ADV: stage1d_f32_kernel<SYS_ADV><<<grid, WPB * 32, 0, st>>>(p); break;
+            case SYS_BURGERS: stage1d_f32_kernel<SYS_BURGERS><<<grid, WPB * 32, 0, st>>>(p); break;
+            case SYS_EULER1D: stage1d_f32_kernel<SYS_EULER1D><<<grid, WPB * 32, 0, st>>>(p); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (p.sys) {
-        case SYS_ADV: stage1d_kernel<T, SYS_ADV><<<grid, NT, 0, st>>>(p); break;
-        case SYS_BURGERS: stage1d_kernel<T, SYS_BURGERS><<<grid, NT, 0, st>>>(p); break;
-        case SYS_EULER1D: stage1d_kernel<T, SYS_EULER1D><<<grid, NT, 0, st>>>(p); break;
+        case SYS_ADV: stage1d_kernel<T, SYS_ADV><<<grid, WPB * 32, 0, st>>>(p); break;
+        case SYS_BURGERS: stage1d_kernel<T, SYS_BURGERS><<<grid, WPB * 32, 0, st>>>(p); break;
+        case SYS_EULER1D: stage1d_kernel<T, SYS_EULER1D><<<grid, WPB * 32, 0, st>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -555,7 +1043,7 @@ cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_alpha1d(const Alpha1D &p, cudaStream_t st) {
     int grid = (p.n + 255) / 256;
-    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid > num_sms() * 8) grid = num_sms() * 8;
     switch (p.sys) {
         case SYS_ADV: alpha1d_kernel<T, SYS_ADV><<<grid, 256, 0, st>>>(p); break;
         case SYS_BURGERS: alpha1d_kernel<T, SYS_BURGERS><<<grid, 256, 0, st>>>(p); break;
