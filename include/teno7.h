@@ -125,6 +125,29 @@ t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, 
 t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out);
 
+/* The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory -- plug-ins whose host application owns every device
+ * allocation, real-time loops that forbid allocation after start-up, and
+ * processes whose device memory is budgeted by an external allocator.
+ *
+ * One SSP-RK3 step of size dt of a 1D system (grid->sys advection, Burgers or
+ * 1D Euler), in place on the caller's device array U ([m][nx], grid->prec),
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).  It creates no
+ * context and allocates nothing: the two stage buffers and the control block
+ * live in one file-scope device array of T7_STATIC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Sizes whose scratch does not fit (2 x m x nx x element size plus
+ * 256 bytes, each buffer rounded up to 256 bytes) are rejected with T7_EINVAL
+ * before any GPU work.  The first call on each device looks up that device's
+ * address of the array (with the device current), so make that first call
+ * before any stream capture.  Every call reuses the array and clears the part
+ * that must start at zero; calls that overlap on the GPU (on different
+ * streams, or from several host threads) race on it.  Results equal
+ * t7_rk3_step's.  Synchronises the stream and returns any non-physical or
+ * non-finite state met.  errbuf (nullable) receives a message. */
+#define T7_STATIC_SCRATCH_BYTES (16u << 20)
+t7_status t7_rk3_step_static(const t7_grid *grid, void *U, double dt, void *stream, char *errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

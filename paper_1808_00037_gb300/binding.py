@@ -64,6 +64,7 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_rk3_step": ([vp, vp, d], i),
         "t7_run": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         "t7_run_host": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+        "t7_rk3_step_static": ([ctypes.POINTER(t7_grid), vp, d, vp, ctypes.c_char_p, ctypes.c_size_t], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -177,6 +178,15 @@ class Context:
         self._check(self.lib.t7_run_host(self.h, ptr, cfl, t_end, max_steps, ctypes.byref(steps), ctypes.byref(t)),
                     "t7_run_host")
         return steps.value, t.value
+
+    def rk3_step_static(self, U, dt: float):
+        """One RK3 step through t7_rk3_step_static (no allocation, static scratch)."""
+        buf = ctypes.create_string_buffer(256)
+        st = self.lib.t7_rk3_step_static(ctypes.byref(self.grid), _ptr(self._dev(U)), dt,
+                                         ctypes.c_void_p(self.stream.cuda_stream), buf, 256)
+        if st != T7_OK:
+            raise T7Error(st, f"t7_rk3_step_static: {buf.value.decode()}")
+        return U
 
     def sync(self):
         self._check(self.lib.t7_sync(self.h), "t7_sync")

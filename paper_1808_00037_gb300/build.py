@@ -23,6 +23,7 @@ UNITS = {
     "teno7_api.cu": [],
     "teno7_f64.cu": ["-fmad=false"],
     "teno7_f32.cu": [],
+    "teno7_static.cu": [],
 }
 
 
