@@ -39,13 +39,20 @@ TILES = 10486
 N1 = 1600
 CFL = 0.5
 GAMMA = 1.4
-# FP32 / FP64 lanes: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+# ALU peaks from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flop per FMA x 2.07 GHz; FP64 is GB300's nominal 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (nominal)
-# Floating-point operations per cell per stage launch of the fused Euler-1D
-# stage kernel, counted by ncu (fadd + fmul + 2 ffma, plus the double-precision
-# equivalents) on the tiled Shu-Osher workload: see profiles/.
-FLOPS_PER_CELL_STAGE = {"f32": None, "f64": None}
+FP64_PEAK_TFLOPS = 1.25
+# Algorithmic floating-point operations per cell per stage launch of the fused
+# 1D-Euler stage kernel (FMA = 2, add/mul/divide/rcp/sqrt/compare = 1), counted
+# from the kernel's arithmetic without the warp-tile redundancy:
+#   FP32: 31 per-cell staging + 751 per face + 26 update = 808
+#   FP64: 30 per-cell staging + 718 per face + 28 update = 776 (no FMA)
+FLOPS_PER_CELL_STAGE = {"f32": 808.0, "f64": 776.0}
+# DRAM bytes per stage launch per cell measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, averaged over the three stage launches of one RK3
+# step at N = 16,777,600) for the current kernels; None when not captured.
+TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.5, "f64": 61.9}
 
 
 def peaks():
@@ -235,14 +242,27 @@ def main():
         ms, clocks = time_run(torch, ctx, U, steps, dist, world, sampler_index=local if rank == 0 else None)
         s = 4 if name == "f32" else 8
         launches = 3 * steps
-        stage_ms = ms / launches  # the stage kernel is the only per-step launch
+        # the fused stage kernel is the only per-step launch (2 small launches
+        # per run set up the control block and alpha): its average duration is
+        # the timed region over the stage launches
+        stage_ms = ms / launches
         alg_bytes = 8 * 3 * s / 3 * n  # per stage launch, averaged over the three stages
         achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
+        flops = FLOPS_PER_CELL_STAGE[name] * n
+        tflops = flops / (stage_ms * 1e-3) / 1e12
+        peak_alu = FP32_PEAK_TFLOPS if name == "f32" else FP64_PEAK_TFLOPS
+        tr = TRAFFIC_PER_CELL_LAUNCH[name]
         res[name] = {
             "value": n * steps * world / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps, "steps": steps,
-            "clocks": clocks, "gpu_launches": launches + 2,
+            "clocks": clocks, "gpu_launches": launches + 2, "stage_launch_ms": stage_ms,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": tflops / peak_alu, "traffic": None if tr is None else tr * n,
+                         "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[name],
+                         "peak_kind": "derived from unit counts and max SM clock" if name == "f32"
+                         else "nominal GB300 FP64 rate"},
             "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                    "peak_kind": peak_kind, "bytes_per_cell_step": 8 * 3 * s},
+                    "peak_kind": peak_kind, "bytes_per_cell_step": 8 * 3 * s,
+                    "traffic": None if tr is None else tr * n},
         }
         # end-to-end through the host-array entry point: per step H2D + step + D2H
         if not args.no_e2e:
@@ -305,10 +325,8 @@ def main():
                                f"N={n} cells per GPU, zero-gradient ends, CFL 0.5, device-side dt",
                    "l2": "inputs larger than L2 (state 201 MB f32 / 403 MB f64 > 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": main_res["hbm"]["achieved"], "peak": hbm_peak, "unit": "GB/s",
-                     "frac": main_res["hbm"]["frac"], "traffic": None,
-                     "note": f"peak = {peak_kind} HBM copy bandwidth; achieved = 8 m s bytes per cell-step / "
-                             "average stage-launch time"},
+        "roofline": main_res["roofline"],
+        "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
         "f64": res["f64"], "accuracy": acc, "cpu_baseline": cpu,
