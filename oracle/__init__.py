@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
         _lib.or_run_2d.argtypes = [p, i, i, d, d, d, d, d, d, p, d, d, d, i, p, p]
         _lib.or_frame_1d.argtypes = [p, p, d, p, p]
         _lib.or_alpha_1d.argtypes = [i, p, i, d, d, p]
+        _lib.or_alpha_2d.argtypes = [p, i, i, d, p]
         _lib.or_frame_2d.argtypes = [p, p, d, i, p, p]
     return _lib
 
@@ -210,6 +211,16 @@ def rhs_2d(U, dx, dy, *, gamma=1.4, CT=1e-5, eps=(-1.0, -1.0),
         k = 8 * ny * (nx + 1)
         masks = (buf[:k].reshape(2, 4, ny, nx + 1), buf[k:].reshape(2, 4, nx, ny + 1))
     return out, (float(al[0]), float(al[1])), masks
+
+
+def alpha_2d(U, *, gamma=1.4):
+    """(max |u|+c, max |v|+c) over the cells of U[4, ny, nx]."""
+    U = _f64(U)
+    _, ny, nx = U.shape
+    out = np.zeros(2)
+    st = lib().or_alpha_2d(_ptr(U), nx, ny, gamma, _ptr(out))
+    _check(st, "alpha_2d", True)
+    return float(out[0]), float(out[1])
 
 
 def cfl_dt_2d(U, dx, dy, cfl, *, gamma=1.4):

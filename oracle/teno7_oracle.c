@@ -743,3 +743,13 @@ int or_alpha_1d(int sys, const double *U, int n, double gamma, double a, double 
     if (bad & 1) return OR_ENONPHYSICAL;
     return OR_OK;
 }
+
+/* Global Lax-Friedrichs alphas (x, y) of a 2D state (exported for sampled checks). */
+int or_alpha_2d(const double *U, int nx, int ny, double gamma, double *alpha_out) {
+    sysdef S = {SYS_EULER2D, 4, gamma, 0.0};
+    int bad = 0;
+    alpha_2d(&S, U, nx, ny, &alpha_out[0], &alpha_out[1], &bad);
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
+}

@@ -140,11 +140,22 @@ class Context:
         return fhat, d3, D5
 
     def euler_rhs(self, U, want_masks: bool = False, out=None):
+        """L(U).  masks: 1D [2, m, nx+1]; 2D a pair (x faces [2, 4, ny, nx+1],
+        y faces [2, 4, nx, ny+1])."""
         torch = self._torch
         U = self._dev(U)
         out = torch.empty_like(U) if out is None else self._dev(out)
-        masks = torch.empty((2, self.m, self.nx + 1), dtype=torch.uint8, device=U.device) if want_masks else None
+        masks = None
+        if want_masks:
+            if self.sys == T7_EULER2D:
+                nx, ny = self.nx, self.ny
+                masks = torch.empty(8 * ny * (nx + 1) + 8 * nx * (ny + 1), dtype=torch.uint8, device=U.device)
+            else:
+                masks = torch.empty((2, self.m, self.nx + 1), dtype=torch.uint8, device=U.device)
         self._check(self.lib.t7_euler_rhs(self.h, _ptr(U), _ptr(out), _ptr(masks)), "t7_euler_rhs")
+        if want_masks and self.sys == T7_EULER2D:
+            k = 8 * self.ny * (self.nx + 1)
+            masks = (masks[:k].view(2, 4, self.ny, self.nx + 1), masks[k:].view(2, 4, self.nx, self.ny + 1))
         return out, masks
 
     def cfl_dt(self, U, cfl: float) -> float:

@@ -21,6 +21,7 @@ struct t7_ctx {
     cudaStream_t stream;
     int device;
     void *U1, *U2;         // RK stage buffers
+    void *R;               // 2D: x part of L(U)
     void *Uhost;           // device state for the host-array entry point
     t7::DevCtl *ctl;       // device control block
     t7::DevCtl *ctl_host;  // pinned mirror for status reads
@@ -49,13 +50,14 @@ bool is_1d(int sys) { return sys == T7_SCALAR_ADVECTION || sys == T7_EULER1D || 
 
 double eps_of(double eps, double d) { return eps < 0.0 ? d * d * d : eps; }
 
-__global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, double dx, int max_steps) {
+__global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, double dx, double dy, int max_steps) {
     for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = 0ull;
     ctl->t = 0.0;
     ctl->dt = 0.0;
     ctl->t_end = t_end;
     ctl->cfl = cfl;
     ctl->dx = dx;
+    ctl->dy = dy;
     ctl->steps = 0;
     ctl->max_steps = max_steps;
     ctl->active = 1;
@@ -91,10 +93,49 @@ cudaError_t stage(t7_ctx *c, const t7::Stage1D &p) {
     return c->g.prec == T7_F64 ? t7::launch_stage1d_f64(p, c->stream) : t7::launch_stage1d_f32(p, c->stream);
 }
 
-// alpha(U) into slot 0 after clearing all slots
-cudaError_t alpha_init(t7_ctx *c, const void *U) {
-    cudaError_t e = cudaMemsetAsync(c->ctl->amax, 0, sizeof(c->ctl->amax), c->stream);
-    if (e != cudaSuccess) return e;
+t7::Stage2D stage2d_params(t7_ctx *c, const void *Us, const void *U0, void *out, void *R) {
+    t7::Stage2D p;
+    memset(&p, 0, sizeof(p));
+    p.Us = Us;
+    p.U0 = U0;
+    p.out = out;
+    p.R = R;
+    p.nx = c->g.nx;
+    p.ny = c->g.ny;
+    for (int b = 0; b < 4; b++) p.bc[b] = c->g.bc[b];
+    p.dx = c->g.dx;
+    p.dy = c->g.dy;
+    p.eps_x = eps_of(c->g.eps_x, c->g.dx);
+    p.eps_y = eps_of(c->g.eps_y, c->g.dy);
+    p.CT = c->g.CT;
+    p.gamma = c->g.gamma;
+    p.ctl = c->ctl;
+    p.f_dx = (float)p.dx;
+    p.f_dy = (float)p.dy;
+    p.f_eps_x = (float)p.eps_x;
+    p.f_eps_y = (float)p.eps_y;
+    p.f_CT = (float)p.CT;
+    p.f_gamma = (float)p.gamma;
+    p.f_gm1 = (float)(p.gamma - 1.0);
+    return p;
+}
+
+cudaError_t stage2d(t7_ctx *c, const t7::Stage2D &p) {
+    return c->g.prec == T7_F64 ? t7::launch_stage2d_f64(p, c->stream) : t7::launch_stage2d_f32(p, c->stream);
+}
+
+// alpha(U) (per direction in 2D) into slot 0, no slot cleared
+cudaError_t alpha_launch(t7_ctx *c, const void *U) {
+    if (c->g.sys == T7_EULER2D) {
+        t7::Alpha2D a;
+        a.U = U;
+        a.nx = c->g.nx;
+        a.ny = c->g.ny;
+        a.gamma = c->g.gamma;
+        a.ctl = c->ctl;
+        a.slot = 0;
+        return c->g.prec == T7_F64 ? t7::launch_alpha2d_f64(a, c->stream) : t7::launch_alpha2d_f32(a, c->stream);
+    }
     t7::Alpha1D a;
     a.U = U;
     a.n = c->g.nx;
@@ -106,10 +147,31 @@ cudaError_t alpha_init(t7_ctx *c, const void *U) {
     return c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
 }
 
+// alpha(U) into slot 0 after clearing all slots
+cudaError_t alpha_init(t7_ctx *c, const void *U) {
+    cudaError_t e = cudaMemsetAsync(c->ctl->amax, 0, sizeof(c->ctl->amax), c->stream);
+    if (e != cudaSuccess) return e;
+    return alpha_launch(c, U);
+}
+
+
 // three stage launches; dt_fixed > 0 fixes the step, otherwise CFL on device
 cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed) {
     void *bufs_in[3] = {U, c->U1, c->U2};
     void *bufs_out[3] = {c->U1, c->U2, U};
+    if (c->g.sys == T7_EULER2D) {
+        for (int k = 0; k < 3; k++) {
+            t7::Stage2D p = stage2d_params(c, bufs_in[k], k == 0 ? nullptr : U, bufs_out[k], c->R);
+            p.rhs_mode = 0;
+            p.stage = k;
+            p.dt_fixed = dt_fixed;
+            p.f_dt_fixed = (float)dt_fixed;
+            p.slot_in = k;
+            cudaError_t e = stage2d(c, p);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int k = 0; k < 3; k++) {
         t7::Stage1D p = stage_params(c, bufs_in[k], k == 0 ? nullptr : U, bufs_out[k]);
         p.rhs_mode = 0;
@@ -145,11 +207,17 @@ t7_status check_1d(t7_ctx *c) {
     return T7_OK;
 }
 
+t7_status check_sys(t7_ctx *c) {
+    if (!c) return T7_EINVAL;
+    return T7_OK;
+}
+
 }  // namespace
 
 namespace t7 {
-cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, int max_steps, cudaStream_t s) {
-    ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, t_end, cfl, dx, max_steps);
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, double dy, int max_steps,
+                             cudaStream_t s) {
+    ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, t_end, cfl, dx, dy, max_steps);
     return cudaGetLastError();
 }
 }  // namespace t7
@@ -181,6 +249,7 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     cudaError_t e;
     if ((e = cudaMalloc(&c->U1, bytes)) != cudaSuccess || (e = cudaMalloc(&c->U2, bytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->Uhost, bytes)) != cudaSuccess ||
+        (g->sys == T7_EULER2D && (e = cudaMalloc(&c->R, bytes)) != cudaSuccess) ||
         (e = cudaMalloc((void **)&c->ctl, sizeof(t7::DevCtl))) != cudaSuccess ||
         (e = cudaMallocHost((void **)&c->ctl_host, sizeof(t7::DevCtl))) != cudaSuccess) {
         t7_destroy(c);
@@ -205,6 +274,7 @@ t7_status t7_destroy(t7_ctx *c) {
     if (c->U1) cudaFree(c->U1);
     if (c->U2) cudaFree(c->U2);
     if (c->Uhost) cudaFree(c->Uhost);
+    if (c->R) cudaFree(c->R);
     if (c->ctl) cudaFree(c->ctl);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
     delete c;
@@ -247,11 +317,20 @@ t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double
 }
 
 t7_status t7_euler_rhs(t7_ctx *c, const void *U, void *dUdt, uint8_t *masks) {
-    t7_status st = check_1d(c);
+    t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !dUdt) return fail(c, T7_EINVAL, "t7_euler_rhs: null array");
     cudaError_t e = alpha_init(c, U);
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
+    if (c->g.sys == T7_EULER2D) {
+        t7::Stage2D p = stage2d_params(c, U, nullptr, dUdt, dUdt);
+        p.rhs_mode = 1;
+        p.masks = masks;
+        p.slot_in = 0;
+        e = stage2d(c, p);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rhs launch");
+        return T7_OK;
+    }
     t7::Stage1D p = stage_params(c, U, nullptr, dUdt);
     p.rhs_mode = 1;
     p.masks = masks;
@@ -262,22 +341,26 @@ t7_status t7_euler_rhs(t7_ctx *c, const void *U, void *dUdt, uint8_t *masks) {
 }
 
 t7_status t7_cfl_dt(t7_ctx *c, const void *U, double cfl, double *dt_out) {
-    t7_status st = check_1d(c);
+    t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !dt_out || !(cfl > 0.0)) return fail(c, T7_EINVAL, "t7_cfl_dt: bad argument");
     cudaError_t e = alpha_init(c, U);
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
     if ((st = collect(c))) return st;
-    double alpha = 0.0;
-    unsigned long long bits = c->ctl_host->amax[0][0];
+    double alpha = 0.0, alpha_y = 0.0;
+    unsigned long long bits = c->ctl_host->amax[0][0], bits_y = c->ctl_host->amax[0][1];
     memcpy(&alpha, &bits, sizeof(alpha));
-    *dt_out = (cfl * c->g.dx) / alpha;
+    memcpy(&alpha_y, &bits_y, sizeof(alpha_y));
+    if (c->g.sys == T7_EULER2D)
+        *dt_out = cfl / (alpha / c->g.dx + alpha_y / c->g.dy);
+    else
+        *dt_out = (cfl * c->g.dx) / alpha;
     return T7_OK;
 }
 
 t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
-    t7_status st = check_1d(c);
+    t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step: bad argument");
     cudaError_t e = alpha_init(c, U);
@@ -287,20 +370,12 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
 }
 
 t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out) {
-    t7_status st = check_1d(c);
+    t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
-    cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, c->g.dx, max_steps, c->stream);
+    cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, c->g.dx, c->g.dy, max_steps, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ctl");
-    t7::Alpha1D a;
-    a.U = U;
-    a.n = c->g.nx;
-    a.sys = c->g.sys;
-    a.gamma = c->g.gamma;
-    a.a = c->g.adv_speed;
-    a.ctl = c->ctl;
-    a.slot = 0;
-    e = c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+    e = alpha_launch(c, U);
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
     // Steps are launched in chunks; between chunks the host polls whether the
     // device-side clock has reached t_end (a step past it is a no-op anyway).
@@ -328,7 +403,7 @@ t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, in
 
 t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out) {
-    t7_status st = check_1d(c);
+    t7_status st = check_sys(c);
     if (st) return st;
     if (!U_host) return fail(c, T7_EINVAL, "t7_run_host: null array");
     size_t bytes = c->ncell * c->m * c->esize;

@@ -1,8 +1,11 @@
 // FP32 instantiation of the TENO7-ext kernels (FMA contraction on).
 #include "teno7_kernels.cuh"
+#include "teno7_kernels2d.cuh"
 
 namespace t7 {
 cudaError_t launch_stage1d_f32(const Stage1D &p, cudaStream_t s) { return launch_stage1d<float>(p, s); }
 cudaError_t launch_alpha1d_f32(const Alpha1D &p, cudaStream_t s) { return launch_alpha1d<float>(p, s); }
 cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s) { return launch_recon<float>(p, s); }
+cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s) { return launch_stage2d<float>(p, s); }
+cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s) { return launch_alpha2d<float>(p, s); }
 }  // namespace t7

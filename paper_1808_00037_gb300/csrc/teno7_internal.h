@@ -20,7 +20,7 @@ enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4 };
 // t and computes the next CFL step, so that no CTA ever divides in FP64.
 struct DevCtl {
     unsigned long long amax[3][2];
-    double t, dt, t_end, cfl, dx;
+    double t, dt, t_end, cfl, dx, dy;
     float alpha_f[3][2];
     float dt_f, pad_f;
     int steps, max_steps, active, err;
@@ -53,6 +53,37 @@ struct Alpha1D {
     int slot;
 };
 
+// One stage of the 2D Euler system, dimension by dimension: the x sweep
+// writes Lx(U) into R, the y sweep adds Ly(U) and applies the RK stage.
+struct Stage2D {
+    const void *Us;  // stage input [4][ny][nx]
+    const void *U0;  // U^n (stages 1 and 2)
+    void *out;       // RK mode: stage output; RHS mode: dU/dt (== R)
+    void *R;         // x part of L(U), [4][ny][nx]
+    uint8_t *masks;  // RHS mode, nullable: x faces [2][4][ny][nx+1], then y faces [2][4][nx][ny+1]
+    int nx, ny;
+    int bc[4];
+    double dx, dy, eps_x, eps_y, CT, gamma;
+    int rhs_mode, stage;
+    double dt_fixed;
+    DevCtl *ctl;
+    int slot_in;
+    float f_dx, f_dy, f_eps_x, f_eps_y, f_CT, f_gamma, f_gm1, f_dt_fixed;
+};
+
+struct Alpha2D {
+    const void *U;
+    int nx, ny;
+    double gamma;
+    DevCtl *ctl;
+    int slot;
+};
+
+cudaError_t launch_stage2d_f64(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_alpha2d_f64(const Alpha2D &p, cudaStream_t s);
+cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s);
+
 // Finalization done by the last CTA of a launch (see DevCtl).
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_STEP = 2 };
 
@@ -73,6 +104,7 @@ cudaError_t launch_recon_f64(const Recon &p, cudaStream_t s);
 cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s);
 
 // Control-block helpers (teno7_api.cu).
-cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, int max_steps, cudaStream_t s);
+cudaError_t launch_ctl_begin(DevCtl *ctl, double t_end, double cfl, double dx, double dy, int max_steps,
+                             cudaStream_t s);
 
 }  // namespace t7

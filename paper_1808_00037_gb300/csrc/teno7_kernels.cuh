@@ -266,14 +266,17 @@ __device__ __forceinline__ T poly_f0(T v0, T v1, T v2, T v3, T v4, T v5, T v6) {
 //                alpha(U^n) = amax[slot_out] (oracle's expression order)
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zero_slot, bool end_of_step,
-                                              bool plan_step) {
+                                              bool plan_step, bool two_d = false) {
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
-    if (prev != gridDim.x - 1) return;
+    if (prev != gridDim.x * gridDim.y - 1) return;
     __threadfence();
     const double a = __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][0], 0ull));
+    const double ay = two_d ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][1], 0ull)) : 0.0;
     ctl->alpha_f[slot_out][0] = (float)a;
+    ctl->alpha_f[slot_out][1] = (float)ay;
     ctl->amax[zero_slot][0] = 0ull;
+    ctl->amax[zero_slot][1] = 0ull;
     if (end_of_step) {
         ctl->t = ctl->t + ctl->dt;
         ctl->steps = ctl->steps + 1;
@@ -281,7 +284,8 @@ __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zer
     if (plan_step) {
         const double t = ctl->t, t_end = ctl->t_end;
         const int active = (ctl->steps < ctl->max_steps) && (t < t_end);
-        double dt = (ctl->cfl * ctl->dx) / a;
+        // CFL step in the oracle's expression order: 1D cfl dx / a, 2D cfl / (ax/dx + ay/dy)
+        double dt = two_d ? ctl->cfl / (a / ctl->dx + ay / ctl->dy) : (ctl->cfl * ctl->dx) / a;
         if (t + dt > t_end) dt = t_end - t;
         ctl->active = active;
         ctl->dt = dt;
