@@ -171,6 +171,41 @@ def cpu_baseline(budget_s=15.0):
             "sample": f"{steps} RK3 steps of the Shu-Osher profile tiled x4 (N={n}), single-threaded C oracle"}
 
 
+def bench_2d(args, torch, B, dist, world, rank):
+    """2D Euler, four-quadrant Riemann data on [0,1]^2 at 2048^2 (seed 2024),
+    transmissive boundaries, CFL 0.4: Gcell-steps/s in FP32 and FP64."""
+    n = 2048
+    U0, dx, dy, _ = I.quadrants_2d(2024, n, n)
+    out = {"workload": "four-quadrant Riemann data, 2048x2048 on [0,1]^2, transmissive, CFL 0.4"}
+    for name, prec, dtype, steps in (("f32", B.T7_F32, torch.float32, args.steps_2d),
+                                     ("f64", B.T7_F64, torch.float64, args.f64_steps_2d)):
+        ctx = B.Context(B.T7_EULER2D, n, dx, ny=n, dy=dy, prec=prec, bc=(1, 1, 1, 1), gamma=GAMMA)
+        U = torch.tensor(U0, dtype=dtype, device="cuda")
+        ctx.run(U, 0.4, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(ctx.stream)
+        done, _ = ctx.run(U, 0.4, max_steps=steps)
+        end.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        assert done == steps
+        out[name] = {"value": n * n * steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s",
+                     "ms_per_step": ms / steps, "steps": steps, "gpu_launches": 6 * steps + 2}
+        ctx.close()
+        del U
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -209,7 +244,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--only", choices=["f32", "f64"], default=None, help="time one precision (profiling)")
+    ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--steps-2d", type=int, default=20)
+    ap.add_argument("--f64-steps-2d", type=int, default=3)
+    ap.add_argument("--only", choices=["f32", "f64", "2d"], default=None,
+                    help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
@@ -227,6 +266,11 @@ def main():
         dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
         dist = dist_mod
 
+    if args.only == "2d":
+        r2 = bench_2d(args, torch, B, dist, world, rank)
+        if rank == 0:
+            print(json.dumps({"only": "2d", **r2}), flush=True)
+        return 0
     U0, dx = I.shu_osher(N1, tiles=args.tiles)
     n = U0.shape[1]
     hbm_peak, peak_kind = peaks()
@@ -291,6 +335,7 @@ def main():
         if rank == 0:
             print(json.dumps({"only": args.only, **res[args.only]}), flush=True)
         return 0
+    res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
     acc = {}
     Ua, dxa = I.shu_osher(N1)
@@ -329,7 +374,7 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "accuracy": acc, "cpu_baseline": cpu,
+        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -125,6 +125,34 @@ t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, 
 t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out);
 
+/* Ragged batch of independent 1D Euler problems (shock tubes) of uneven
+ * length, each advanced by its own SSP-RK3 loop with its own CFL step
+ * dt = CFL dx_t / alpha_t(U^n) to t_end (or max_steps), all in ONE persistent
+ * launch: groups of `group_warps` warps take tubes from a device work queue,
+ * costliest (longest) first, so no host round trip happens per step.  The
+ * scheme inside each tube is exactly t7_run's (Eq. app, the TENO7-ext
+ * reconstruction, Remark 3, SSP-RK3).
+ *   ctx          created with sys = T7_EULER1D, nx = total cells, bc[0..1]
+ *                applied at both ends of every tube
+ *   U            device, [3][nx] (variable-major over the concatenation),
+ *                advanced in place
+ *   offsets      host, ntubes + 1 ascending, offsets[0] = 0, offsets[ntubes] = nx
+ *   dx           host, per-tube cell width (epsilon = dx^3 per tube)
+ *   group_warps  1, 2, 4 or 8 warps per tube; 0 = the value chosen by
+ *                t7_batch_autotune (8 if never tuned)
+ *   steps_out, t_out  host or NULL, per tube
+ * Synchronises.  Returns non-physical / non-finite states met in any tube. */
+t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const double *dx, int ntubes, double t_end,
+                       double cfl, int max_steps, int group_warps, int *steps_out, double *t_out);
+
+/* Autotuner of the batch tile shape: times trial_steps steps of every tube
+ * for group_warps = 1, 2, 4, 8 on a device copy of U (U is not modified),
+ * keeps the fastest in the context for later t7_batch_run calls, and returns
+ * it in *group_out (nullable); ms_out (nullable, 4 floats) receives the trial
+ * times.  Synchronises. */
+t7_status t7_batch_autotune(t7_ctx *ctx, const void *U, const int64_t *offsets, const double *dx, int ntubes,
+                            double cfl, int trial_steps, int *group_out, float *ms_out);
+
 /* The paper has no counterpart to this call: it serves callers that cannot
  * allocate device memory -- plug-ins whose host application owns every device
  * allocation, real-time loops that forbid allocation after start-up, and

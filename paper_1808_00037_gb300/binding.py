@@ -65,6 +65,8 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_run": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         "t7_run_host": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         "t7_rk3_step_static": ([ctypes.POINTER(t7_grid), vp, d, vp, ctypes.c_char_p, ctypes.c_size_t], i),
+        "t7_batch_run": ([vp, vp, vp, vp, i, d, d, i, i, vp, vp], i),
+        "t7_batch_autotune": ([vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), vp], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -198,6 +200,33 @@ class Context:
         if st != T7_OK:
             raise T7Error(st, f"t7_rk3_step_static: {buf.value.decode()}")
         return U
+
+    # ------------------------------------------------------- ragged batch --
+    def batch_run(self, U, offsets, dx, t_end: float, cfl: float, max_steps: int = 2**31 - 1,
+                  group_warps: int = 0):
+        """Advance every tube of the concatenated batch U ([3][sum n]) to t_end in
+        one persistent launch.  Returns (steps[ntubes], t[ntubes])."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        dxa = np.ascontiguousarray(dx, dtype=np.float64)
+        nt = off.size - 1
+        steps = np.zeros(nt, np.int32)
+        t = np.zeros(nt, np.float64)
+        self._check(self.lib.t7_batch_run(self.h, _ptr(self._dev(U)), off.ctypes.data, dxa.ctypes.data, nt, t_end,
+                                          cfl, max_steps, group_warps, steps.ctypes.data, t.ctypes.data),
+                    "t7_batch_run")
+        return steps, t
+
+    def batch_autotune(self, U, offsets, dx, cfl: float, trial_steps: int = 3):
+        """Pick group_warps (warps per tube) by timing trial steps; U is not modified.
+        Returns (group_warps, trial milliseconds for 1, 2, 4, 8)."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        dxa = np.ascontiguousarray(dx, dtype=np.float64)
+        g = ctypes.c_int()
+        ms = np.zeros(4, np.float32)
+        self._check(self.lib.t7_batch_autotune(self.h, _ptr(self._dev(U)), off.ctypes.data, dxa.ctypes.data,
+                                               off.size - 1, cfl, trial_steps, ctypes.byref(g), ms.ctypes.data),
+                    "t7_batch_autotune")
+        return g.value, ms
 
     def sync(self):
         self._check(self.lib.t7_sync(self.h), "t7_sync")

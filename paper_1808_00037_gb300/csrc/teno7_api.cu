@@ -8,7 +8,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <numeric>
+#include <vector>
 
 #include "teno7.h"
 #include "teno7_internal.h"
@@ -24,6 +27,12 @@ struct t7_ctx {
     void *R;               // 2D: x part of L(U)
     void *Uhost;           // device state for the host-array entry point
     t7::DevCtl *ctl;       // device control block
+    // ragged-batch metadata (device), grown on demand
+    long long *b_off;
+    double *b_dx, *b_t;
+    int *b_order, *b_steps, *b_queue;
+    int b_cap;
+    int b_group;           // warps per tube chosen by t7_batch_autotune (0: not tuned)
     t7::DevCtl *ctl_host;  // pinned mirror for status reads
     char err[512];
 };
@@ -275,6 +284,12 @@ t7_status t7_destroy(t7_ctx *c) {
     if (c->U2) cudaFree(c->U2);
     if (c->Uhost) cudaFree(c->Uhost);
     if (c->R) cudaFree(c->R);
+    if (c->b_off) cudaFree(c->b_off);
+    if (c->b_dx) cudaFree(c->b_dx);
+    if (c->b_t) cudaFree(c->b_t);
+    if (c->b_order) cudaFree(c->b_order);
+    if (c->b_steps) cudaFree(c->b_steps);
+    if (c->b_queue) cudaFree(c->b_queue);
     if (c->ctl) cudaFree(c->ctl);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
     delete c;
@@ -415,6 +430,149 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
     if (e != cudaSuccess) return cuda_fail(c, e, "D2H copy");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
     return st;
+}
+
+// ---------------------------------------------------------------- batch ----
+static t7_status batch_prepare(t7_ctx *c, const int64_t *offsets, const double *dx, int ntubes) {
+    if (ntubes > c->b_cap) {
+        cudaFree(c->b_off);
+        cudaFree(c->b_dx);
+        cudaFree(c->b_t);
+        cudaFree(c->b_order);
+        cudaFree(c->b_steps);
+        cudaFree(c->b_queue);
+        c->b_off = nullptr;
+        c->b_dx = c->b_t = nullptr;
+        c->b_order = c->b_steps = c->b_queue = nullptr;
+        c->b_cap = 0;
+        if (cudaMalloc((void **)&c->b_off, sizeof(long long) * (ntubes + 1)) != cudaSuccess ||
+            cudaMalloc((void **)&c->b_dx, sizeof(double) * ntubes) != cudaSuccess ||
+            cudaMalloc((void **)&c->b_t, sizeof(double) * ntubes) != cudaSuccess ||
+            cudaMalloc((void **)&c->b_order, sizeof(int) * ntubes) != cudaSuccess ||
+            cudaMalloc((void **)&c->b_steps, sizeof(int) * ntubes) != cudaSuccess ||
+            cudaMalloc((void **)&c->b_queue, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, T7_ENOMEM, "batch metadata allocation failed");
+        }
+        c->b_cap = ntubes;
+    }
+    // costliest first: work ~ cells x steps ~ n^2 for comparable wave speeds
+    std::vector<int> order(ntubes);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double na = (double)(offsets[a + 1] - offsets[a]), nb = (double)(offsets[b + 1] - offsets[b]);
+        return na * na > nb * nb;
+    });
+    std::vector<long long> off(offsets, offsets + ntubes + 1);
+    cudaError_t e;
+    if ((e = cudaMemcpy(c->b_off, off.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(c->b_dx, dx, sizeof(double) * ntubes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->b_order, order.data(), sizeof(int) * ntubes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "batch metadata copy");
+    return T7_OK;
+}
+
+static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, double cfl, int max_steps,
+                                int group) {
+    cudaError_t e = cudaMemsetAsync(c->b_queue, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    t7::Batch1D p;
+    memset(&p, 0, sizeof(p));
+    p.U = U;
+    p.W1 = c->U1;
+    p.W2 = c->U2;
+    p.offsets = c->b_off;
+    p.dx = c->b_dx;
+    p.order = c->b_order;
+    p.ntubes = ntubes;
+    p.Ntot = c->g.nx;
+    p.bc_lo = c->g.bc[0];
+    p.bc_hi = c->g.bc[1];
+    p.t_end = t_end;
+    p.cfl = cfl;
+    p.gamma = c->g.gamma;
+    p.CT = c->g.CT;
+    p.max_steps = max_steps;
+    p.group_warps = group;
+    p.queue = c->b_queue;
+    p.steps_out = c->b_steps;
+    p.t_out = c->b_t;
+    p.ctl = c->ctl;
+    return c->g.prec == T7_F64 ? t7::launch_batch1d_f64(p, c->stream) : t7::launch_batch1d_f32(p, c->stream);
+}
+
+static t7_status batch_check(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes) {
+    if (!c) return T7_EINVAL;
+    if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "batches take a 1D Euler context");
+    if (!U || !offsets || !dx || ntubes < 1) return fail(c, T7_EINVAL, "batch: bad argument");
+    if (offsets[0] != 0 || offsets[ntubes] != (int64_t)c->g.nx)
+        return fail(c, T7_EINVAL, "batch: offsets must run from 0 to the context's nx (%d)", c->g.nx);
+    for (int t = 0; t < ntubes; t++) {
+        if (offsets[t + 1] - offsets[t] < 1) return fail(c, T7_EINVAL, "batch: tube %d is empty", t);
+        if (!(dx[t] > 0.0)) return fail(c, T7_EINVAL, "batch: dx of tube %d is not positive", t);
+    }
+    return T7_OK;
+}
+
+t7_status t7_batch_run(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes, double t_end,
+                       double cfl, int max_steps, int group_warps, int *steps_out, double *t_out) {
+    t7_status st = batch_check(c, U, offsets, dx, ntubes);
+    if (st) return st;
+    if (!(cfl > 0.0) || !(t_end >= 0.0) || max_steps < 0) return fail(c, T7_EINVAL, "t7_batch_run: bad argument");
+    int group = group_warps > 0 ? group_warps : (c->b_group > 0 ? c->b_group : 8);
+    if (group != 1 && group != 2 && group != 4 && group != 8)
+        return fail(c, T7_EINVAL, "t7_batch_run: group_warps must be 1, 2, 4 or 8");
+    if ((st = batch_prepare(c, offsets, dx, ntubes))) return st;
+    cudaError_t e = batch_launch(c, U, ntubes, t_end, cfl, max_steps, group);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch launch");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    if (steps_out && (e = cudaMemcpy(steps_out, c->b_steps, sizeof(int) * ntubes, cudaMemcpyDeviceToHost)) !=
+                         cudaSuccess)
+        return cuda_fail(c, e, "steps copy");
+    if (t_out && (e = cudaMemcpy(t_out, c->b_t, sizeof(double) * ntubes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "t copy");
+    return collect(c);
+}
+
+t7_status t7_batch_autotune(t7_ctx *c, const void *U, const int64_t *offsets, const double *dx, int ntubes,
+                            double cfl, int trial_steps, int *group_out, float *ms_out) {
+    t7_status st = batch_check(c, (void *)U, offsets, dx, ntubes);
+    if (st) return st;
+    if (!(cfl > 0.0) || trial_steps < 1) return fail(c, T7_EINVAL, "t7_batch_autotune: bad argument");
+    if ((st = batch_prepare(c, offsets, dx, ntubes))) return st;
+    const size_t bytes = c->ncell * c->m * c->esize;
+    const int groups[4] = {1, 2, 4, 8};
+    float best = 0.f;
+    int best_g = 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int gi = 0; gi < 4; gi++) {
+        // every candidate advances the same copy of the state by trial_steps steps
+        cudaError_t e = cudaMemcpyAsync(c->Uhost, U, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = batch_launch(c, c->Uhost, ntubes, INFINITY, cfl, trial_steps, groups[gi]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(c, e, "autotune trial");
+        }
+        if (ms_out) ms_out[gi] = ms;
+        if (gi == 0 || ms < best) {
+            best = ms;
+            best_g = groups[gi];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->b_group = best_g;
+    if (group_out) *group_out = best_g;
+    return collect(c);
 }
 
 }  // extern "C"

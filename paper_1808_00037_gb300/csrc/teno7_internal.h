@@ -84,6 +84,30 @@ cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s);
 cudaError_t launch_alpha2d_f64(const Alpha2D &p, cudaStream_t s);
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s);
 
+// A ragged batch of independent 1D Euler tubes, concatenated variable-major
+// ([3][Ntot]); each tube runs its own SSP-RK3 loop to t_end inside one
+// persistent launch.
+struct Batch1D {
+    void *U;                   // state, advanced in place
+    void *W1, *W2;             // stage buffers, same layout
+    const long long *offsets;  // device, ntubes + 1
+    const double *dx;          // device, per tube
+    const int *order;          // device, processing order
+    int ntubes;
+    long long Ntot;
+    int bc_lo, bc_hi;
+    double t_end, cfl, gamma, CT;
+    int max_steps;
+    int group_warps;           // warps per tube (1, 2, 4 or 8)
+    int *queue;                // device work counter, zero before the launch
+    int *steps_out;            // device, per tube
+    double *t_out;             // device, per tube
+    DevCtl *ctl;               // error word
+};
+
+cudaError_t launch_batch1d_f64(const Batch1D &p, cudaStream_t s);
+cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s);
+
 // Finalization done by the last CTA of a launch (see DevCtl).
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_STEP = 2 };
 

@@ -142,6 +142,10 @@ __device__ __forceinline__ unsigned cutoff_bits(float w0, float w1, float w2, fl
     float b1 = fmaf(0.25f * s1a, s1a, c13 * s1b * s1b);
     float b2 = fmaf(0.25f * s2a, s2a, c13 * s2b * s2b);
     float tau = fabsf(b0 - b2);
+    // FP32 round-off floor of epsilon (2^-24 Q^2 / 12 for the unscaled beta;
+    // see RO_FLOOR12 below)
+    const float q = fmaxf(fmaxf(fabsf(w0), fabsf(w2)), fabsf(w4));
+    eps = fmaxf(eps, (5.9604644775390625e-08f / 12.f) * (q * q));
     float g0 = 1.f + __fdividef(tau, b0 + eps);
     float g1 = 1.f + __fdividef(tau, b1 + eps);
     float g2 = 1.f + __fdividef(tau, b2 + eps);
@@ -295,70 +299,63 @@ __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zer
 }
 
 // ==========================================================================
-// Fused 1D stage kernel.  SYS in {SYS_ADV, SYS_BURGERS, SYS_EULER1D}.
-//
-// Warp tiles: warp tile w updates the WT = 29 cells c0 = 29 w .. c0 + 28.
-// Lane l owns the face j+1/2 with j = c0 - 2 + l (faces c0-2 .. c0+29) and
-// stages cells c0-5+l (and c0+27+l for l < 7) in warp-private shared memory.
+// Warp-tile sweep of one 1D problem (a whole domain, or one tube of a ragged
+// batch), shared by the grid-wide stage kernels and the persistent batch
+// kernel.  Warp tile w updates the WT = 29 cells c0 = 29 w .. c0 + 28; lane l
+// owns the face j+1/2 with j = c0 - 2 + l (faces c0-2 .. c0+29) and stages
+// cells c0-5+l (and c0+27+l for l < 7) in warp-private shared memory.
 // Neighbouring faces' cutoff words and face fluxes travel by __shfl, so the
-// hot loop has no CTA-wide barrier; lanes 1..30 produce face fluxes and
-// lanes 2..30 update cells.  Warps loop over tiles with a grid stride.
+// loop has no CTA-wide barrier; lanes 1..30 produce face fluxes and lanes
+// 2..30 update cells.  Returns this lane's max characteristic speed of the
+// cells it wrote (RK mode).
 // ==========================================================================
 constexpr int WT = 29;   // cells updated per warp tile
 constexpr int WS = 39;   // cells staged per warp tile
 constexpr int WC = 40;   // padded row length
 constexpr int WPB = 8;   // warps per CTA
 
+template <typename T>
+struct TileArgs {
+    const T *Us;     // stage input (stencil reads)
+    const T *U0;     // U^n (pointwise reads; stages 1 and 2)
+    T *out;          // RK: stage output; RHS: dU/dt
+    uint8_t *masks;  // RHS only, nullable: [2][m][n+1]
+    int n;           // cells
+    size_t cs;       // stride between conserved variables
+    int bc_lo, bc_hi;
+    double dx;
+    float f_dx;
+    T alpha, dtT, gamma, gm1, a, eps, CT;
+    int rhs_mode, stage;
+    int ebase;       // added to cell/face indices in error reports
+    DevCtl *ctl;
+};
+
 template <typename T, int SYS>
-__global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
+__device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)[WC], T (*sgm)[WC], T (*spr)[WC],
+                                     const T *scoef, int tile0, int tstride) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;  // u, H, sqrt(rho)
     constexpr bool F64 = sizeof(T) == 8;
-    __shared__ T s_U[WPB][M][WC];
-    __shared__ T s_gp[WPB][M][WC];
-    __shared__ T s_gm[WPB][M][WC];
-    __shared__ T s_pr[WPB][NP][WC];
-    __shared__ T s_coef[WPB][92];
-    __shared__ T s_red[WPB];
-
-    DevCtl *ctl = p.ctl;
-    const bool fixed = p.dt_fixed > 0.0;
-    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
-
-    T alpha, dtT;
-    if constexpr (F64) {
-        alpha = __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
-        dtT = fixed ? p.dt_fixed : ctl->dt;
-    } else {
-        alpha = ctl->alpha_f[p.slot_in][0];
-        dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
-    }
-    const T gamma = pick<T>(p.gamma, p.f_gamma), gm1 = pick<T>(p.gamma - 1.0, p.f_gm1), a = pick<T>(p.a, p.f_a);
-    const T eps = pick<T>(p.eps, p.f_eps), CT = pick<T>(p.CT, p.f_CT);
-    const T *Us = static_cast<const T *>(p.Us);
-    const T *U0 = static_cast<const T *>(p.U0);
-    T *out = static_cast<T *>(p.out);
-    const int n = p.n;
+    const int lane = threadIdx.x & 31;
+    const T *Us = A.Us;
+    const T *U0 = A.U0;
+    T *out = A.out;
+    const int n = A.n;
+    const size_t cs = A.cs;
     const int ntiles = (n + WT - 1) / WT;
-    T (*sU)[WC] = s_U[warp];
-    T (*sgp)[WC] = s_gp[warp];
-    T (*sgm)[WC] = s_gm[warp];
-    T (*spr)[WC] = s_pr[warp];
-    const T *scoef = s_coef[warp];
+    const T alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a, eps = A.eps, CT = A.CT;
+    DevCtl *ctl = A.ctl;
     T wsmax = T(0);
-    __syncwarp();
-
-    for (int tile = blockIdx.x * WPB + warp; tile < ntiles; tile += gridDim.x * WPB) {
+    for (int tile = tile0; tile < ntiles; tile += tstride) {
         const int c0 = tile * WT;
         // ---- stage cells c0-5 .. c0+33 -----------------------------------
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
-            if (gi < 0 || gi >= n) gi = ghost_map(gi, n, p.bc_lo, p.bc_hi);
+            if (gi < 0 || gi >= n) gi = ghost_map(gi, n, A.bc_lo, A.bc_hi);
             T U[M], F[M];
 #pragma unroll
-            for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * n + gi];
+            for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * cs + gi];
             if (SYS == SYS_ADV) {
                 F[0] = a * U[0];
             } else if (SYS == SYS_BURGERS) {
@@ -501,9 +498,9 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
             else
                 fm = poly7(scoef + 7 * mm, qm[k][6], qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], qm[k][0]);
             f[k] = fp + fm;
-            if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= n - 1) {
-                p.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dp;
-                p.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dm;
+            if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
+                A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dp;
+                A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dm;
             }
         }
         T fh[M];
@@ -517,7 +514,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
             fh[0] = f[0];
         }
         if (flag && face_out && j >= -2 && j <= n)
-            latch_error(ctl, (flag & ERR_NONPHYSICAL) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), j);
+            latch_error(ctl, (flag & ERR_NONPHYSICAL) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), A.ebase + j);
 
         // ---- flux difference and RK stage ----------------------------------
         T fprev[M];
@@ -528,43 +525,97 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
             T r[M];
             if constexpr (F64) {
 #pragma unroll
-                for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) / p.dx;
+                for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) / A.dx;
             } else {
-                const float idx = __frcp_rn(p.f_dx);
+                const float idx = __frcp_rn(A.f_dx);
 #pragma unroll
                 for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
             }
-            if (p.rhs_mode) {
+            if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * n + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * cs + i] = r[k];
             } else {
                 T o[M];
 #pragma unroll
                 for (int k = 0; k < M; k++) {
                     const T us = sU[k][lane + 3];
-                    if (p.stage == 0) {
+                    if (A.stage == 0) {
                         o[k] = us + dtT * r[k];
-                    } else if (p.stage == 1) {
-                        o[k] = T(0.75) * U0[(size_t)k * n + i] + T(0.25) * (us + dtT * r[k]);
+                    } else if (A.stage == 1) {
+                        o[k] = T(0.75) * U0[(size_t)k * cs + i] + T(0.25) * (us + dtT * r[k]);
                     } else {
                         if constexpr (F64) {
-                            o[k] = T(1.0 / 3.0) * U0[(size_t)k * n + i] + T(2.0 / 3.0) * (us + dtT * r[k]);
+                            o[k] = T(1.0 / 3.0) * U0[(size_t)k * cs + i] + T(2.0 / 3.0) * (us + dtT * r[k]);
                         } else {
                             // in FP32, float(1/3) + float(2/3) = 1 + 6e-8 would grow the
                             // solution by that factor every step: use u0 + 2/3 (v - u0)
-                            const T u0 = U0[(size_t)k * n + i];
+                            const T u0 = U0[(size_t)k * cs + i];
                             o[k] = fmaf(2.0f / 3.0f, (us + dtT * r[k]) - u0, u0);
                         }
                     }
-                    out[(size_t)k * n + i] = o[k];
+                    out[(size_t)k * cs + i] = o[k];
                 }
                 int wflag = 0;
                 wsmax = fmax(wsmax, wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag));
-                if (wflag) latch_error(ctl, wflag, i);
+                if (wflag) latch_error(ctl, wflag, A.ebase + i);
             }
         }
         __syncwarp();  // the next tile overwrites this warp's staging rows
     }
+
+    return wsmax;
+}
+
+// ==========================================================================
+// Fused 1D stage kernel (grid-wide), SYS in {SYS_ADV, SYS_BURGERS, SYS_EULER1D}.
+// ==========================================================================
+template <typename T, int SYS>
+__global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    __shared__ T s_U[WPB][M][WC];
+    __shared__ T s_gp[WPB][M][WC];
+    __shared__ T s_gm[WPB][M][WC];
+    __shared__ T s_pr[WPB][NP][WC];
+    __shared__ T s_coef[WPB][92];
+    __shared__ T s_red[WPB];
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
+
+    TileArgs<T> A;
+    if constexpr (sizeof(T) == 8) {
+        A.alpha = __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
+        A.dtT = fixed ? p.dt_fixed : ctl->dt;
+    } else {
+        A.alpha = ctl->alpha_f[p.slot_in][0];
+        A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
+    }
+    A.Us = static_cast<const T *>(p.Us);
+    A.U0 = static_cast<const T *>(p.U0);
+    A.out = static_cast<T *>(p.out);
+    A.masks = p.masks;
+    A.n = p.n;
+    A.cs = (size_t)p.n;
+    A.bc_lo = p.bc_lo;
+    A.bc_hi = p.bc_hi;
+    A.dx = p.dx;
+    A.f_dx = p.f_dx;
+    A.gamma = pick<T>(p.gamma, p.f_gamma);
+    A.gm1 = pick<T>(p.gamma - 1.0, p.f_gm1);
+    A.a = pick<T>(p.a, p.f_a);
+    A.eps = pick<T>(p.eps, p.f_eps);
+    A.CT = pick<T>(p.CT, p.f_CT);
+    A.rhs_mode = p.rhs_mode;
+    A.stage = p.stage;
+    A.ebase = 0;
+    A.ctl = ctl;
+    __syncwarp();
+    T wsmax = tiles1d<T, SYS>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
+                              blockIdx.x * WPB + warp, gridDim.x * WPB);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -599,6 +650,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// FP32 round-off floor of epsilon.  The characteristic values of a window
+// carry rounding errors of a few ulps of their magnitude Q = max|w|, which
+// reach 12 beta (3 a^2 + 13 b^2) and tau as noise up to ~1.3e4 (2^-24 Q)^2
+// = 5e-11 Q^2.  With epsilon = dx^3 below that level (fine grids in FP32) the
+// noise alone makes chi random in flat regions, switches stencils (including
+// the downwind-biased candidates) and grows into grid-scale oscillations --
+// the failure the choice of epsilon is meant to prevent.  In FP32 the epsilon
+// of 12 beta is therefore max(12 dx^3, 2^-24 Q^2): the FP32 unit round-off
+// times Q^2, three orders above that noise, so that tau/(beta + eps) stays
+// below 1e-3 for pure noise, while jumps above ~1e-4 Q are measured as
+// before.  (FP64 round-off is ~1e-32 Q^2, far below dx^3: FP64 keeps
+// epsilon = dx^3.)
+constexpr float RO_FLOOR12 = 5.9604644775390625e-08f;  // 2^-24
+
 // Cutoff codes of a '+' window (.x) and a '-' window (.y), w0..w4 in upwind
 // order.  beta is scaled by 12 (3 a^2 + 13 b^2) with eps12 = 12 eps, which
 // leaves gamma unchanged; chi_k is evaluated as x_k^6 / sum x^6 with
@@ -617,7 +682,13 @@ __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 
     const float2 b2 = __ffma2_rn(f2(3.f), __fmul2_rn(s2a, s2a), __fmul2_rn(f2(13.f), __fmul2_rn(s2b, s2b)));
     const float2 td = __ffma2_rn(f2(-1.f), b2, b0);
     const float2 tau = make_float2(fabsf(td.x), fabsf(td.y));
-    const float2 d0 = __fadd2_rn(b0, f2(eps12)), d1 = __fadd2_rn(b1, f2(eps12)), d2 = __fadd2_rn(b2, f2(eps12));
+    // epsilon no smaller than the FP32 round-off level of the window (see
+    // RO_FLOOR12), so that rounding noise cannot trigger the cutoff
+    const float qx = fmaxf(fmaxf(fabsf(w0.x), fabsf(w2.x)), fabsf(w4.x));
+    const float qy = fmaxf(fmaxf(fabsf(w0.y), fabsf(w2.y)), fabsf(w4.y));
+    const float2 ro = __fmul2_rn(f2(RO_FLOOR12), __fmul2_rn(make_float2(qx, qy), make_float2(qx, qy)));
+    const float2 ee = make_float2(fmaxf(eps12, ro.x), fmaxf(eps12, ro.y));
+    const float2 d0 = __fadd2_rn(b0, ee), d1 = __fadd2_rn(b1, ee), d2 = __fadd2_rn(b2, ee);
     const float2 g0 = __ffma2_rn(tau, make_float2(rcp_approx(d0.x), rcp_approx(d0.y)), f2(1.f));
     const float2 g1 = __ffma2_rn(tau, make_float2(rcp_approx(d1.x), rcp_approx(d1.y)), f2(1.f));
     const float2 g2 = __ffma2_rn(tau, make_float2(rcp_approx(d2.x), rcp_approx(d2.y)), f2(1.f));
@@ -659,45 +730,43 @@ constexpr unsigned SLOT_MID = 0x1CE739CEu;  // bits 3..1 of every slot
 constexpr unsigned SLOT_LO = 0x02108421u;   // bit 0 of every slot
 constexpr unsigned SLOT_PLUS = 0x00007FFFu; // slots 0..2 ('+' split)
 
-#ifndef T7_F32_MINB
-#define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
-#endif
-
-template <int SYS>
-__global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(const Stage1D p) {
-    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
-    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
-    __shared__ float s_U[WPB][M][WC];
-    __shared__ float s_gp[WPB][M][WC];
-    __shared__ float s_gm[WPB][M][WC];
-    __shared__ float s_pr[WPB][NP][WC];
-    __shared__ __align__(16) float s_cf[32][8];  // row Delta: Table co2 row of Table co3's choice
-    __shared__ float s_red[WPB];
-
-    DevCtl *ctl = p.ctl;
-    const bool fixed = p.dt_fixed > 0.0;
-    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {
-        const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
+// Delta-indexed coefficient table: row D holds Table co2's row for Table co3's
+// choice at D ("no exist" rows get f11); filled by a 256-thread CTA.
+__device__ __forceinline__ void fill_delta_table(float (*s_cf)[8]) {
+    const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
+    if (row < 32) {
         int m = lut_select(row);
         if (m == 15) m = 11;
         s_cf[row][t] = t < 7 ? coef<float>(7 * m + t) : 0.f;
     }
-    const float alpha = ctl->alpha_f[p.slot_in][0];
-    const float dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
-    const float gamma = p.f_gamma, gm1 = p.f_gm1, a = p.f_a;
-    const float eps12 = 12.f * p.f_eps, CT = p.f_CT;
-    const float idx = 1.f / p.f_dx;
-    const float *Us = static_cast<const float *>(p.Us);
-    const float *U0 = static_cast<const float *>(p.U0);
-    float *out = static_cast<float *>(p.out);
-    const int n = p.n;
+}
+
+#ifndef T7_F32_MINB
+#define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
+#endif
+
+// FP32 warp-tile sweep (paired splits); same contract as tiles1d.  s_cf is
+// the Delta-indexed coefficient table [32][8].  The raw state of a warp
+// tile's staged cells (lane and lane + 32) is loaded one tile ahead, and U^n
+// of the tile's own cells at the start of the tile, so DRAM latency overlaps
+// the face work.
+template <int SYS>
+__device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*sU)[WC], float (*sgp)[WC],
+                                             float (*sgm)[WC], float (*spr)[WC], const float (*s_cf)[8], int tile0,
+                                             int tstride) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    const int lane = threadIdx.x & 31;
+    const float alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a;
+    const float eps12 = 12.f * A.eps, CT = A.CT;
+    const float idx = 1.f / A.f_dx;
+    const float *Us = A.Us;
+    const float *U0 = A.U0;
+    float *out = A.out;
+    const int n = A.n;
+    const size_t cs = A.cs;
     const int ntiles = (n + WT - 1) / WT;
-    float (*sU)[WC] = s_U[warp];
-    float (*sgp)[WC] = s_gp[warp];
-    float (*sgm)[WC] = s_gm[warp];
-    float (*spr)[WC] = s_pr[warp];
+    DevCtl *ctl = A.ctl;
     float wsmax = 0.f;
     // Software pipelining: the raw state of a warp tile's staged cells (lane
     // and lane + 32) is loaded one tile ahead, and U^n of the tile's own cells
@@ -706,26 +775,25 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     auto load_tile = [&](int tile) {
         const int c0 = tile * WT;
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
-        if (ga < 0 || ga >= n) ga = ghost_map(ga, n, p.bc_lo, p.bc_hi);
-        if (gb < 0 || gb >= n) gb = ghost_map(gb, n, p.bc_lo, p.bc_hi);
+        if (ga < 0 || ga >= n) ga = ghost_map(ga, n, A.bc_lo, A.bc_hi);
+        if (gb < 0 || gb >= n) gb = ghost_map(gb, n, A.bc_lo, A.bc_hi);
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            ua[k] = Us[(size_t)k * n + ga];
-            ub[k] = (lane < WS - 32) ? Us[(size_t)k * n + gb] : 0.f;
+            ua[k] = Us[(size_t)k * cs + ga];
+            ub[k] = (lane < WS - 32) ? Us[(size_t)k * cs + gb] : 0.f;
         }
     };
-    int tile = blockIdx.x * WPB + warp;
+    int tile = tile0;
     if (tile < ntiles) load_tile(tile);
-    __syncthreads();
 
-    for (; tile < ntiles; tile += gridDim.x * WPB) {
+    for (; tile < ntiles; tile += tstride) {
         const int c0 = tile * WT;
         const int jc = c0 - 2 + lane;  // this lane's cell (if it updates one)
         float u0r[M];
-        if (!p.rhs_mode && p.stage > 0) {
+        if (!A.rhs_mode && A.stage > 0) {
             const int ic = jc < n ? jc : n - 1;
 #pragma unroll
-            for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * n + (ic < 0 ? 0 : ic)];
+            for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * cs + (ic < 0 ? 0 : ic)];
         }
         float Ucur[2][M];
 #pragma unroll
@@ -733,7 +801,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
             Ucur[0][k] = ua[k];
             Ucur[1][k] = ub[k];
         }
-        if (tile + gridDim.x * WPB < ntiles) load_tile(tile + gridDim.x * WPB);
+        if (tile + tstride < ntiles) load_tile(tile + tstride);
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int c = lane + 32 * r;
@@ -852,11 +920,11 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
                 f[k] = s.x + s.y;
             }
         }
-        if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= n - 1) {
+        if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
 #pragma unroll
             for (int k = 0; k < M; k++) {
-                p.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * k)) & 31u);
-                p.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * (3 + k))) & 31u);
+                A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * k)) & 31u);
+                A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * (3 + k))) & 31u);
             }
         }
         float fh[M];
@@ -867,7 +935,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
         } else {
             fh[0] = f[0];
         }
-        if (flag && face_out && j >= -2 && j <= n) latch_error(ctl, flag, j);
+        if (flag && face_out && j >= -2 && j <= n) latch_error(ctl, flag, A.ebase + j);
 
         float fprev[M];
 #pragma unroll
@@ -877,32 +945,77 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
             float r[M];
 #pragma unroll
             for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
-            if (p.rhs_mode) {
+            if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * n + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * cs + i] = r[k];
             } else {
                 float o[M];
 #pragma unroll
                 for (int k = 0; k < M; k++) {
                     const float v = fmaf(dtT, r[k], sU[k][lane + 3]);
-                    if (p.stage == 0) {
+                    if (A.stage == 0) {
                         o[k] = v;
-                    } else if (p.stage == 1) {
+                    } else if (A.stage == 1) {
                         o[k] = fmaf(0.75f, u0r[k], 0.25f * v);
                     } else {
                         // u0 + 2/3 (v - u0): float(1/3) + float(2/3) != 1 would
                         // grow the solution by 6e-8 every step
                         o[k] = fmaf(2.0f / 3.0f, v - u0r[k], u0r[k]);
                     }
-                    out[(size_t)k * n + i] = o[k];
+                    out[(size_t)k * cs + i] = o[k];
                 }
                 int wflag = 0;
                 wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(o, gm1, gamma, a, &wflag));
-                if (wflag) latch_error(ctl, wflag, i);
+                if (wflag) latch_error(ctl, wflag, A.ebase + i);
             }
         }
         __syncwarp();
     }
+
+    return wsmax;
+}
+
+template <int SYS>
+__global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(const Stage1D p) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    __shared__ float s_U[WPB][M][WC];
+    __shared__ float s_gp[WPB][M][WC];
+    __shared__ float s_gm[WPB][M][WC];
+    __shared__ float s_pr[WPB][NP][WC];
+    __shared__ __align__(16) float s_cf[32][8];  // row Delta: Table co2 row of Table co3's choice
+    __shared__ float s_red[WPB];
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    fill_delta_table(s_cf);
+    TileArgs<float> A;
+    A.alpha = ctl->alpha_f[p.slot_in][0];
+    A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
+    A.Us = static_cast<const float *>(p.Us);
+    A.U0 = static_cast<const float *>(p.U0);
+    A.out = static_cast<float *>(p.out);
+    A.masks = p.masks;
+    A.n = p.n;
+    A.cs = (size_t)p.n;
+    A.bc_lo = p.bc_lo;
+    A.bc_hi = p.bc_hi;
+    A.dx = p.dx;
+    A.f_dx = p.f_dx;
+    A.gamma = p.f_gamma;
+    A.gm1 = p.f_gm1;
+    A.a = p.f_a;
+    A.eps = p.f_eps;
+    A.CT = p.f_CT;
+    A.rhs_mode = p.rhs_mode;
+    A.stage = p.stage;
+    A.ebase = 0;
+    A.ctl = ctl;
+    __syncthreads();
+    float wsmax = tiles1d_f32<SYS>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf, blockIdx.x * WPB + warp,
+                                   gridDim.x * WPB);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -1061,6 +1174,149 @@ template <typename T>
 cudaError_t launch_recon(const Recon &p, cudaStream_t st) {
     const int grid = (p.n + TILE - 1) / TILE;
     recon_kernel<T><<<grid, NT, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace t7
+
+// ==========================================================================
+// Persistent ragged-batch kernel (1D Euler).  The CTA's warps form groups of
+// G = p.group_warps warps; each group's leader takes the next tube from an
+// atomic queue (the host orders tubes costliest first) and the group runs the
+// tube's whole SSP-RK3 loop to t_end: alpha of U^n and the CFL step (the
+// oracle's expressions), then three stages, each a warp-tile sweep over the
+// tube followed by a group reduction of the new state's max(|u| + c), which is
+// the next stage's alpha.  Group barriers are named barriers (id = group + 1).
+// Tubes are independent, so groups never wait on each other.
+// ==========================================================================
+namespace t7 {
+
+__device__ __forceinline__ void group_sync(int group, int G) {
+    if (G == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(G * 32) : "memory");
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_kernel(const Batch1D p) {
+    __shared__ T s_U[WPB][3][WC];
+    __shared__ T s_gp[WPB][3][WC];
+    __shared__ T s_gm[WPB][3][WC];
+    __shared__ T s_pr[WPB][3][WC];
+    __shared__ T s_coef[WPB][92];
+    __shared__ __align__(16) float s_cf[32][8];
+    __shared__ T s_red[WPB];
+    __shared__ int s_tube[WPB];
+    constexpr bool F64 = sizeof(T) == 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = p.group_warps, group = warp / G, wg = warp % G;
+    for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
+    if constexpr (!F64) fill_delta_table(s_cf);
+    __syncthreads();
+    T *U = static_cast<T *>(p.U);
+    T *W1 = static_cast<T *>(p.W1);
+    T *W2 = static_cast<T *>(p.W2);
+    const size_t cs = (size_t)p.Ntot;
+    const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0);
+
+    // group max over its G warps; every lane of the group gets the result
+    auto group_max = [&](T v) -> T {
+        v = warp_max(v);
+        if (lane == 0) s_red[warp] = v;
+        group_sync(group, G);
+        T m = s_red[group * G];
+        for (int w = 1; w < G; w++) m = fmax(m, s_red[group * G + w]);
+        group_sync(group, G);
+        return m;
+    };
+
+    for (;;) {
+        if (wg == 0 && lane == 0) s_tube[group] = atomicAdd(p.queue, 1);
+        group_sync(group, G);
+        const int q = s_tube[group];
+        group_sync(group, G);
+        if (q >= p.ntubes) break;
+        const int tube = p.order[q];
+        const long long off = p.offsets[tube];
+        const int n = (int)(p.offsets[tube + 1] - off);
+        const double dx = p.dx[tube];
+
+        // alpha of U^n over the tube's cells
+        T a0 = T(0);
+        int flag = 0, first = 0x7fffffff;
+        for (int i = wg * 32 + lane; i < n; i += G * 32) {
+            T Uc[3] = {U[off + i], U[cs + off + i], U[2 * cs + off + i]};
+            int f = 0;
+            a0 = fmax(a0, wavespeed1d<T, SYS_EULER1D>(Uc, gm1, gamma, T(0), &f));
+            if (f) {
+                flag |= f;
+                first = min(first, i);
+            }
+        }
+        if (flag) latch_error(p.ctl, flag, (int)(off + first));
+        T alpha = group_max(a0);
+
+        TileArgs<T> A;
+        A.masks = nullptr;
+        A.n = n;
+        A.cs = cs;
+        A.bc_lo = p.bc_lo;
+        A.bc_hi = p.bc_hi;
+        A.dx = dx;
+        A.f_dx = (float)dx;
+        A.gamma = gamma;
+        A.gm1 = gm1;
+        A.a = T(0);
+        A.eps = T((dx * dx) * dx);
+        A.CT = T(p.CT);
+        A.rhs_mode = 0;
+        A.ebase = (int)off;
+        A.ctl = p.ctl;
+        A.U0 = U + off;
+        T *ins[3] = {U + off, W1 + off, W2 + off};
+        T *outs[3] = {W1 + off, W2 + off, U + off};
+
+        double t = 0.0;
+        int steps = 0;
+        while (steps < p.max_steps && t < p.t_end) {
+            double dt = (p.cfl * dx) / (double)alpha;
+            if (t + dt > p.t_end) dt = p.t_end - t;
+            A.dtT = T(dt);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                A.Us = ins[k];
+                A.out = outs[k];
+                A.stage = k;
+                A.alpha = alpha;
+                T ws;
+                if constexpr (F64) {
+                    ws = tiles1d<T, SYS_EULER1D>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp], wg, G);
+                } else {
+                    ws = tiles1d_f32<SYS_EULER1D>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf, wg, G);
+                }
+                alpha = group_max(ws);  // also orders this stage's writes before the next stage's reads
+            }
+            t = t + dt;
+            steps = steps + 1;
+        }
+        if (wg == 0 && lane == 0) {
+            p.steps_out[tube] = steps;
+            p.t_out[tube] = t;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch1d(const Batch1D &p, cudaStream_t st) {
+    if (p.group_warps != 1 && p.group_warps != 2 && p.group_warps != 4 && p.group_warps != 8)
+        return cudaErrorInvalidValue;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch1d_kernel<T>, WPB * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    batch1d_kernel<T><<<num_sms() * per_sm, WPB * 32, 0, st>>>(p);
     return cudaGetLastError();
 }
 

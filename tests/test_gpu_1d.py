@@ -288,3 +288,37 @@ def test_nonphysical_state_is_reported():
     U2, _ = I.shu_osher(1600)
     steps, _ = c.run(dev(U2), 0.5, max_steps=2)
     assert steps == 2
+
+
+def test_f32_flat_region_fine_grid_masks_match_f64():
+    """A nearly uniform, high-energy Euler state on a fine grid (dx = 1/8192,
+    epsilon = dx^3 = 1.8e-12): FP32 rounding noise in beta is far above
+    epsilon there, and without the FP32 round-off floor of epsilon the FP32
+    cutoff cuts stencils at random.  Masks must agree with the FP64 oracle."""
+    n = 8192
+    x = (np.arange(n) + 0.5) / n
+    U = I.prim_to_cons_1d(2.35 + 1e-3 * np.sin(2 * np.pi * x), np.full(n, -0.015), np.full(n, 10.8))
+    ro, _, mo = oracle.rhs_1d(oracle.SYS_EULER1D, U, 1.0 / n, want_masks=True)
+    c = ctx(oracle.SYS_EULER1D, n, 1.0 / n, prec=B.T7_F32)
+    rg, mg = c.euler_rhs(dev(U, torch.float32), want_masks=True)
+    c.sync()
+    assert (mg.cpu().numpy() == mo).mean() >= 0.9999
+
+
+@pytest.mark.parametrize("tube", [2099, 1452])
+def test_f32_fine_tube_stays_close_to_f64(tube):
+    """Shock tubes of the 4096-tube configuration (seed 7; 4717 and 5047 cells)
+    that went non-physical in FP32 before the round-off floor of epsilon: the
+    FP32 run reaches t = 0.1 and stays within 2e-4 relative L1 of FP64."""
+    U, off, dx, _ = I.riemann_tube_batch(7, 4096, 256, 8192)
+    t = tube
+    Ut = np.ascontiguousarray(U[:, off[t]:off[t + 1]])
+    n = Ut.shape[1]
+    out = {}
+    for prec, dtype in ((B.T7_F64, torch.float64), (B.T7_F32, torch.float32)):
+        c = ctx(oracle.SYS_EULER1D, n, dx[t], bc=(1, 1), prec=prec)
+        Ug = dev(Ut, dtype)
+        steps, tt = c.run(Ug, 0.5, t_end=0.1)
+        assert tt == pytest.approx(0.1, abs=1e-12)
+        out[prec] = host(Ug)
+    assert rel_l1(out[B.T7_F32][0], out[B.T7_F64][0]) < 2e-4
