@@ -206,6 +206,58 @@ def bench_2d(args, torch, B, dist, world, rank):
     return out
 
 
+def bench_batch(args, torch, B, dist, world, rank):
+    """Ragged batch: 4096 Riemann tubes on [0,1], lengths U[256, 8192] (seed 7),
+    states rho U[0.1,2], u U[-1,1], p U[0.1,10], each to t = 0.1 at CFL 0.5 in
+    one persistent launch.  Gcell-steps/s = sum over tubes of cells x steps /
+    time; FP64 and FP32 also timed over a fixed 10 steps of every tube."""
+    from oracle import riemann  # exact solution: accuracy check only, not timed
+    U0, off, dx, states = I.riemann_tube_batch(7, 4096, 256, 8192)
+    n = np.diff(off)
+    out = {"workload": "4096 Riemann tubes, N ~ U[256, 8192] (17.5M cells), t = 0.1, CFL 0.5"}
+    ctx = B.Context(B.T7_EULER1D, U0.shape[1], 1.0, prec=B.T7_F32, bc=(1, 1, 0, 0), gamma=GAMMA)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    g, trial = ctx.batch_autotune(U, off, dx, 0.5, trial_steps=3)
+    out["autotune"] = {"group_warps": g, "trial_ms": {str(k): float(v) for k, v in zip((1, 2, 4, 8), trial)}}
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(ctx.stream)
+    steps, t = ctx.batch_run(U, off, dx, 0.1, 0.5)
+    end.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    cell_steps = float(np.sum(n * steps))
+    out["f32"] = {"value": cell_steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s", "ms": ms,
+                  "cell_steps": cell_steps, "gpu_launches": 1, "all_reached_t_end": bool(np.allclose(t, 0.1))}
+    got = U.double().cpu().numpy()
+    rng = np.random.default_rng(0)
+    errs = []
+    for k in rng.choice(4096, 32, replace=False):
+        a, b = off[k], off[k + 1]
+        x = (np.arange(b - a) + 0.5) / (b - a)
+        rho, _, _ = riemann.sample(tuple(states[k, 0]), tuple(states[k, 1]), (x - 0.5) / 0.1)
+        errs.append(np.mean(np.abs(got[0, a:b] - rho)) / (np.ptp(rho) + 1e-12))
+    out["f32"]["rho_l1_vs_exact_over_range_mean32"] = float(np.mean(errs))
+    fixed = {}
+    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        c = B.Context(B.T7_EULER1D, U0.shape[1], 1.0, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
+        Ug = torch.tensor(U0, dtype=dtype, device="cuda")
+        torch.cuda.synchronize()
+        start.record(c.stream)
+        st, _ = c.batch_run(Ug, off, dx, 0.1, 0.5, max_steps=10, group_warps=g)
+        end.record(c.stream)
+        torch.cuda.synchronize()
+        fixed[name] = float(np.sum(n * st)) / (start.elapsed_time(end) * 1e-3) / 1e9
+        c.close()
+    out["fixed_10_steps_gcell_steps_per_s"] = fixed
+    out["f32_over_f64"] = fixed["f32"] / fixed["f64"]
+    ctx.close()
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -245,9 +297,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
-    ap.add_argument("--only", choices=["f32", "f64", "2d"], default=None,
+    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch"], default=None,
                     help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -266,10 +319,10 @@ def main():
         dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
         dist = dist_mod
 
-    if args.only == "2d":
-        r2 = bench_2d(args, torch, B, dist, world, rank)
+    if args.only in ("2d", "batch"):
+        r2 = (bench_2d if args.only == "2d" else bench_batch)(args, torch, B, dist, world, rank)
         if rank == 0:
-            print(json.dumps({"only": "2d", **r2}), flush=True)
+            print(json.dumps({"only": args.only, **r2}), flush=True)
         return 0
     U0, dx = I.shu_osher(N1, tiles=args.tiles)
     n = U0.shape[1]
@@ -336,6 +389,7 @@ def main():
             print(json.dumps({"only": args.only, **res[args.only]}), flush=True)
         return 0
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
+    resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
     # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
     acc = {}
     Ua, dxa = I.shu_osher(N1)
@@ -374,7 +428,7 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "cpu_baseline": cpu,
+        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "batch": resb, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0

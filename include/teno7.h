@@ -125,6 +125,22 @@ t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, 
 t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out);
 
+/* Discrete adjoint of t7_euler_rhs for 1D Euler: out = (dL/dU)^T v at the
+ * state U, with the stencil selection (every Delta_i of both splits and all
+ * fields) and the global Lax-Friedrichs alpha frozen at their values for U;
+ * the Roe frame, the characteristic projection, the split fluxes and the flux
+ * difference are differentiated exactly.  U, v, out: device [3][nx].  Async.
+ * (FP32 contexts take the masks from a forward evaluation of U, so the
+ * selection is the forward kernel's bit for bit.) */
+t7_status t7_euler_rhs_adjoint(t7_ctx *ctx, const void *U, const void *v, void *out);
+
+/* Adjoint of one SSP-RK3 step of size dt from the state U (the step's start,
+ * unchanged): recomputes the stage states, then maps lambda (device [3][nx],
+ * the adjoint of the step's result) in place to the adjoint of U:
+ *   U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U3 = 1/3 U + 2/3 (U2 + dt L(U2))
+ * transposed, with L^T from t7_euler_rhs_adjoint at each stage.  Async. */
+t7_status t7_rk3_step_adjoint(t7_ctx *ctx, const void *U, double dt, void *lambda);
+
 /* Ragged batch of independent 1D Euler problems (shock tubes) of uneven
  * length, each advanced by its own SSP-RK3 loop with its own CFL step
  * dt = CFL dx_t / alpha_t(U^n) to t_end (or max_steps), all in ONE persistent

@@ -66,6 +66,8 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_run_host": ([vp, vp, d, d, i, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         "t7_rk3_step_static": ([ctypes.POINTER(t7_grid), vp, d, vp, ctypes.c_char_p, ctypes.c_size_t], i),
         "t7_batch_run": ([vp, vp, vp, vp, i, d, d, i, i, vp, vp], i),
+        "t7_euler_rhs_adjoint": ([vp, vp, vp, vp], i),
+        "t7_rk3_step_adjoint": ([vp, vp, d, vp], i),
         "t7_batch_autotune": ([vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), vp], i),
     }
     for name, (args, res) in sigs.items():
@@ -200,6 +202,21 @@ class Context:
         if st != T7_OK:
             raise T7Error(st, f"t7_rk3_step_static: {buf.value.decode()}")
         return U
+
+    # ------------------------------------------------------------ adjoint --
+    def euler_rhs_adjoint(self, U, v, out=None):
+        """(dL/dU)^T v with the stencil selection and alpha frozen at U."""
+        torch = self._torch
+        out = torch.empty_like(U) if out is None else self._dev(out)
+        self._check(self.lib.t7_euler_rhs_adjoint(self.h, _ptr(self._dev(U)), _ptr(self._dev(v)), _ptr(out)),
+                    "t7_euler_rhs_adjoint")
+        return out
+
+    def rk3_step_adjoint(self, U, dt: float, lam):
+        """Map lam (adjoint of the step result) in place to the adjoint of U."""
+        self._check(self.lib.t7_rk3_step_adjoint(self.h, _ptr(self._dev(U)), dt, _ptr(self._dev(lam))),
+                    "t7_rk3_step_adjoint")
+        return lam
 
     # ------------------------------------------------------- ragged batch --
     def batch_run(self, U, offsets, dx, t_end: float, cfl: float, max_steps: int = 2**31 - 1,

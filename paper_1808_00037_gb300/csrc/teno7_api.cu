@@ -15,6 +15,7 @@
 
 #include "teno7.h"
 #include "teno7_internal.h"
+#include "teno7_adjoint_params.h"
 
 struct t7_ctx {
     t7_grid g;
@@ -33,6 +34,8 @@ struct t7_ctx {
     int *b_order, *b_steps, *b_queue;
     int b_cap;
     int b_group;           // warps per tube chosen by t7_batch_autotune (0: not tuned)
+    void *adj[3];          // adjoint work vectors (allocated on first use)
+    uint8_t *adj_masks[3]; // FP32: forward masks of the three stage states
     t7::DevCtl *ctl_host;  // pinned mirror for status reads
     char err[512];
 };
@@ -290,6 +293,10 @@ t7_status t7_destroy(t7_ctx *c) {
     if (c->b_order) cudaFree(c->b_order);
     if (c->b_steps) cudaFree(c->b_steps);
     if (c->b_queue) cudaFree(c->b_queue);
+    for (int k = 0; k < 3; k++) {
+        if (c->adj[k]) cudaFree(c->adj[k]);
+        if (c->adj_masks[k]) cudaFree(c->adj_masks[k]);
+    }
     if (c->ctl) cudaFree(c->ctl);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
     delete c;
@@ -430,6 +437,121 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
     if (e != cudaSuccess) return cuda_fail(c, e, "D2H copy");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
     return st;
+}
+
+// -------------------------------------------------------------- adjoint ----
+static t7_status adj_check(t7_ctx *c) {
+    if (!c) return T7_EINVAL;
+    if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "the adjoint takes a 1D Euler context");
+    const size_t bytes = c->ncell * c->m * c->esize;
+    const size_t mbytes = (size_t)2 * 3 * (c->g.nx + 1);
+    for (int k = 0; k < 3; k++) {
+        if (!c->adj[k] && cudaMalloc(&c->adj[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, T7_ENOMEM, "adjoint buffers");
+        }
+        if (c->g.prec == T7_F32 && !c->adj_masks[k] && cudaMalloc((void **)&c->adj_masks[k], mbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, T7_ENOMEM, "adjoint mask buffers");
+        }
+    }
+    return T7_OK;
+}
+
+// out = (dL/dU)^T v at U with alpha from `slot`, masks frozen (given or recomputed)
+static cudaError_t adj_apply(t7_ctx *c, const void *U, int slot, const uint8_t *masks, const void *v, void *out) {
+    cudaError_t e = cudaMemsetAsync(out, 0, c->ncell * c->m * c->esize, c->stream);
+    if (e != cudaSuccess) return e;
+    t7::Adjoint1D a;
+    memset(&a, 0, sizeof(a));
+    a.U = U;
+    a.v = v;
+    a.out = out;
+    a.masks = masks;
+    a.n = c->g.nx;
+    a.bc_lo = c->g.bc[0];
+    a.bc_hi = c->g.bc[1];
+    a.dx = c->g.dx;
+    a.eps = eps_of(c->g.eps_x, c->g.dx);
+    a.CT = c->g.CT;
+    a.gamma = c->g.gamma;
+    a.ctl = c->ctl;
+    a.slot_in = slot;
+    return c->g.prec == T7_F64 ? t7::launch_rhs_adjoint1d_f64(a, c->stream) : t7::launch_rhs_adjoint1d_f32(a, c->stream);
+}
+
+static cudaError_t combine(t7_ctx *c, void *out, const void *x, const void *y, const void *z, double c1, double c2,
+                           double c3) {
+    const size_t N = c->ncell * c->m;
+    return c->g.prec == T7_F64 ? t7::launch_combine_f64(out, x, y, z, c1, c2, c3, N, c->stream)
+                               : t7::launch_combine_f32(out, x, y, z, c1, c2, c3, N, c->stream);
+}
+
+// FP32: masks of the forward stage kernel at state U (alpha in `slot`), so the
+// adjoint uses exactly the forward's selection
+static cudaError_t forward_masks(t7_ctx *c, const void *U, int slot, uint8_t *masks, void *scratch) {
+    t7::Stage1D p = stage_params(c, U, nullptr, scratch);
+    p.rhs_mode = 1;
+    p.masks = masks;
+    p.slot_in = slot;
+    return stage(c, p);
+}
+
+t7_status t7_euler_rhs_adjoint(t7_ctx *c, const void *U, const void *v, void *out) {
+    t7_status st = adj_check(c);
+    if (st) return st;
+    if (!U || !v || !out) return fail(c, T7_EINVAL, "t7_euler_rhs_adjoint: null array");
+    cudaError_t e = alpha_init(c, U);
+    const uint8_t *masks = nullptr;
+    if (e == cudaSuccess && c->g.prec == T7_F32) {
+        e = forward_masks(c, U, 0, c->adj_masks[0], c->adj[0]);
+        masks = c->adj_masks[0];
+    }
+    if (e == cudaSuccess) e = adj_apply(c, U, 0, masks, v, out);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+    return T7_OK;
+}
+
+t7_status t7_rk3_step_adjoint(t7_ctx *c, const void *U, double dt, void *lambda) {
+    t7_status st = adj_check(c);
+    if (st) return st;
+    if (!U || !lambda || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step_adjoint: bad argument");
+    // Recompute the stage states U1, U2; slot k holds alpha of stage state k
+    // while it is needed (the stage-1 launch clears slot 0, so alpha(U) is
+    // taken again before the last adjoint application).  FP32 records each
+    // state's forward masks as soon as its alpha is known.
+    const void *Us[3] = {U, c->U1, c->U2};
+    const uint8_t *mk[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = alpha_init(c, U);
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+        if (c->g.prec == T7_F32) {
+            e = forward_masks(c, Us[k], k, c->adj_masks[k], c->adj[0]);
+            mk[k] = c->adj_masks[k];
+        }
+        if (k == 2 || e != cudaSuccess) break;
+        t7::Stage1D p = stage_params(c, Us[k], k == 0 ? nullptr : U, k == 0 ? c->U1 : c->U2);
+        p.rhs_mode = 0;
+        p.stage = k;
+        p.dt_fixed = dt;
+        p.f_dt_fixed = (float)dt;
+        p.slot_in = k;
+        e = stage(c, p);
+    }
+    void *tmp = c->adj[0], *w = c->adj[1], *acc = c->adj[2];
+    // U3 = U/3 + 2/3 (U2 + dt L(U2))
+    if (e == cudaSuccess) e = adj_apply(c, Us[2], 2, mk[2], lambda, tmp);
+    if (e == cudaSuccess) e = combine(c, w, nullptr, lambda, tmp, 0.0, 2.0 / 3.0, dt);
+    if (e == cudaSuccess) e = combine(c, acc, nullptr, lambda, lambda, 0.0, 1.0 / 3.0, 0.0);
+    // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+    if (e == cudaSuccess) e = adj_apply(c, Us[1], 1, mk[1], w, tmp);
+    if (e == cudaSuccess) e = combine(c, acc, acc, w, w, 1.0, 0.75, 0.0);
+    if (e == cudaSuccess) e = combine(c, w, nullptr, w, tmp, 0.0, 0.25, dt);
+    // U1 = U + dt L(U); alpha(U) into slot 0 again (cleared by the stage-1 launch)
+    if (e == cudaSuccess) e = alpha_launch(c, U);
+    if (e == cudaSuccess) e = adj_apply(c, Us[0], 0, mk[0], w, tmp);
+    if (e == cudaSuccess) e = combine(c, lambda, acc, w, tmp, 1.0, 1.0, dt);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
+    return T7_OK;
 }
 
 // ---------------------------------------------------------------- batch ----

@@ -1,6 +1,7 @@
 // FP32 instantiation of the TENO7-ext kernels (FMA contraction on).
 #include "teno7_kernels.cuh"
 #include "teno7_kernels2d.cuh"
+#include "teno7_adjoint.cuh"
 
 namespace t7 {
 cudaError_t launch_stage1d_f32(const Stage1D &p, cudaStream_t s) { return launch_stage1d<float>(p, s); }
@@ -9,4 +10,9 @@ cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s) { return launch_rec
 cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s) { return launch_stage2d<float>(p, s); }
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s) { return launch_alpha2d<float>(p, s); }
 cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s) { return launch_batch1d<float>(p, s); }
+cudaError_t launch_rhs_adjoint1d_f32(const Adjoint1D &p, cudaStream_t s) { return launch_rhs_adjoint1d<float>(p, s); }
+cudaError_t launch_combine_f32(void *out, const void *x, const void *y, const void *z, double c1, double c2,
+                               double c3, size_t N, cudaStream_t s) {
+    return launch_combine<float>(out, x, y, z, c1, c2, c3, N, s);
+}
 }  // namespace t7

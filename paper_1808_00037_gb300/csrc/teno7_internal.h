@@ -108,6 +108,15 @@ struct Batch1D {
 cudaError_t launch_batch1d_f64(const Batch1D &p, cudaStream_t s);
 cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s);
 
+// Discrete adjoint of the 1D Euler right-hand side (teno7_adjoint.cuh).
+struct Adjoint1D;
+cudaError_t launch_rhs_adjoint1d_f64(const Adjoint1D &p, cudaStream_t s);
+cudaError_t launch_rhs_adjoint1d_f32(const Adjoint1D &p, cudaStream_t s);
+cudaError_t launch_combine_f64(void *out, const void *x, const void *y, const void *z, double c1, double c2,
+                               double c3, size_t N, cudaStream_t s);
+cudaError_t launch_combine_f32(void *out, const void *x, const void *y, const void *z, double c1, double c2,
+                               double c3, size_t N, cudaStream_t s);
+
 // Finalization done by the last CTA of a launch (see DevCtl).
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_STEP = 2 };
 
