@@ -213,8 +213,11 @@ def bench_batch(args, torch, B, dist, world, rank):
     time; FP64 and FP32 also timed over a fixed 10 steps of every tube."""
     from oracle import riemann  # exact solution: accuracy check only, not timed
     U0, off, dx, states = I.riemann_tube_batch(7, 4096, 256, 8192)
+    out = {"workload": "4096 Riemann tubes per GPU, N ~ U[256, 8192] (17.5M cells), t = 0.1, CFL 0.5"}
+    if world > 1:
+        # weak scaling: every rank takes its own 4096 tubes (seed 7 + rank), no collective
+        U0, off, dx, states = I.riemann_tube_batch(7 + rank, 4096, 256, 8192)
     n = np.diff(off)
-    out = {"workload": "4096 Riemann tubes, N ~ U[256, 8192] (17.5M cells), t = 0.1, CFL 0.5"}
     ctx = B.Context(B.T7_EULER1D, U0.shape[1], 1.0, prec=B.T7_F32, bc=(1, 1, 0, 0), gamma=GAMMA)
     U = torch.tensor(U0, dtype=torch.float32, device="cuda")
     g, trial = ctx.batch_autotune(U, off, dx, 0.5, trial_steps=3)
@@ -258,6 +261,31 @@ def bench_batch(args, torch, B, dist, world, rank):
     return out
 
 
+def bench_adjoint(args, torch, B):
+    """Sine-mode adjoint problem: N = 4096 periodic, 64 modes (seed 11), 2000
+    SSP-RK3 steps of fixed dt, checkpoints every 100 steps.  Times a plain
+    forward run and the full gradient (checkpointed forward + reverse); the
+    reverse cost is reported as a multiple of the forward cost."""
+    from paper_1808_00037_gb300 import adjoint as A
+    a = I.adjoint_modes(11, K=64)
+    out = {"workload": "1D Euler periodic N=4096, 64 sine modes, 2000 RK3 steps, checkpoints every 100"}
+    for name, prec in (("f64", B.T7_F64), ("f32", B.T7_F32)):
+        J, g, dt = A.sine_modes_gradient(a, n=4096, nsteps=20, every=10, prec=prec)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A.sine_modes_objective(a, 4096, 2000, dt, prec=prec)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        J, g, _ = A.sine_modes_gradient(a, n=4096, nsteps=2000, every=100, prec=prec, dt=dt)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+        out[name] = {"forward_s": t_fwd, "gradient_s": t_grad,
+                     "reverse_over_forward": (t_grad - t_fwd) / t_fwd, "J": J,
+                     "grad_norm": float(np.linalg.norm(g))}
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -298,9 +326,10 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
-    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch"], default=None,
+    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint"], default=None,
                     help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -319,6 +348,10 @@ def main():
         dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
         dist = dist_mod
 
+    if args.only == "adjoint":
+        if rank == 0:
+            print(json.dumps({"only": "adjoint", **bench_adjoint(args, torch, B)}), flush=True)
+        return 0
     if args.only in ("2d", "batch"):
         r2 = (bench_2d if args.only == "2d" else bench_batch)(args, torch, B, dist, world, rank)
         if rank == 0:
@@ -390,6 +423,7 @@ def main():
         return 0
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
+    resa = None if (args.no_adjoint or rank != 0) else bench_adjoint(args, torch, B)
     # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
     acc = {}
     Ua, dxa = I.shu_osher(N1)
@@ -428,7 +462,8 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "batch": resb, "cpu_baseline": cpu,
+        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
+        "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0
