@@ -73,6 +73,9 @@ def lib() -> ctypes.CDLL:
         _lib.or_frame_1d.argtypes = [p, p, d, p, p]
         _lib.or_alpha_1d.argtypes = [i, p, i, d, d, p]
         _lib.or_alpha_2d.argtypes = [p, i, i, d, p]
+        _lib.or_set_scheme.argtypes = [i]
+        _lib.or_select5.argtypes = [i]
+        _lib.or_coeffs5.argtypes = [p]
         _lib.or_frame_2d.argtypes = [p, p, d, i, p, p]
     return _lib
 
@@ -93,6 +96,35 @@ def _check(st: int, what: str, strict: bool):
     if st != OK and strict:
         raise OracleError(f"{what}: status {st}")
     return st
+
+
+SCHEME_TENO7EXT, SCHEME_TENO5 = 0, 1
+
+
+class scheme:
+    """Context manager selecting the oracle's scheme (TENO7-ext by default;
+    TENO5 is the baseline the paper compares with)."""
+
+    def __init__(self, which: int):
+        self.which = which
+
+    def __enter__(self):
+        self.prev = lib().or_get_scheme()
+        lib().or_set_scheme(self.which)
+        return self
+
+    def __exit__(self, *a):
+        lib().or_set_scheme(self.prev)
+
+
+def coeffs5() -> np.ndarray:
+    out = np.zeros(7 * 5)
+    lib().or_coeffs5(_ptr(out))
+    return out.reshape(7, 5)
+
+
+def select5(bits: int) -> int:
+    return int(lib().or_select5(int(bits)))
 
 
 # ---------------------------------------------------------------- tables ----

@@ -84,6 +84,48 @@ static const char *PATTERN[13] = {
     "0100*", /* f12 */
 };
 
+/* Table co1: the fifth-order TENO scheme (TENO5) written as single
+ * polynomials on f_{i-2} .. f_{i+2}, selected by its own cutoff bits
+ * (delta_0, delta_1, delta_2), rows as printed; (0,0,0) cannot occur. */
+static const char *CO1_KEY[7] = {"111", "011", "110", "001", "010", "100", "101"};
+static const double CO1[7][5] = {
+    {1.0 / 30.0, -13.0 / 60.0, 47.0 / 60.0, 9.0 / 20.0, -1.0 / 20.0},
+    {0.0, -1.0 / 9.0, 2.0 / 3.0, 1.0 / 2.0, -1.0 / 18.0},
+    {1.0 / 21.0, -13.0 / 42.0, 41.0 / 42.0, 2.0 / 7.0, 0.0},
+    {0.0, 0.0, 1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0},
+    {0.0, -1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
+    {1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0},
+    {1.0 / 12.0, -7.0 / 24.0, 17.0 / 24.0, 5.0 / 8.0, -1.0 / 8.0},
+};
+
+/* Scheme switch of the whole oracle: 0 = TENO7-ext (the paper's method),
+ * 1 = TENO5 (the baseline it is compared with). */
+#define SCHEME_TENO7EXT 0
+#define SCHEME_TENO5 1
+static int g_scheme = SCHEME_TENO7EXT;
+void or_set_scheme(int scheme) { g_scheme = scheme; }
+int or_get_scheme(void) { return g_scheme; }
+
+/* Table co1 row for the three cutoff bits d0 | d1<<1 | d2<<2, -1 if none. */
+int or_select5(int bits) {
+    for (int r = 0; r < 7; r++) {
+        int key = (CO1_KEY[r][0] - '0') | ((CO1_KEY[r][1] - '0') << 1) | ((CO1_KEY[r][2] - '0') << 2);
+        if (key == bits) return r;
+    }
+    return -1;
+}
+
+void or_coeffs5(double *out /* 7*5 */) {
+    for (int r = 0; r < 7; r++)
+        for (int t = 0; t < 5; t++) out[r * 5 + t] = CO1[r][t];
+}
+
+static double poly5(int r, const double *v) {
+    double s = 0.0;
+    for (int t = 0; t < 5; t++) s = s + CO1[r][t] * v[t];
+    return s;
+}
+
 void or_coeffs(double *out /* 13*7 */) {
     for (int m = 0; m < 13; m++)
         for (int t = 0; t < 7; t++) out[m * 7 + t] = COEF[m][t];
@@ -179,6 +221,18 @@ int or_teno7_reconstruct(const double *v, int n, int sign, double eps, double CT
         if (d3) d3[j + 2] = (uint8_t)bits[j + 2];
     }
     for (int i = -1; i <= n - 1; i++) {
+        if (g_scheme == SCHEME_TENO5) {
+            int r = or_select5(bits[i + 2]);
+            if (r < 0) {
+                r = 0;
+                status = OR_ENONFINITE;
+            }
+            double vv[5];
+            for (int t = 0; t < 5; t++) vv[t] = (sign > 0) ? c[i - 2 + t] : c[i + 3 - t];
+            fhat[i + 1] = poly5(r, vv);
+            if (D5) D5[i + 1] = (uint8_t)bits[i + 2];
+            continue;
+        }
         int D = (sign > 0) ? pack_delta(bits[i + 1], bits[i + 2], bits[i + 3])
                            : pack_delta(bits[i + 3], bits[i + 2], bits[i + 1]);
         int m = or_select(D);
@@ -391,6 +445,33 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
         frame(S, dir, UL, UR, L, R);
         for (int k = 0; k < m; k++) {
             const int *bp = bits + (0 * m + k) * nf, *bm = bits + (1 * m + k) * nf;
+            if (g_scheme == SCHEME_TENO5) {
+                /* TENO5: the face's own bits select a Table co1 row (no
+                 * neighbour faces); masks report the three-bit code */
+                int rp = or_select5(bp[i + 2]), rm = or_select5(bm[i + 2]);
+                if (rp < 0 || rm < 0) {
+                    status = OR_ENONFINITE;
+                    if (rp < 0) rp = 0;
+                    if (rm < 0) rm = 0;
+                }
+                double vp[5], vm[5];
+                for (int t = 0; t < 5; t++) {
+                    int lp = i - 2 + t + NG, lm = i + 3 - t + NG;
+                    double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
+                    for (int c = 1; c < m; c++) {
+                        sp = sp + L[k][c] * Gp[c * np + lp];
+                        sm = sm + L[k][c] * Gm[c * np + lm];
+                    }
+                    vp[t] = sp;
+                    vm[t] = sm;
+                }
+                f[k] = poly5(rp, vp) + poly5(rm, vm);
+                if (masks) {
+                    masks[(0 * m + k) * (n + 1) + i + 1] = (uint8_t)bp[i + 2];
+                    masks[(1 * m + k) * (n + 1) + i + 1] = (uint8_t)bm[i + 2];
+                }
+                continue;
+            }
             int Dp = pack_delta(bp[i + 1], bp[i + 2], bp[i + 3]);
             int Dm = pack_delta(bm[i + 3], bm[i + 2], bm[i + 1]);
             int mp = or_select(Dp), mm = or_select(Dm);
@@ -471,7 +552,9 @@ int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a
     sysdef S = {sys, nvars_of(sys), gamma, a};
     int m = S.m, np = n + 2 * NG;
     int bad = 0;
-    double eps = (eps_in < 0.0) ? dx * dx * dx : eps_in;
+    /* default epsilon: dx^3 for TENO7-ext (Sec. "The parameter epsilon"),
+     * 1e-40 for TENO5 (as given with Eq. TENO1) */
+    double eps = (eps_in < 0.0) ? (g_scheme == SCHEME_TENO5 ? 1e-40 : dx * dx * dx) : eps_in;
     double alpha = (alpha_in < 0.0) ? alpha_1d(&S, U, n, &bad) : alpha_in;
     if (alpha_out) *alpha_out = alpha;
     double *P[4], *Fh[4];
@@ -594,8 +677,8 @@ int or_rhs_2d(const double *U, int nx, int ny, double dx, double dy, double gamm
         alpha_out[0] = ax;
         alpha_out[1] = ay;
     }
-    double epsx = (eps_x_in < 0.0) ? dx * dx * dx : eps_x_in;
-    double epsy = (eps_y_in < 0.0) ? dy * dy * dy : eps_y_in;
+    double epsx = (eps_x_in < 0.0) ? (g_scheme == SCHEME_TENO5 ? 1e-40 : dx * dx * dx) : eps_x_in;
+    double epsy = (eps_y_in < 0.0) ? (g_scheme == SCHEME_TENO5 ? 1e-40 : dy * dy * dy) : eps_y_in;
     double *P[4], *Fh[4];
     int nmax = nx > ny ? nx : ny;
     for (int c = 0; c < 4; c++) {
