@@ -286,6 +286,31 @@ def bench_adjoint(args, torch, B):
     return out
 
 
+def bench_teno5(args, torch, B, U0, dx, res, dist, world):
+    """The TENO5 baseline (Table co1, five-point polynomials selected by each
+    face's own cutoff bits) on the same workload and kernels: its throughput
+    and the TENO7-ext / TENO5 time ratio per precision -- the measured form of
+    the claim that TENO7-ext costs about as much as TENO5."""
+    n = U0.shape[1]
+    out = {"workload": "same tiled Shu-Osher state and step count as the TENO7-ext lines"}
+    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        if name not in res:
+            continue
+        steps = res[name]["steps"]
+        ctx = B.Context(B.T7_EULER1D, n, dx, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA, scheme=B.T7_TENO5)
+        U = torch.tensor(U0, dtype=dtype, device="cuda")
+        ctx.run(U, CFL, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        ms, _ = time_run(torch, ctx, U, steps, dist, world)
+        out[name] = {"value": n * steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s",
+                     "ms_per_step": ms / steps, "steps": steps,
+                     "teno7ext_over_teno5_time": res[name]["ms_per_step"] / (ms / steps)}
+        ctx.close()
+        del U
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -327,6 +352,7 @@ def main():
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-teno5", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
     ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint"], default=None,
@@ -421,6 +447,7 @@ def main():
         if rank == 0:
             print(json.dumps({"only": args.only, **res[args.only]}), flush=True)
         return 0
+    res5 = None if args.no_teno5 else bench_teno5(args, torch, B, U0, dx, res, dist, world)
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
     resa = None if (args.no_adjoint or rank != 0) else bench_adjoint(args, torch, B)
@@ -462,7 +489,7 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
+        "f64": res["f64"], "teno5": res5, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

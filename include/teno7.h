@@ -55,6 +55,12 @@ typedef enum {
 typedef enum { T7_BC_PERIODIC = 0, T7_BC_ZERO_GRADIENT = 1 /* = transmissive */ } t7_bc;
 typedef enum { T7_F64 = 0, T7_F32 = 1 } t7_prec;
 typedef enum { T7_SCALAR_ADVECTION = 0, T7_EULER1D = 1, T7_EULER2D = 2, T7_BURGERS = 3 } t7_system;
+/* T7_TENO7EXT: the paper's scheme.  T7_TENO5: the fifth-order TENO scheme
+ * it is compared with (Sec. 2, Table co1: each face picks one of seven
+ * five-point polynomials from its own three cutoff bits), provided for the
+ * 1D systems through t7_euler_rhs, t7_cfl_dt, t7_rk3_step, t7_run and
+ * t7_run_host; the other entry points reject a TENO5 context (T7_EINVAL). */
+typedef enum { T7_TENO7EXT = 0, T7_TENO5 = 1 } t7_scheme;
 
 /* Grid and parameters of one problem.  Cell-centred uniform grid with cell
  * widths dx, dy; four ghost cells per side are built inside the kernels from
@@ -63,7 +69,10 @@ typedef enum { T7_SCALAR_ADVECTION = 0, T7_EULER1D = 1, T7_EULER2D = 2, T7_BURGE
  *   adv_speed a in u_t + a u_x = 0 (scalar advection)
  *   CT        cutoff C_T of Eq. seclect (the paper uses 1e-5)
  *   eps_x/y   epsilon of Eq. TENO1; a negative value selects dx^3 (dy^3),
- *             the paper's choice (Sec. "The parameter epsilon").            */
+ *             the paper's choice (Sec. "The parameter epsilon"), or 1e-40
+ *             for TENO5 (the value given with Eq. TENO1).
+ *   scheme    t7_scheme (zero-initialised grids get TENO7-ext).  In FP32,
+ *             TENO5's epsilon is raised to FLT_MIN (1e-40 is subnormal).   */
 typedef struct {
     int sys;  /* t7_system */
     int prec; /* t7_prec   */
@@ -71,6 +80,7 @@ typedef struct {
     double dx, dy;
     int bc[4];
     double gamma, adv_speed, CT, eps_x, eps_y;
+    int scheme; /* t7_scheme */
 } t7_grid;
 
 typedef struct t7_ctx t7_ctx;

@@ -20,6 +20,7 @@ T7_OK, T7_EINVAL, T7_ECUDA, T7_ENONPHYSICAL, T7_ENONFINITE, T7_ETIMEOUT, T7_ENOM
 T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
 T7_F64, T7_F32 = 0, 1
 T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
+T7_TENO7EXT, T7_TENO5 = 0, 1
 
 _STATUS = {0: "T7_OK", -1: "T7_EINVAL", -2: "T7_ECUDA", -3: "T7_ENONPHYSICAL", -4: "T7_ENONFINITE",
            -5: "T7_ETIMEOUT", -6: "T7_ENOMEM"}
@@ -35,7 +36,7 @@ class t7_grid(ctypes.Structure):
     _fields_ = [("sys", ctypes.c_int), ("prec", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("gamma", ctypes.c_double), ("adv_speed", ctypes.c_double), ("CT", ctypes.c_double),
-                ("eps_x", ctypes.c_double), ("eps_y", ctypes.c_double)]
+                ("eps_x", ctypes.c_double), ("eps_y", ctypes.c_double), ("scheme", ctypes.c_int)]
 
 
 _lib = None
@@ -90,7 +91,7 @@ class Context:
 
     def __init__(self, sys: int, nx: int, dx: float, *, prec: int = T7_F64, ny: int = 1, dy: float = 0.0,
                  bc=(T7_BC_PERIODIC,) * 4, gamma: float = 1.4, adv_speed: float = 1.0, CT: float = 1e-5,
-                 eps_x: float = -1.0, eps_y: float = -1.0, stream=None):
+                 eps_x: float = -1.0, eps_y: float = -1.0, scheme: int = 0, stream=None):
         import torch
         self._torch = torch
         self.lib = load()
@@ -99,7 +100,8 @@ class Context:
         self.dtype = torch.float64 if prec == T7_F64 else torch.float32
         self.np_dtype = np.float64 if prec == T7_F64 else np.float32
         bc = tuple(bc) + (T7_BC_PERIODIC,) * (4 - len(bc))
-        g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y)
+        g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y, scheme)
+        self.scheme = scheme
         self.grid = g
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -60,7 +60,10 @@ int nvars(int sys) { return sys == T7_EULER1D ? 3 : (sys == T7_EULER2D ? 4 : 1);
 
 bool is_1d(int sys) { return sys == T7_SCALAR_ADVECTION || sys == T7_EULER1D || sys == T7_BURGERS; }
 
-double eps_of(double eps, double d) { return eps < 0.0 ? d * d * d : eps; }
+// default epsilon: dx^3 for TENO7-ext, 1e-40 for the TENO5 baseline
+double eps_of(double eps, double d, int scheme = T7_TENO7EXT) {
+    return eps < 0.0 ? (scheme == T7_TENO5 ? 1e-40 : d * d * d) : eps;
+}
 
 __global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, double dx, double dy, int max_steps) {
     for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = 0ull;
@@ -87,11 +90,12 @@ t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
     p.bc_lo = c->g.bc[0];
     p.bc_hi = c->g.bc[1];
     p.dx = c->g.dx;
-    p.eps = eps_of(c->g.eps_x, c->g.dx);
+    p.eps = eps_of(c->g.eps_x, c->g.dx, c->g.scheme);
     p.CT = c->g.CT;
     p.gamma = c->g.gamma;
     p.a = c->g.adv_speed;
     p.ctl = c->ctl;
+    p.scheme = c->g.scheme;
     p.f_dx = (float)p.dx;
     p.f_eps = (float)p.eps;
     p.f_CT = (float)p.CT;
@@ -248,6 +252,8 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
         if (g->bc[b] != T7_BC_PERIODIC && g->bc[b] != T7_BC_ZERO_GRADIENT) return T7_EINVAL;
     if ((double)g->nx * (double)g->ny * nvars(g->sys) > 2147483647.0) return T7_EINVAL;
     if (!(g->CT > 0.0 && g->CT < 1.0)) return T7_EINVAL;
+    if (g->scheme != T7_TENO7EXT && g->scheme != T7_TENO5) return T7_EINVAL;
+    if (g->scheme == T7_TENO5 && !is_1d(g->sys)) return T7_EINVAL;  // the baseline runs the 1D systems
     t7_ctx *c = new (std::nothrow) t7_ctx;
     if (!c) return T7_ENOMEM;
     memset(c, 0, sizeof(*c));
@@ -323,6 +329,7 @@ t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double
     if (!c) return T7_EINVAL;
     if (!v || !fhat || n < 1 || (sign != 1 && sign != -1) || !(eps > 0.0))
         return fail(c, T7_EINVAL, "t7_teno7_reconstruct: bad argument");
+    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "t7_teno7_reconstruct: a TENO7-ext context only");
     t7::Recon p;
     p.v = v;
     p.fhat = fhat;
@@ -443,6 +450,7 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
 static t7_status adj_check(t7_ctx *c) {
     if (!c) return T7_EINVAL;
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "the adjoint takes a 1D Euler context");
+    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "the adjoint takes a TENO7-ext context");
     const size_t bytes = c->ncell * c->m * c->esize;
     const size_t mbytes = (size_t)2 * 3 * (c->g.nx + 1);
     for (int k = 0; k < 3; k++) {
@@ -627,6 +635,7 @@ static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, do
 static t7_status batch_check(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes) {
     if (!c) return T7_EINVAL;
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "batches take a 1D Euler context");
+    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "batches take a TENO7-ext context");
     if (!U || !offsets || !dx || ntubes < 1) return fail(c, T7_EINVAL, "batch: bad argument");
     if (offsets[0] != 0 || offsets[ntubes] != (int64_t)c->g.nx)
         return fail(c, T7_EINVAL, "batch: offsets must run from 0 to the context's nx (%d)", c->g.nx);

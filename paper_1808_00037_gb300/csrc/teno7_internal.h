@@ -43,6 +43,7 @@ struct Stage1D {
     int slot_in;     // alpha of Us
     // the same parameters rounded to float, for the FP32 kernels
     float f_dx, f_eps, f_CT, f_gamma, f_gm1, f_a, f_dt_fixed;
+    int scheme;      // 0: TENO7-ext, 1: TENO5 baseline
 };
 
 struct Alpha1D {

@@ -262,6 +262,48 @@ __device__ __forceinline__ T poly_f0(T v0, T v1, T v2, T v3, T v4, T v5, T v6) {
 }
 
 // --------------------------------------------------------------------------
+// TENO5 baseline (the fifth-order TENO scheme the paper measures TENO7-ext
+// against).  A face selects its polynomial from its OWN three cutoff bits --
+// no neighbour faces -- among the seven rows of Table co1, polynomials on
+// f_{i-2} .. f_{i+2} in upwind order.
+// --------------------------------------------------------------------------
+enum { SCH_TENO7EXT = 0, SCH_TENO5 = 1 };
+
+// Table co1 row for the code d0 | d1<<1 | d2<<2 as eight 4-bit entries
+// (7 = no cutoff bit set, which finite data cannot produce).
+constexpr unsigned SEL5 = 0x01632457u;
+__device__ __forceinline__ int sel5(unsigned code) { return (int)((SEL5 >> (4 * (code & 7u))) & 15u); }
+
+// Table co1 coefficients, row-major [7][5]; FP64 entries are the nearest
+// doubles to the printed rationals.
+template <typename T>
+__device__ __forceinline__ T coef5(int idx) {
+    switch (idx) {
+        // clang-format off
+        case 0: return T(1.0/30.0); case 1: return T(-13.0/60.0); case 2: return T(47.0/60.0); case 3: return T(9.0/20.0); case 4: return T(-1.0/20.0);
+        case 5: return T(0); case 6: return T(-1.0/9.0); case 7: return T(2.0/3.0); case 8: return T(1.0/2.0); case 9: return T(-1.0/18.0);
+        case 10: return T(1.0/21.0); case 11: return T(-13.0/42.0); case 12: return T(41.0/42.0); case 13: return T(2.0/7.0); case 14: return T(0);
+        case 15: return T(0); case 16: return T(0); case 17: return T(1.0/3.0); case 18: return T(5.0/6.0); case 19: return T(-1.0/6.0);
+        case 20: return T(0); case 21: return T(-1.0/6.0); case 22: return T(5.0/6.0); case 23: return T(1.0/3.0); case 24: return T(0);
+        case 25: return T(1.0/3.0); case 26: return T(-7.0/6.0); case 27: return T(11.0/6.0); case 28: return T(0); case 29: return T(0);
+        case 30: return T(1.0/12.0); case 31: return T(-7.0/24.0); case 32: return T(17.0/24.0); case 33: return T(5.0/8.0); case 34: return T(-1.0/8.0);
+        default: return T(0);
+        // clang-format on
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T poly5(const T *__restrict__ c, const T v0, const T v1, const T v2, const T v3,
+                                   const T v4) {
+    T s = c[0] * v0;
+    s = s + c[1] * v1;
+    s = s + c[2] * v2;
+    s = s + c[3] * v3;
+    s = s + c[4] * v4;
+    return s;
+}
+
+// --------------------------------------------------------------------------
 // Last-CTA finalization of a launch (see DevCtl).  Called by thread 0 of every
 // CTA after its atomicMax into amax[slot_out].
 //   zero_slot    the slot the next launch accumulates into (cleared here)
@@ -331,7 +373,7 @@ struct TileArgs {
     DevCtl *ctl;
 };
 
-template <typename T, int SYS>
+template <typename T, int SYS, int SCH = SCH_TENO7EXT>
 __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)[WC], T (*sgm)[WC], T (*spr)[WC],
                                      const T *scoef, int tile0, int tstride) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -449,6 +491,10 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
         for (int k = 0; k < M; k++) {
 #pragma unroll
             for (int t = 0; t < 7; t++) {
+                if (SCH == SCH_TENO5 && (t == 0 || t == 6)) {  // five-point stencils
+                    qp[k][t] = qm[k][t] = T(0);
+                    continue;
+                }
                 if (M == 1) {
                     qp[k][t] = sgp[0][lane + t];
                     qm[k][t] = sgm[0][lane + 1 + t];
@@ -469,12 +515,35 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
             word |= bp << (3 * k);
             word |= bm << (3 * (M + k));
         }
-        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
-        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
-
         // ---- selection, polynomial, back-projection ------------------------
         const bool face_out = lane >= 1 && lane <= 30;
         T f[M];
+        if constexpr (SCH == SCH_TENO5) {
+            // TENO5: the face's own code picks a Table co1 row; '+' taps are
+            // cells j-2 .. j+2, '-' taps cells j+3 .. j-1
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const unsigned bp = (word >> (3 * k)) & 7u, bm = (word >> (3 * (M + k))) & 7u;
+                int rp = sel5(bp), rm = sel5(bm);
+                if (rp == 7) {
+                    rp = 0;
+                    if (face_out) flag |= ERR_NOEXIST;
+                }
+                if (rm == 7) {
+                    rm = 0;
+                    if (face_out) flag |= ERR_NOEXIST;
+                }
+                const T fp = poly5(scoef + 5 * rp, qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5]);
+                const T fm = poly5(scoef + 5 * rm, qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1]);
+                f[k] = fp + fm;
+                if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
+                    A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)bp;
+                    A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)bm;
+                }
+            }
+        } else {
+        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
+        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
 #pragma unroll
         for (int k = 0; k < M; k++) {
             const int Dp = pack_delta(wl >> (3 * k), word >> (3 * k), wr >> (3 * k));
@@ -503,6 +572,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                 A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dm;
             }
         }
+        }  // TENO7-ext
         T fh[M];
         if (SYS == SYS_EULER1D) {
             // R columns: eigenvectors of u-c, u, u+c at the Roe state
@@ -569,7 +639,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
 // ==========================================================================
 // Fused 1D stage kernel (grid-wide), SYS in {SYS_ADV, SYS_BURGERS, SYS_EULER1D}.
 // ==========================================================================
-template <typename T, int SYS>
+template <typename T, int SYS, int SCH>
 __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -584,7 +654,11 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     const bool fixed = p.dt_fixed > 0.0;
     if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
+    if (SCH == SCH_TENO5) {
+        for (int q = lane; q < 35; q += 32) s_coef[warp][q] = coef5<T>(q);
+    } else {
+        for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
+    }
 
     TileArgs<T> A;
     if constexpr (sizeof(T) == 8) {
@@ -614,8 +688,8 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     A.ebase = 0;
     A.ctl = ctl;
     __syncwarp();
-    T wsmax = tiles1d<T, SYS>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
-                              blockIdx.x * WPB + warp, gridDim.x * WPB);
+    T wsmax = tiles1d<T, SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
+                                   blockIdx.x * WPB + warp, gridDim.x * WPB);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -741,6 +815,24 @@ __device__ __forceinline__ void fill_delta_table(float (*s_cf)[8]) {
     }
 }
 
+// TENO5 counterpart: row D (only bits 3..1 = d0, d1, d2 are ever set) holds
+// the Table co1 row of the code on taps 1..5 of the seven-tap layout.
+__device__ __forceinline__ void fill_delta_table5(float (*s_cf)[8]) {
+    const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
+    if (row < 32) {
+        const unsigned code = ((row >> 3) & 1) | (((row >> 2) & 1) << 1) | (((row >> 1) & 1) << 2);
+        int r = sel5(code);
+        if (r == 7) r = 0;
+        s_cf[row][t] = (t >= 1 && t <= 5) ? coef5<float>(5 * r + t - 1) : 0.f;
+    }
+}
+
+// Five-bit code of a slot of the FP32 word (bits 3..1 = d0, d1, d2) in the
+// oracle's d0 | d1<<1 | d2<<2 form (TENO5 masks).
+__device__ __forceinline__ unsigned slot_code(unsigned s) {
+    return ((s >> 3) & 1u) | (((s >> 2) & 1u) << 1) | (((s >> 1) & 1u) << 2);
+}
+
 #ifndef T7_F32_MINB
 #define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
 #endif
@@ -750,7 +842,7 @@ __device__ __forceinline__ void fill_delta_table(float (*s_cf)[8]) {
 // tile's staged cells (lane and lane + 32) is loaded one tile ahead, and U^n
 // of the tile's own cells at the start of the tile, so DRAM latency overlaps
 // the face work.
-template <int SYS>
+template <int SYS, int SCH = SCH_TENO7EXT>
 __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*sU)[WC], float (*sgp)[WC],
                                              float (*sgm)[WC], float (*spr)[WC], const float (*s_cf)[8], int tile0,
                                              int tstride) {
@@ -758,7 +850,9 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
     const int lane = threadIdx.x & 31;
     const float alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a;
-    const float eps12 = 12.f * A.eps, CT = A.CT;
+    // (TENO5's epsilon of 1e-40 is below FLT_MIN: raise it to FLT_MIN so that
+    // beta + eps is never flushed to zero by the approximate reciprocal)
+    const float eps12 = SCH == SCH_TENO5 ? fmaxf(12.f * A.eps, 1.17549435e-38f) : 12.f * A.eps, CT = A.CT;
     const float idx = 1.f / A.f_dx;
     const float *Us = A.Us;
     const float *U0 = A.U0;
@@ -827,8 +921,16 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
 #pragma unroll
             for (int k = 0; k < M; k++) {
                 sU[k][c] = U[k];
-                sgp[k][c] = 0.5f * fmaf(alpha, U[k], F[k]);
-                sgm[k][c] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                if (SYS == SYS_ADV) {
+                    // linear flux: (a +- alpha) / 2 is exactly 0 for the
+                    // downwind split (alpha = |a|), so that split is exactly
+                    // zero rather than FMA round-off noise
+                    sgp[k][c] = (0.5f * (a + alpha)) * U[k];
+                    sgm[k][c] = (0.5f * (a - alpha)) * U[k];
+                } else {
+                    sgp[k][c] = 0.5f * fmaf(alpha, U[k], F[k]);
+                    sgm[k][c] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                }
             }
         }
         __syncwarp();
@@ -865,6 +967,11 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         float2 P[M][7];
 #pragma unroll
         for (int t = 0; t < 7; t++) {
+            if (SCH == SCH_TENO5 && (t == 0 || t == 6)) {  // five-point stencils
+#pragma unroll
+                for (int k = 0; k < M; k++) P[k][t] = f2(0.f);
+                continue;
+            }
             float2 g[M];
 #pragma unroll
             for (int c = 0; c < M; c++) g[c] = make_float2(sgp[c][lane + t], sgm[c][lane + 7 - t]);
@@ -887,16 +994,43 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
             cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps12, CT, cp, cm);
             word |= (cp << (5 * k + 1)) | (cm << (5 * (3 + k) + 1));
         }
-        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
-        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
-        const unsigned Dp = ((wl << 1) & SLOT_HI) | (word & SLOT_MID) | ((wr >> 1) & SLOT_LO);
-        const unsigned Dm = ((wr << 1) & SLOT_HI) | (word & SLOT_MID) | ((wl >> 1) & SLOT_LO);
-        const unsigned D = (Dp & SLOT_PLUS) | (Dm & ~SLOT_PLUS);
+        unsigned D;
+        if constexpr (SCH == SCH_TENO5) {
+            D = word;  // TENO5: own bits only
+        } else {
+            const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
+            const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
+            const unsigned Dp = ((wl << 1) & SLOT_HI) | (word & SLOT_MID) | ((wr >> 1) & SLOT_LO);
+            const unsigned Dm = ((wr << 1) & SLOT_HI) | (word & SLOT_MID) | ((wl >> 1) & SLOT_LO);
+            D = (Dp & SLOT_PLUS) | (Dm & ~SLOT_PLUS);
+        }
         const bool face_out = lane >= 1 && lane <= 30;
 
         float f[M];
-        constexpr unsigned ALL_SMOOTH = (M == 3) ? 0x3FFFFFFFu : ((31u) | (31u << 15));
-        if ((D & ALL_SMOOTH) == ALL_SMOOTH) {
+        constexpr unsigned ALL_SMOOTH = SCH == SCH_TENO5 ? ((M == 3) ? SLOT_MID : ((14u) | (14u << 15)))
+                                                         : ((M == 3) ? 0x3FFFFFFFu : ((31u) | (31u << 15)));
+        if (SCH == SCH_TENO5 && (D & ALL_SMOOTH) == ALL_SMOOTH) {
+            // every split of every field selects Table co1's fifth-order row
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                float2 s = __fmul2_rn(f2(1.f / 30.f), P[k][1]);
+                s = __ffma2_rn(f2(-13.f / 60.f), P[k][2], s);
+                s = __ffma2_rn(f2(47.f / 60.f), P[k][3], s);
+                s = __ffma2_rn(f2(9.f / 20.f), P[k][4], s);
+                s = __ffma2_rn(f2(-1.f / 20.f), P[k][5], s);
+                f[k] = s.x + s.y;
+            }
+        } else if (SCH == SCH_TENO5) {
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const float *cp = s_cf[(D >> (5 * k)) & 31u];
+                const float *cm = s_cf[(D >> (5 * (3 + k))) & 31u];
+                float2 s = __fmul2_rn(make_float2(cp[1], cm[1]), P[k][1]);
+#pragma unroll
+                for (int t = 2; t < 6; t++) s = __ffma2_rn(make_float2(cp[t], cm[t]), P[k][t], s);
+                f[k] = s.x + s.y;
+            }
+        } else if ((D & ALL_SMOOTH) == ALL_SMOOTH) {
             // every split of every field selects f0 (the seventh-order polynomial)
 #pragma unroll
             for (int k = 0; k < M; k++) {
@@ -923,8 +1057,9 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
 #pragma unroll
             for (int k = 0; k < M; k++) {
-                A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * k)) & 31u);
-                A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)((D >> (5 * (3 + k))) & 31u);
+                const unsigned sp = (D >> (5 * k)) & 31u, sm = (D >> (5 * (3 + k))) & 31u;
+                A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)(SCH == SCH_TENO5 ? slot_code(sp) : sp);
+                A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)(SCH == SCH_TENO5 ? slot_code(sm) : sm);
             }
         }
         float fh[M];
@@ -975,7 +1110,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     return wsmax;
 }
 
-template <int SYS>
+template <int SYS, int SCH>
 __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -990,7 +1125,10 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     const bool fixed = p.dt_fixed > 0.0;
     if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    fill_delta_table(s_cf);
+    if (SCH == SCH_TENO5)
+        fill_delta_table5(s_cf);
+    else
+        fill_delta_table(s_cf);
     TileArgs<float> A;
     A.alpha = ctl->alpha_f[p.slot_in][0];
     A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
@@ -1014,8 +1152,8 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     A.ebase = 0;
     A.ctl = ctl;
     __syncthreads();
-    float wsmax = tiles1d_f32<SYS>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf, blockIdx.x * WPB + warp,
-                                   gridDim.x * WPB);
+    float wsmax = tiles1d_f32<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
+                                        blockIdx.x * WPB + warp, gridDim.x * WPB);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -1139,22 +1277,43 @@ cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
     const int resident = num_sms() * (sizeof(T) == 4 ? T7_F32_MINB : 1) * 4;  // a few waves of resident CTAs
     int grid = (ntiles + WPB - 1) / WPB;
     if (grid > resident) grid = resident;
+    if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
+    const bool t5 = p.scheme == SCH_TENO5;
     if constexpr (sizeof(T) == 4) {
         switch (p.sys) {
-            case SYS_ADV: stage1d_f32_kernel<SYS_ADV><<<grid, WPB * 32, 0, st>>>(p); break;
-            case SYS_BURGERS: stage1d_f32_kernel<SYS_BURGERS><<<grid, WPB * 32, 0, st>>>(p); break;
-            case SYS_EULER1D: stage1d_f32_kernel<SYS_EULER1D><<<grid, WPB * 32, 0, st>>>(p); break;
+            case SYS_ADV:
+                if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
+            case SYS_BURGERS:
+                if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
+            case SYS_EULER1D:
+                if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
-    }
+    } else {
     switch (p.sys) {
-        case SYS_ADV: stage1d_kernel<T, SYS_ADV><<<grid, WPB * 32, 0, st>>>(p); break;
-        case SYS_BURGERS: stage1d_kernel<T, SYS_BURGERS><<<grid, WPB * 32, 0, st>>>(p); break;
-        case SYS_EULER1D: stage1d_kernel<T, SYS_EULER1D><<<grid, WPB * 32, 0, st>>>(p); break;
+        case SYS_ADV:
+            if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_kernel<T, SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            break;
+        case SYS_BURGERS:
+            if (t5) stage1d_kernel<T, SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_kernel<T, SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            break;
+        case SYS_EULER1D:
+            if (t5) stage1d_kernel<T, SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+    }
 }
 
 template <typename T>

@@ -40,3 +40,38 @@ def test_binding_refuses_missing_library(tmp_path):
     from paper_1808_00037_gb300 import binding
     with pytest.raises(RuntimeError):
         binding.load(tmp_path / "nope.so")
+
+
+def test_grid_struct_layout_matches_header(tmp_path):
+    """The binding's t7_grid has the C struct's size and field offsets (a C
+    program compiled against the header prints them)."""
+    import shutil
+    import subprocess
+    from paper_1808_00037_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in binding.t7_grid._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"teno7.h\"\nint main(void){\n"
+                   "printf(\"%zu\\n\", sizeof(t7_grid));\n"
+                   + "".join(f"printf(\"%zu\\n\", offsetof(t7_grid, {f}));\n" for f in fields) + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(binding.t7_grid)
+    assert out[1:] == [getattr(binding.t7_grid, f).offset for f in fields]
+
+
+def test_create_rejects_bad_scheme_without_touching_the_device():
+    """t7_create validates the grid before any CUDA call: an unknown scheme, and
+    the TENO5 baseline on the 2D system, are refused with T7_EINVAL."""
+    from paper_1808_00037_gb300 import binding as B
+    lib = B.load()
+    bc = (ctypes.c_int * 4)(0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    g = B.t7_grid(B.T7_EULER1D, B.T7_F64, 64, 1, 0.1, 0.0, bc, 1.4, 1.0, 1e-5, -1.0, -1.0, 7)
+    assert lib.t7_create(ctypes.byref(g), None, ctypes.byref(h)) == B.T7_EINVAL
+    g = B.t7_grid(B.T7_EULER2D, B.T7_F64, 64, 64, 0.1, 0.1, bc, 1.4, 1.0, 1e-5, -1.0, -1.0, B.T7_TENO5)
+    assert lib.t7_create(ctypes.byref(g), None, ctypes.byref(h)) == B.T7_EINVAL
+    assert not h.value

@@ -61,3 +61,32 @@ def test_teno5_sod_against_exact():
     Uf7, _, _, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=0.2, cfl=0.6, bc=(1, 1))
     assert oracle.lib().or_get_scheme() == oracle.SCHEME_TENO7EXT
     assert not np.array_equal(Uf, Uf7)
+
+
+def flat_faces(U, bc):
+    """Faces j+1/2, j = -1 .. n-1, whose cells j-2 .. j+3 hold one constant
+    state (ghost cells by the boundary condition)."""
+    P = np.pad(U, ((0, 0), (4, 4)), mode="wrap" if bc[0] == 0 else "edge")
+    n = U.shape[1]
+    flat = np.ones(n + 1, bool)
+    for d in range(-2, 4):  # cell j + d for j = -1 .. n-1 sits at padded index j + d + 4
+        flat &= np.all(P[:, 3 + d:3 + d + n + 1] == P[:, 3:3 + n + 1], axis=0)
+    return flat
+
+
+def test_teno5_decides_on_roundoff_in_constant_states():
+    """On Sod's constant right state TENO5 (epsilon 1e-40) cuts a stencil of
+    one characteristic field: beta_2 is the square of the rounding error of
+    3 w, and against 1e-40 that decides the cutoff.  TENO7-ext's epsilon =
+    dx^3 keeps every stencil on faces whose neighbours are flat too (the
+    motivation for redefining epsilon, Sec. "The parameter epsilon")."""
+    U, dx = I.riemann_tube(1600, *I.SOD)[:2]
+    flat = flat_faces(U, (1, 1))
+    with oracle.scheme(oracle.SCHEME_TENO5):
+        _, _, m5 = oracle.rhs_1d(oracle.SYS_EULER1D, U, dx, bc=(1, 1), want_masks=True)
+    assert np.any(m5[:, :, flat] != 7)
+    _, _, m7 = oracle.rhs_1d(oracle.SYS_EULER1D, U, dx, bc=(1, 1), want_masks=True)
+    inner = np.zeros_like(flat)
+    inner[1:-1] = flat[1:-1] & flat[:-2] & flat[2:]
+    assert inner.sum() > 1500
+    assert np.all(m7[:, :, inner] == 31)
