@@ -55,6 +55,36 @@ def advection_sin3(n: int):
     return (np.sin(np.pi * x) ** 3)[None, :], dx, x
 
 
+def four_wave(n: int = 400):
+    """u3 of Eq. init_LinAdv3 on [-1, 1), periodic: Gaussian, square wave,
+    triangle and half ellipse (Eqs. FG, coof).  The printed intervals lie in
+    [0.2, 1.6], outside the stated domain, and the triangle printed there is
+    negative; they are read as shifted by +1, i.e. the pieces sit on
+    [-0.8, -0.6], [-0.4, -0.2], [0, 0.2] and [0.4, 0.6], with the Gaussian
+    centre z = -0.7 (printed 0.7), the triangle 1 - |10 (x - 0.1)| and the
+    ellipse centre a = 0.5 as printed."""
+    x, dx = cell_centres(-1.0, 1.0, n)
+    z, delta, alpha, a = -0.7, 0.005, 10.0, 0.5
+    beta = np.log(2.0) / (36.0 * delta * delta)
+
+    def G(xx, zz):
+        return np.exp(-beta * (xx - zz) ** 2)
+
+    def F(xx, aa):
+        return np.sqrt(np.maximum(1.0 - alpha * alpha * (xx - aa) ** 2, 0.0))
+
+    u = np.zeros(n)
+    m = (x >= -0.8) & (x <= -0.6)
+    u[m] = (G(x[m], z - delta) + G(x[m], z + delta) + 4.0 * G(x[m], z)) / 6.0
+    m = (x >= -0.4) & (x <= -0.2)
+    u[m] = 1.0
+    m = (x >= 0.0) & (x <= 0.2)
+    u[m] = 1.0 - np.abs(10.0 * (x[m] - 0.1))
+    m = (x >= 0.4) & (x <= 0.6)
+    u[m] = (F(x[m], a - delta) + F(x[m], a + delta) + 4.0 * F(x[m], a)) / 6.0
+    return u[None, :], dx, x
+
+
 def burgers_sine(n: int):
     """u = 1/2 + sin(pi x) on [0, 2) (inviscid Burgers case)."""
     x, dx = cell_centres(0.0, 2.0, n)
