@@ -311,6 +311,41 @@ def bench_teno5(args, torch, B, U0, dx, res, dist, world):
     return out
 
 
+def bench_mixed(args, torch, B, U0, dx, res, dist, world):
+    """Mixed precision (FP64 state, FP32 reconstruction, FP64 flux difference
+    and RK combination) on the same workload: throughput, its speedup over the
+    FP64 path, and the drift of the domain sums over the timed steps with
+    periodic ends (FP64 round-off, against the FP32 state's)."""
+    n = U0.shape[1]
+    steps = args.steps
+    ctx = B.Context(B.T7_EULER1D, n, dx, prec=B.T7_MIXED, bc=(1, 1, 0, 0), gamma=GAMMA)
+    U = torch.tensor(U0, dtype=torch.float64, device="cuda")
+    ctx.run(U, CFL, max_steps=args.warmup)
+    torch.cuda.synchronize()
+    ms, _ = time_run(torch, ctx, U, steps, dist, world)
+    out = {"value": n * steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s", "ms_per_step": ms / steps,
+           "steps": steps, "gpu_launches": 3 * steps + 2}
+    if "f64" in res:
+        out["speedup_vs_f64"] = res["f64"]["ms_per_step"] / (ms / steps)
+    if "f32" in res:
+        out["time_vs_f32"] = (ms / steps) / res["f32"]["ms_per_step"]
+    ctx.close()
+    drift = {}
+    for name, prec, dtype in (("mixed", B.T7_MIXED, torch.float64), ("f32", B.T7_F32, torch.float32)):
+        c = B.Context(B.T7_EULER1D, n, dx, prec=prec, bc=(0, 0, 0, 0), gamma=GAMMA)
+        Ug = torch.tensor(U0, dtype=dtype, device="cuda")
+        s0 = Ug.double().sum(dim=1)
+        c.run(Ug, CFL, max_steps=steps)
+        s1 = Ug.double().sum(dim=1)
+        drift[name] = float(((s1 - s0).abs() / Ug.double().abs().sum(dim=1)).max().item())
+        c.close()
+        del Ug
+    out["periodic_sum_drift"] = {**drift, "steps": steps}
+    del U
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -353,6 +388,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-teno5", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
     ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint"], default=None,
@@ -448,6 +484,7 @@ def main():
             print(json.dumps({"only": args.only, **res[args.only]}), flush=True)
         return 0
     res5 = None if args.no_teno5 else bench_teno5(args, torch, B, U0, dx, res, dist, world)
+    resm = None if args.no_mixed else bench_mixed(args, torch, B, U0, dx, res, dist, world)
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
     resa = None if (args.no_adjoint or rank != 0) else bench_adjoint(args, torch, B)
@@ -456,7 +493,8 @@ def main():
     Ua, dxa = I.shu_osher(N1)
     outs = {}
     for name, prec, dtype in (() if args.no_accuracy else
-                              (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64))):
+                              (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64),
+                               ("mixed", B.T7_MIXED, torch.float64))):
         c = B.Context(B.T7_EULER1D, N1, dxa, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
         Ug = torch.tensor(Ua, dtype=dtype, device="cuda")
         c.run(Ug, CFL, t_end=1.8)
@@ -465,6 +503,8 @@ def main():
         f32 = outs["f32"][1].double().cpu().numpy()
         f64 = outs["f64"][1].double().cpu().numpy()
         acc["f32_vs_f64_rel_l1_rho"] = float(np.abs(f32[0] - f64[0]).sum() / np.abs(f64[0]).sum())
+        mix = outs["mixed"][1].cpu().numpy()
+        acc["mixed_vs_f64_rel_l1_rho"] = float(np.abs(mix[0] - f64[0]).sum() / np.abs(f64[0]).sum())
         # stencil-selection flips: both precisions evaluate L(U) on the same FP64 end state
         _, m64 = outs["f64"][0].euler_rhs(outs["f64"][1], want_masks=True)
         _, m32 = outs["f32"][0].euler_rhs(outs["f64"][1].float(), want_masks=True)
@@ -489,7 +529,7 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "teno5": res5, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
+        "f64": res["f64"], "mixed": resm, "teno5": res5, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

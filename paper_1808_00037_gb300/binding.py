@@ -18,7 +18,7 @@ LIB_PATH = PKG / "libteno7.so"
 
 T7_OK, T7_EINVAL, T7_ECUDA, T7_ENONPHYSICAL, T7_ENONFINITE, T7_ETIMEOUT, T7_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
-T7_F64, T7_F32 = 0, 1
+T7_F64, T7_F32, T7_MIXED = 0, 1, 2
 T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
 T7_TENO7EXT, T7_TENO5 = 0, 1
 
@@ -97,8 +97,8 @@ class Context:
         self.lib = load()
         self.sys, self.prec, self.nx, self.ny = sys, prec, nx, ny
         self.m = {T7_SCALAR_ADVECTION: 1, T7_BURGERS: 1, T7_EULER1D: 3, T7_EULER2D: 4}[sys]
-        self.dtype = torch.float64 if prec == T7_F64 else torch.float32
-        self.np_dtype = np.float64 if prec == T7_F64 else np.float32
+        self.dtype = torch.float32 if prec == T7_F32 else torch.float64  # mixed: FP64 state
+        self.np_dtype = np.float32 if prec == T7_F32 else np.float64
         bc = tuple(bc) + (T7_BC_PERIODIC,) * (4 - len(bc))
         g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y, scheme)
         self.scheme = scheme

@@ -106,6 +106,7 @@ t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
 }
 
 cudaError_t stage(t7_ctx *c, const t7::Stage1D &p) {
+    if (c->g.prec == T7_MIXED) return t7::launch_stage1d_mixed(p, c->stream);
     return c->g.prec == T7_F64 ? t7::launch_stage1d_f64(p, c->stream) : t7::launch_stage1d_f32(p, c->stream);
 }
 
@@ -160,7 +161,8 @@ cudaError_t alpha_launch(t7_ctx *c, const void *U) {
     a.a = c->g.adv_speed;
     a.ctl = c->ctl;
     a.slot = 0;
-    return c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+    // (a mixed-precision state is FP64)
+    return c->g.prec != T7_F32 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
 }
 
 // alpha(U) into slot 0 after clearing all slots
@@ -245,7 +247,8 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     *out = nullptr;
     if (g->sys != T7_SCALAR_ADVECTION && g->sys != T7_EULER1D && g->sys != T7_BURGERS && g->sys != T7_EULER2D)
         return T7_EINVAL;
-    if (g->prec != T7_F64 && g->prec != T7_F32) return T7_EINVAL;
+    if (g->prec != T7_F64 && g->prec != T7_F32 && g->prec != T7_MIXED) return T7_EINVAL;
+    if (g->prec == T7_MIXED && !is_1d(g->sys)) return T7_EINVAL;
     if (g->nx < 1 || g->ny < 1 || (is_1d(g->sys) && g->ny != 1)) return T7_EINVAL;
     if (!(g->dx > 0.0) || (g->sys == T7_EULER2D && !(g->dy > 0.0))) return T7_EINVAL;
     for (int b = 0; b < 4; b++)
@@ -259,7 +262,7 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     memset(c, 0, sizeof(*c));
     c->g = *g;
     c->m = nvars(g->sys);
-    c->esize = g->prec == T7_F64 ? 8 : 4;
+    c->esize = g->prec == T7_F32 ? 4 : 8;
     c->ncell = (size_t)g->nx * g->ny;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
@@ -329,7 +332,8 @@ t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double
     if (!c) return T7_EINVAL;
     if (!v || !fhat || n < 1 || (sign != 1 && sign != -1) || !(eps > 0.0))
         return fail(c, T7_EINVAL, "t7_teno7_reconstruct: bad argument");
-    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "t7_teno7_reconstruct: a TENO7-ext context only");
+    if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
+        return fail(c, T7_EINVAL, "t7_teno7_reconstruct: a TENO7-ext FP64 or FP32 context only");
     t7::Recon p;
     p.v = v;
     p.fhat = fhat;
@@ -450,7 +454,8 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
 static t7_status adj_check(t7_ctx *c) {
     if (!c) return T7_EINVAL;
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "the adjoint takes a 1D Euler context");
-    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "the adjoint takes a TENO7-ext context");
+    if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
+        return fail(c, T7_EINVAL, "the adjoint takes a TENO7-ext FP64 or FP32 context");
     const size_t bytes = c->ncell * c->m * c->esize;
     const size_t mbytes = (size_t)2 * 3 * (c->g.nx + 1);
     for (int k = 0; k < 3; k++) {
@@ -635,7 +640,8 @@ static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, do
 static t7_status batch_check(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes) {
     if (!c) return T7_EINVAL;
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "batches take a 1D Euler context");
-    if (c->g.scheme != T7_TENO7EXT) return fail(c, T7_EINVAL, "batches take a TENO7-ext context");
+    if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
+        return fail(c, T7_EINVAL, "batches take a TENO7-ext FP64 or FP32 context");
     if (!U || !offsets || !dx || ntubes < 1) return fail(c, T7_EINVAL, "batch: bad argument");
     if (offsets[0] != 0 || offsets[ntubes] != (int64_t)c->g.nx)
         return fail(c, T7_EINVAL, "batch: offsets must run from 0 to the context's nx (%d)", c->g.nx);

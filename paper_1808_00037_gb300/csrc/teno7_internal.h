@@ -132,6 +132,7 @@ struct Recon {
 
 cudaError_t launch_stage1d_f64(const Stage1D &p, cudaStream_t s);
 cudaError_t launch_stage1d_f32(const Stage1D &p, cudaStream_t s);
+cudaError_t launch_stage1d_mixed(const Stage1D &p, cudaStream_t s);  // FP64 state, FP32 reconstruction
 cudaError_t launch_alpha1d_f64(const Alpha1D &p, cudaStream_t s);
 cudaError_t launch_alpha1d_f32(const Alpha1D &p, cudaStream_t s);
 cudaError_t launch_recon_f64(const Recon &p, cudaStream_t s);

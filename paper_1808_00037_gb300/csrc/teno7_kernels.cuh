@@ -368,6 +368,7 @@ struct TileArgs {
     double dx;
     float f_dx;
     T alpha, dtT, gamma, gm1, a, eps, CT;
+    double dtD;      // FP64 step (mixed precision: FP64 state, FP32 reconstruction)
     int rhs_mode, stage;
     int ebase;       // added to cell/face indices in error reports
     DevCtl *ctl;
@@ -838,14 +839,19 @@ __device__ __forceinline__ unsigned slot_code(unsigned s) {
 #endif
 
 // FP32 warp-tile sweep (paired splits); same contract as tiles1d.  s_cf is
-// the Delta-indexed coefficient table [32][8].  The raw state of a warp
+// the Delta-indexed coefficient table [32][8].  S is the state type: float,
+// or double for the mixed-precision form, where the state stays FP64, the
+// reconstruction up to the face flux runs in FP32 and the flux difference and
+// the RK combination run in FP64 -- each face flux enters both neighbouring
+// cells as the same FP64 value, so domain sums are conserved to FP64 round-off.  The raw state of a warp
 // tile's staged cells (lane and lane + 32) is loaded one tile ahead, and U^n
 // of the tile's own cells at the start of the tile, so DRAM latency overlaps
 // the face work.
-template <int SYS, int SCH = SCH_TENO7EXT>
+template <int SYS, int SCH = SCH_TENO7EXT, typename S = float>
 __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*sU)[WC], float (*sgp)[WC],
                                              float (*sgm)[WC], float (*spr)[WC], const float (*s_cf)[8], int tile0,
                                              int tstride) {
+    constexpr bool MIXED = sizeof(S) == 8;
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
     const int lane = threadIdx.x & 31;
@@ -854,9 +860,10 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     // beta + eps is never flushed to zero by the approximate reciprocal)
     const float eps12 = SCH == SCH_TENO5 ? fmaxf(12.f * A.eps, 1.17549435e-38f) : 12.f * A.eps, CT = A.CT;
     const float idx = 1.f / A.f_dx;
-    const float *Us = A.Us;
-    const float *U0 = A.U0;
-    float *out = A.out;
+    const S *Us = reinterpret_cast<const S *>(A.Us);
+    const S *U0 = reinterpret_cast<const S *>(A.U0);
+    S *out = reinterpret_cast<S *>(A.out);
+    const double idxD = 1.0 / A.dx, cD = A.dtD * idxD;
     const int n = A.n;
     const size_t cs = A.cs;
     const int ntiles = (n + WT - 1) / WT;
@@ -873,8 +880,8 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (gb < 0 || gb >= n) gb = ghost_map(gb, n, A.bc_lo, A.bc_hi);
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            ua[k] = Us[(size_t)k * cs + ga];
-            ub[k] = (lane < WS - 32) ? Us[(size_t)k * cs + gb] : 0.f;
+            ua[k] = (float)Us[(size_t)k * cs + ga];
+            ub[k] = (lane < WS - 32) ? (float)Us[(size_t)k * cs + gb] : 0.f;
         }
     };
     int tile = tile0;
@@ -883,7 +890,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     for (; tile < ntiles; tile += tstride) {
         const int c0 = tile * WT;
         const int jc = c0 - 2 + lane;  // this lane's cell (if it updates one)
-        float u0r[M];
+        S u0r[M];
         if (!A.rhs_mode && A.stage > 0) {
             const int ic = jc < n ? jc : n - 1;
 #pragma unroll
@@ -1076,7 +1083,33 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
 #pragma unroll
         for (int k = 0; k < M; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
         const int i = j;
-        if (lane >= 2 && lane <= 30 && i < n) {
+        if (MIXED && lane >= 2 && lane <= 30 && i < n) {
+            // FP64 flux difference and RK combination (Shu-Osher form)
+            double o[M];
+            float of[M];
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const double d = (double)fprev[k] - (double)fh[k];
+                if (A.rhs_mode) {
+                    o[k] = d * idxD;
+                } else {
+                    const double v = fma(cD, d, (double)Us[(size_t)k * cs + i]);
+                    if (A.stage == 0)
+                        o[k] = v;
+                    else if (A.stage == 1)
+                        o[k] = fma(0.75, (double)u0r[k], 0.25 * v);
+                    else
+                        o[k] = fma(2.0 / 3.0, v, (1.0 / 3.0) * (double)u0r[k]);
+                }
+                out[(size_t)k * cs + i] = (S)o[k];
+                of[k] = (float)o[k];
+            }
+            if (!A.rhs_mode) {
+                int wflag = 0;
+                wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(of, gm1, gamma, a, &wflag));
+                if (wflag) latch_error(ctl, wflag, A.ebase + i);
+            }
+        } else if (lane >= 2 && lane <= 30 && i < n) {
             float r[M];
 #pragma unroll
             for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
@@ -1091,13 +1124,13 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                     if (A.stage == 0) {
                         o[k] = v;
                     } else if (A.stage == 1) {
-                        o[k] = fmaf(0.75f, u0r[k], 0.25f * v);
+                        o[k] = fmaf(0.75f, (float)u0r[k], 0.25f * v);
                     } else {
                         // u0 + 2/3 (v - u0): float(1/3) + float(2/3) != 1 would
                         // grow the solution by 6e-8 every step
-                        o[k] = fmaf(2.0f / 3.0f, v - u0r[k], u0r[k]);
+                        o[k] = fmaf(2.0f / 3.0f, v - (float)u0r[k], (float)u0r[k]);
                     }
-                    out[(size_t)k * cs + i] = o[k];
+                    out[(size_t)k * cs + i] = (S)o[k];
                 }
                 int wflag = 0;
                 wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(o, gm1, gamma, a, &wflag));
@@ -1110,7 +1143,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     return wsmax;
 }
 
-template <int SYS, int SCH>
+template <int SYS, int SCH, typename S = float>
 __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -1132,6 +1165,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     TileArgs<float> A;
     A.alpha = ctl->alpha_f[p.slot_in][0];
     A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
+    A.dtD = fixed ? p.dt_fixed : ctl->dt;
     A.Us = static_cast<const float *>(p.Us);
     A.U0 = static_cast<const float *>(p.U0);
     A.out = static_cast<float *>(p.out);
@@ -1152,8 +1186,8 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     A.ebase = 0;
     A.ctl = ctl;
     __syncthreads();
-    float wsmax = tiles1d_f32<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
-                                        blockIdx.x * WPB + warp, gridDim.x * WPB);
+    float wsmax = tiles1d_f32<SYS, SCH, S>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
+                                           blockIdx.x * WPB + warp, gridDim.x * WPB);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -1271,48 +1305,60 @@ inline int num_sms() {
     return sms;
 }
 
-template <typename T>
-cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
+// FP32 paired-split stage kernels; S = float (FP32 state) or double (mixed).
+template <typename S>
+cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     const int ntiles = (p.n + WT - 1) / WT;
-    const int resident = num_sms() * (sizeof(T) == 4 ? T7_F32_MINB : 1) * 4;  // a few waves of resident CTAs
+    const int resident = num_sms() * T7_F32_MINB * 4;  // a few waves of resident CTAs
     int grid = (ntiles + WPB - 1) / WPB;
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
-    if constexpr (sizeof(T) == 4) {
-        switch (p.sys) {
-            case SYS_ADV:
-                if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
-                break;
-            case SYS_BURGERS:
-                if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
-                break;
-            case SYS_EULER1D:
-                if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
-                break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    } else {
     switch (p.sys) {
         case SYS_ADV:
-            if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_kernel<T, SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
             break;
         case SYS_BURGERS:
-            if (t5) stage1d_kernel<T, SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_kernel<T, SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
             break;
         case SYS_EULER1D:
-            if (t5) stage1d_kernel<T, SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
             break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        return launch_stage1d_paired<float>(p, st);
+    } else {
+        const int ntiles = (p.n + WT - 1) / WT;
+        const int resident = num_sms() * 4;  // a few waves of resident CTAs
+        int grid = (ntiles + WPB - 1) / WPB;
+        if (grid > resident) grid = resident;
+        if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
+        const bool t5 = p.scheme == SCH_TENO5;
+        switch (p.sys) {
+            case SYS_ADV:
+                if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
+            case SYS_BURGERS:
+                if (t5) stage1d_kernel<T, SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
+            case SYS_EULER1D:
+                if (t5) stage1d_kernel<T, SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
     }
 }
 
