@@ -173,11 +173,13 @@ def cpu_baseline(budget_s=15.0):
 
 def bench_2d(args, torch, B, dist, world, rank):
     """2D Euler, four-quadrant Riemann data on [0,1]^2 at 2048^2 (seed 2024),
-    transmissive boundaries, CFL 0.4: Gcell-steps/s in FP32 and FP64."""
+    transmissive boundaries, CFL 0.4: Gcell-steps/s in FP32, mixed precision
+    (FP64 state and sums) and FP64."""
     n = 2048
     U0, dx, dy, _ = I.quadrants_2d(2024, n, n)
     out = {"workload": "four-quadrant Riemann data, 2048x2048 on [0,1]^2, transmissive, CFL 0.4"}
     for name, prec, dtype, steps in (("f32", B.T7_F32, torch.float32, args.steps_2d),
+                                     ("mixed", B.T7_MIXED, torch.float64, args.steps_2d),
                                      ("f64", B.T7_F64, torch.float64, args.f64_steps_2d)):
         ctx = B.Context(B.T7_EULER2D, n, dx, ny=n, dy=dy, prec=prec, bc=(1, 1, 1, 1), gamma=GAMMA)
         U = torch.tensor(U0, dtype=dtype, device="cuda")
@@ -203,6 +205,8 @@ def bench_2d(args, torch, B, dist, world, rank):
         ctx.close()
         del U
         torch.cuda.empty_cache()
+    for name in ("f32", "mixed"):
+        out[name]["speedup_vs_f64"] = out["f64"]["ms_per_step"] / out[name]["ms_per_step"]
     return out
 
 

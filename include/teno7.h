@@ -56,8 +56,9 @@ typedef enum { T7_BC_PERIODIC = 0, T7_BC_ZERO_GRADIENT = 1 /* = transmissive */ 
 /* T7_MIXED: state arrays in FP64; the reconstruction (frame, projection,
  * smoothness measures, selection, polynomials, face flux) runs in FP32 and the
  * flux difference and RK combination in FP64, so domain sums are conserved
- * to FP64 round-off.  Provided for the 1D systems (t7_euler_rhs, t7_cfl_dt,
- * t7_rk3_step, t7_run, t7_run_host); other entry points return T7_EINVAL. */
+ * to FP64 round-off.  Provided for the 1D and 2D systems (t7_euler_rhs,
+ * t7_cfl_dt, t7_rk3_step, t7_run, t7_run_host); the reconstruction, batch,
+ * adjoint and no-allocation entry points return T7_EINVAL. */
 typedef enum { T7_F64 = 0, T7_F32 = 1, T7_MIXED = 2 } t7_prec;
 typedef enum { T7_SCALAR_ADVECTION = 0, T7_EULER1D = 1, T7_EULER2D = 2, T7_BURGERS = 3 } t7_system;
 /* T7_TENO7EXT: the paper's scheme.  T7_TENO5: the fifth-order TENO scheme

@@ -138,6 +138,7 @@ t7::Stage2D stage2d_params(t7_ctx *c, const void *Us, const void *U0, void *out,
 }
 
 cudaError_t stage2d(t7_ctx *c, const t7::Stage2D &p) {
+    if (c->g.prec == T7_MIXED) return t7::launch_stage2d_mixed(p, c->stream);
     return c->g.prec == T7_F64 ? t7::launch_stage2d_f64(p, c->stream) : t7::launch_stage2d_f32(p, c->stream);
 }
 
@@ -151,7 +152,7 @@ cudaError_t alpha_launch(t7_ctx *c, const void *U) {
         a.gamma = c->g.gamma;
         a.ctl = c->ctl;
         a.slot = 0;
-        return c->g.prec == T7_F64 ? t7::launch_alpha2d_f64(a, c->stream) : t7::launch_alpha2d_f32(a, c->stream);
+        return c->g.prec != T7_F32 ? t7::launch_alpha2d_f64(a, c->stream) : t7::launch_alpha2d_f32(a, c->stream);
     }
     t7::Alpha1D a;
     a.U = U;
@@ -248,7 +249,6 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     if (g->sys != T7_SCALAR_ADVECTION && g->sys != T7_EULER1D && g->sys != T7_BURGERS && g->sys != T7_EULER2D)
         return T7_EINVAL;
     if (g->prec != T7_F64 && g->prec != T7_F32 && g->prec != T7_MIXED) return T7_EINVAL;
-    if (g->prec == T7_MIXED && !is_1d(g->sys)) return T7_EINVAL;
     if (g->nx < 1 || g->ny < 1 || (is_1d(g->sys) && g->ny != 1)) return T7_EINVAL;
     if (!(g->dx > 0.0) || (g->sys == T7_EULER2D && !(g->dy > 0.0))) return T7_EINVAL;
     for (int b = 0; b < 4; b++)

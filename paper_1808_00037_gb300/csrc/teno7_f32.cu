@@ -9,6 +9,7 @@ cudaError_t launch_stage1d_mixed(const Stage1D &p, cudaStream_t s) { return laun
 cudaError_t launch_alpha1d_f32(const Alpha1D &p, cudaStream_t s) { return launch_alpha1d<float>(p, s); }
 cudaError_t launch_recon_f32(const Recon &p, cudaStream_t s) { return launch_recon<float>(p, s); }
 cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s) { return launch_stage2d<float>(p, s); }
+cudaError_t launch_stage2d_mixed(const Stage2D &p, cudaStream_t s) { return launch_stage2d_paired<double>(p, s); }
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s) { return launch_alpha2d<float>(p, s); }
 cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s) { return launch_batch1d<float>(p, s); }
 cudaError_t launch_rhs_adjoint1d_f32(const Adjoint1D &p, cudaStream_t s) { return launch_rhs_adjoint1d<float>(p, s); }

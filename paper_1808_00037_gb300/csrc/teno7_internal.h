@@ -82,6 +82,7 @@ struct Alpha2D {
 
 cudaError_t launch_stage2d_f64(const Stage2D &p, cudaStream_t s);
 cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_stage2d_mixed(const Stage2D &p, cudaStream_t s);  // FP64 state, FP32 reconstruction
 cudaError_t launch_alpha2d_f64(const Alpha2D &p, cudaStream_t s);
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s);
 

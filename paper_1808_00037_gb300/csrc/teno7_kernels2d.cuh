@@ -478,8 +478,462 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const Alpha2D p) {
     }
 }
 
+// ==========================================================================
+// FP32 2D sweeps with paired splits (the 1D FP32 kernel's design, 4 fields).
+// S is the state type: float, or double for the mixed-precision form (FP64
+// state and x-part R, exact FP64 flux differences and RK combination).
+//
+// Per face the split fluxes of the 8 stencil cells are held in registers as
+// pairs g[c][t] = (G+_c at cell j-3+t, G-_c at cell j+4-t); the four
+// characteristic fields are then processed one at a time -- projection
+// P_k[t] = sum_c L_kc g[c][t], cutoff codes, neighbour codes by shuffle,
+// Delta, polynomial -- so that only one field's 7 pairs are live at once and
+// the kernels fit two CTAs per SM.
+// ==========================================================================
+
+// Prims (normal velocity, tangential velocity, H, sqrt(rho)) and split fluxes
+// of one cell along DIR, FP32.
+template <int DIR>
+__device__ __forceinline__ void cell2d_f32(const float U[4], float gm1, float alpha, float pr[4], float gp[4],
+                                           float gm[4]) {
+    const float ri = rcp_approx(U[0]);
+    const float u = U[1] * ri, v = U[2] * ri;
+    const float p = gm1 * (U[3] - 0.5f * (U[1] * u + U[2] * v));
+    float F[4];
+    if (DIR == 0) {
+        F[0] = U[1];
+        F[1] = U[1] * u + p;
+        F[2] = U[2] * u;
+        F[3] = u * (U[3] + p);
+        pr[0] = u;
+        pr[1] = v;
+    } else {
+        F[0] = U[2];
+        F[1] = U[1] * v;
+        F[2] = U[2] * v + p;
+        F[3] = v * (U[3] + p);
+        pr[0] = v;
+        pr[1] = u;
+    }
+    pr[2] = (U[3] + p) * ri;
+    pr[3] = U[0] * rsqrtf(U[0]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        gp[k] = 0.5f * fmaf(alpha, U[k], F[k]);
+        gm[k] = 0.5f * fmaf(-alpha, U[k], F[k]);
+    }
+}
+
+// One face along DIR: frame, per-field projection / cutoff / Delta / polynomial,
+// back-projection to the physical face flux fh[4].  pr(q, i), gp(c, i),
+// gm(c, i) read staged index i (face j+1/2 <-> cells j-3+t at index lane+t).
+// codes_p / codes_m receive the four fields' Delta codes (5 bits each).
+template <int DIR, typename PR, typename GP, typename GM>
+__device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsigned &codes_m, int &flag, PR pr,
+                                           GP gp, GM gm, const float (*s_cf)[8], float eps12, float CT, float gm1,
+                                           int lane) {
+    const float unl = pr(0, lane + 3), unr = pr(0, lane + 4), vtl = pr(1, lane + 3), vtr = pr(1, lane + 4);
+    const float Hl = pr(2, lane + 3), Hr = pr(2, lane + 4), sl = pr(3, lane + 3), sr = pr(3, lane + 4);
+    const float w = rcp_approx(sl + sr);
+    const float un = (sl * unl + sr * unr) * w;
+    const float vt = (sl * vtl + sr * vtr) * w;
+    const float Ht = (sl * Hl + sr * Hr) * w;
+    const float q2 = 0.5f * (un * un + vt * vt);
+    const float c2 = gm1 * (Ht - q2);
+    const float rc = rsqrtf(c2);
+    const float c = c2 * rc;
+    const float b1 = gm1 * (rc * rc), b2 = q2 * b1, uc = un * rc;
+    if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+    // rows of L in the rotated component order (rho, normal, tangential, E);
+    // row 2 (shear) is (-vt, 0, 1, 0)
+    const float L0[4] = {0.5f * (b2 + uc), -0.5f * (b1 * un + rc), -0.5f * (b1 * vt), 0.5f * b1};
+    const float L1[4] = {1.f - b2, b1 * un, b1 * vt, -b1};
+    const float L3[4] = {0.5f * (b2 - uc), -0.5f * (b1 * un - rc), -0.5f * (b1 * vt), 0.5f * b1};
+    constexpr int CN = rot<DIR>(1), CT_ = rot<DIR>(2);  // physical index of the normal / tangential momentum
+    float2 g[4][7];
+#pragma unroll
+    for (int t = 0; t < 7; t++)
+#pragma unroll
+        for (int cc = 0; cc < 4; cc++) g[cc][t] = make_float2(gp(cc, lane + t), gm(cc, lane + 7 - t));
+    float f[4];
+    codes_p = 0;
+    codes_m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float2 P[7];
+        if (k == 2) {
+#pragma unroll
+            for (int t = 0; t < 7; t++) P[t] = __ffma2_rn(f2(-vt), g[0][t], g[CT_][t]);
+        } else {
+            const float *Lk = k == 0 ? L0 : (k == 1 ? L1 : L3);
+            // Lk is in rotated order: physical component cc takes Lk[rot(cc)]
+            const float2 l0 = f2(Lk[0]), ln = f2(Lk[1]), lt = f2(Lk[2]), le = f2(Lk[3]);
+#pragma unroll
+            for (int t = 0; t < 7; t++) {
+                float2 q = __fmul2_rn(l0, g[0][t]);
+                q = __ffma2_rn(ln, g[CN][t], q);
+                q = __ffma2_rn(lt, g[CT_][t], q);
+                P[t] = __ffma2_rn(le, g[3][t], q);
+            }
+        }
+        unsigned cp, cm;
+        cutoff2(P[1], P[2], P[3], P[4], P[5], eps12, CT, cp, cm);
+        const unsigned word = (cp << 1) | (cm << 6);
+        const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
+        const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
+        const unsigned dp = ((wl << 1) & 0x10u) | (word & 0x0Eu) | ((wr >> 1) & 0x01u);
+        const unsigned dm = (((wr << 1) & 0x200u) | (word & 0x1C0u) | ((wl >> 1) & 0x20u)) >> 5;
+        codes_p |= dp << (5 * k);
+        codes_m |= dm << (5 * k);
+        float2 s;
+        if (dp == 31u && dm == 31u) {
+            s = __fmul2_rn(f2(-1.f / 140.f), P[0]);
+            s = __ffma2_rn(f2(5.f / 84.f), P[1], s);
+            s = __ffma2_rn(f2(-101.f / 420.f), P[2], s);
+            s = __ffma2_rn(f2(319.f / 420.f), P[3], s);
+            s = __ffma2_rn(f2(107.f / 210.f), P[4], s);
+            s = __ffma2_rn(f2(-19.f / 210.f), P[5], s);
+            s = __ffma2_rn(f2(1.f / 105.f), P[6], s);
+        } else {
+            const float *cpp = s_cf[dp];
+            const float *cmm = s_cf[dm];
+            s = __fmul2_rn(make_float2(cpp[0], cmm[0]), P[0]);
+#pragma unroll
+            for (int t = 1; t < 7; t++) s = __ffma2_rn(make_float2(cpp[t], cmm[t]), P[t], s);
+        }
+        f[k] = s.x + s.y;
+    }
+    // back-projection: rotated rows (rho, normal, tangential, E) of R
+    const float Fr0 = f[0] + f[1] + f[3];
+    const float Fr1 = (un - c) * f[0] + un * f[1] + (un + c) * f[3];
+    const float Fr2 = vt * (f[0] + f[1] + f[3]) + f[2];
+    const float Fr3 = (Ht - un * c) * f[0] + q2 * f[1] + vt * f[2] + (Ht + un * c) * f[3];
+    fh[0] = Fr0;
+    fh[CN] = Fr1;
+    fh[CT_] = Fr2;
+    fh[3] = Fr3;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D p) {
+    constexpr bool MIXED = sizeof(S) == 8;
+    __shared__ float s_gp[WPB][4][WC];
+    __shared__ float s_gm[WPB][4][WC];
+    __shared__ float s_pr[WPB][4][WC];
+    __shared__ __align__(16) float s_cf[32][8];
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    fill_delta_table(s_cf);
+    const float alpha = ctl->alpha_f[p.slot_in][0];
+    const float gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_x, CT = p.f_CT;
+    const float idx = 1.f / p.f_dx;
+    const double idxD = 1.0 / p.dx;
+    const S *Us = static_cast<const S *>(p.Us);
+    S *R = static_cast<S *>(p.R);
+    const int nx = p.nx, ny = p.ny;
+    const size_t N = (size_t)nx * ny;
+    const int ntx = (nx + WT - 1) / WT;
+    const long ntiles = (long)ntx * ny;
+    float (*sgp)[WC] = s_gp[warp];
+    float (*sgm)[WC] = s_gm[warp];
+    float (*spr)[WC] = s_pr[warp];
+    __syncthreads();
+    float ua[4], ub[4];
+    auto load_tile = [&](long tile) {
+        const int y = (int)(tile / ntx);
+        const int c0 = (int)(tile % ntx) * WT;
+        const S *row = Us + (size_t)y * nx;
+        int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
+        if (ga < 0 || ga >= nx) ga = ghost_map(ga, nx, p.bc[0], p.bc[1]);
+        if (gb < 0 || gb >= nx) gb = ghost_map(gb, nx, p.bc[0], p.bc[1]);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            ua[k] = (float)row[(size_t)k * N + ga];
+            ub[k] = (lane < WS - 32) ? (float)row[(size_t)k * N + gb] : 0.f;
+        }
+    };
+    const long tstride = (long)gridDim.x * WPB;
+    long tile = (long)blockIdx.x * WPB + warp;
+    if (tile < ntiles) load_tile(tile);
+    for (; tile < ntiles; tile += tstride) {
+        const int y = (int)(tile / ntx);
+        const int c0 = (int)(tile % ntx) * WT;
+        float cur[2][4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            cur[0][k] = ua[k];
+            cur[1][k] = ub[k];
+        }
+        if (tile + tstride < ntiles) load_tile(tile + tstride);
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int c = lane + 32 * r;
+            if (c >= WS) break;
+            float pr[4], gp[4], gm[4];
+            cell2d_f32<0>(cur[r], gm1, alpha, pr, gp, gm);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                spr[k][c] = pr[k];
+                sgp[k][c] = gp[k];
+                sgm[k][c] = gm[k];
+            }
+        }
+        __syncwarp();
+        const int j = c0 - 2 + lane;
+        float fh[4];
+        unsigned cpk, cmk;
+        int flag = 0;
+        face2d_f32<0>(
+            fh, cpk, cmk, flag, [&](int q, int i) { return spr[q][i]; }, [&](int cc, int i) { return sgp[cc][i]; },
+            [&](int cc, int i) { return sgm[cc][i]; }, s_cf, eps12, CT, gm1, lane);
+        const bool face_out = lane >= 1 && lane <= 30;
+        if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= nx - 1) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                p.masks[((size_t)k * ny + y) * (nx + 1) + (j + 1)] = (uint8_t)((cpk >> (5 * k)) & 31u);
+                p.masks[((size_t)(4 + k) * ny + y) * (nx + 1) + (j + 1)] = (uint8_t)((cmk >> (5 * k)) & 31u);
+            }
+        }
+        if (flag && face_out && j >= -2 && j <= nx) latch_error(ctl, flag, j);
+        float fprev[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
+        if (lane >= 2 && lane <= 30 && j < nx) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if constexpr (MIXED)
+                    R[(size_t)k * N + (size_t)y * nx + j] = ((double)fprev[k] - (double)fh[k]) * idxD;
+                else
+                    R[(size_t)k * N + (size_t)y * nx + j] = (fprev[k] - fh[k]) * idx;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename S>
+constexpr size_t ysweep_f32_smem_bytes() {
+    return sizeof(float) * (3 * 4 * YB_STAGE * YB_LD) + sizeof(S) * (4 * YB_ROWS * YB_LD) +
+           sizeof(float) * (32 * 8 + 2 * WPB);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D p) {
+    constexpr bool MIXED = sizeof(S) == 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S *s_ry = reinterpret_cast<S *>(smem_raw);                                    // [4][29][33]
+    float *s_gp = reinterpret_cast<float *>(smem_raw + sizeof(S) * 4 * YB_ROWS * YB_LD);  // [4][39][33]
+    float *s_gm = s_gp + 4 * YB_STAGE * YB_LD;
+    float *s_pr = s_gm + 4 * YB_STAGE * YB_LD;
+    float(*s_cf)[8] = reinterpret_cast<float(*)[8]>(s_pr + 4 * YB_STAGE * YB_LD);  // [32][8]
+    float *s_red = reinterpret_cast<float *>(s_cf + 32);                           // [2][WPB]
+    auto at = [](const float *base, int c, int r, int col) -> float {
+        return base[(c * YB_STAGE + r) * YB_LD + col];
+    };
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = p.nx, ny = p.ny;
+    const size_t N = (size_t)nx * ny;
+    const int x0 = blockIdx.x * YB_COLS, r0 = blockIdx.y * YB_ROWS;
+    const float alpha = ctl->alpha_f[p.slot_in][1];
+    const float gamma = p.f_gamma, gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_y, CT = p.f_CT;
+    const S *Us = static_cast<const S *>(p.Us);
+    fill_delta_table(s_cf);
+
+    // ---- stage rows r0-5 .. r0+33 of columns x0 .. x0+31 (coalesced along x);
+    // all of a thread's loads are issued before any is used
+    constexpr int NSTG = (YB_STAGE * YB_COLS + WPB * 32 - 1) / (WPB * 32);
+    float Ust[NSTG][4];
+#pragma unroll
+    for (int sI = 0; sI < NSTG; sI++) {
+        const int q = tid + sI * WPB * 32;
+        const int r = q / YB_COLS, x = x0 + q % YB_COLS;
+        if (q < YB_STAGE * YB_COLS && x < nx) {
+            int y = r0 - 5 + r;
+            if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) Ust[sI][k] = (float)Us[(size_t)k * N + (size_t)y * nx + x];
+        }
+    }
+#pragma unroll
+    for (int sI = 0; sI < NSTG; sI++) {
+        const int q = tid + sI * WPB * 32;
+        const int r = q / YB_COLS, col = q % YB_COLS;
+        if (q < YB_STAGE * YB_COLS && x0 + col < nx) {
+            float pr[4], gp[4], gm[4];
+            cell2d_f32<1>(Ust[sI], gm1, alpha, pr, gp, gm);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                s_pr[(k * YB_STAGE + r) * YB_LD + col] = pr[k];
+                s_gp[(k * YB_STAGE + r) * YB_LD + col] = gp[k];
+                s_gm[(k * YB_STAGE + r) * YB_LD + col] = gm[k];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- faces down the columns: warp w takes columns w, w+8, w+16, w+24
+    const float idy = 1.f / p.f_dy;
+    const double idyD = 1.0 / p.dy;
+    for (int col = warp; col < YB_COLS; col += WPB) {
+        const int x = x0 + col;
+        if (x >= nx) break;
+        const int j = r0 - 2 + lane;
+        float fh[4];
+        unsigned cpk, cmk;
+        int flag = 0;
+        face2d_f32<1>(
+            fh, cpk, cmk, flag, [&](int q, int i) { return at(s_pr, q, i, col); },
+            [&](int cc, int i) { return at(s_gp, cc, i, col); }, [&](int cc, int i) { return at(s_gm, cc, i, col); },
+            s_cf, eps12, CT, gm1, lane);
+        const bool face_out = lane >= 1 && lane <= 30;
+        if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= ny - 1) {
+            uint8_t *ym = p.masks + (size_t)8 * ny * (nx + 1);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                ym[((size_t)k * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)((cpk >> (5 * k)) & 31u);
+                ym[((size_t)(4 + k) * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)((cmk >> (5 * k)) & 31u);
+            }
+        }
+        if (flag && face_out && j >= -2 && j <= ny) latch_error(ctl, flag, j);
+        float fprev[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
+        if (lane >= 2 && lane <= 30) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if constexpr (MIXED)
+                    s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = ((double)fprev[k] - (double)fh[k]) * idyD;
+                else
+                    s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = (fprev[k] - fh[k]) * idy;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- L = Lx + Ly, RK stage, wavespeeds (row-major, coalesced) -----------
+    const S *R = static_cast<const S *>(p.R);
+    const S *U0 = static_cast<const S *>(p.U0);
+    S *out = static_cast<S *>(p.out);
+    const float dtF = p.rhs_mode ? 0.f : (fixed ? p.f_dt_fixed : ctl->dt_f);
+    const double dtD = p.rhs_mode ? 0.0 : (fixed ? p.dt_fixed : ctl->dt);
+    float mx = 0.f, my = 0.f;
+    // EB cells per thread at a time, their loads issued before any is used
+    constexpr int EB = MIXED ? 2 : 4;
+    const bool use_u0 = !p.rhs_mode && p.stage > 0;
+    for (int q0 = tid; q0 < YB_ROWS * YB_COLS; q0 += EB * WPB * 32) {
+        S Rv[EB][4], Uv[EB][4], U0v[EB][4];
+#pragma unroll
+        for (int e = 0; e < EB; e++) {
+            const int q = q0 + e * WPB * 32;
+            const int r = q / YB_COLS, x = x0 + q % YB_COLS, y = r0 + r;
+            if (q < YB_ROWS * YB_COLS && x < nx && y < ny) {
+                const size_t gi = (size_t)y * nx + x;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    Rv[e][k] = R[(size_t)k * N + gi];
+                    Uv[e][k] = p.rhs_mode ? S(0) : Us[(size_t)k * N + gi];
+                    U0v[e][k] = use_u0 ? U0[(size_t)k * N + gi] : S(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < EB; e++) {
+            const int q = q0 + e * WPB * 32;
+            const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col, y = r0 + r;
+            if (!(q < YB_ROWS * YB_COLS && x < nx && y < ny)) continue;
+            const size_t gi = (size_t)y * nx + x;
+            float of[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const S rr = Rv[e][k] + s_ry[(k * YB_ROWS + r) * YB_LD + col];
+                if (p.rhs_mode) {
+                    out[(size_t)k * N + gi] = rr;
+                    continue;
+                }
+                S o;
+                if constexpr (MIXED) {
+                    const double v = fma(dtD, (double)rr, (double)Uv[e][k]);
+                    if (p.stage == 0)
+                        o = v;
+                    else if (p.stage == 1)
+                        o = fma(0.75, (double)U0v[e][k], 0.25 * v);
+                    else
+                        o = fma(2.0 / 3.0, v, (1.0 / 3.0) * (double)U0v[e][k]);
+                } else {
+                    const float v = fmaf(dtF, (float)rr, (float)Uv[e][k]);
+                    if (p.stage == 0) {
+                        o = v;
+                    } else if (p.stage == 1) {
+                        o = fmaf(0.75f, (float)U0v[e][k], 0.25f * v);
+                    } else {
+                        const float u0 = (float)U0v[e][k];
+                        o = fmaf(2.0f / 3.0f, v - u0, u0);
+                    }
+                }
+                out[(size_t)k * N + gi] = o;
+                of[k] = (float)o;
+            }
+            if (!p.rhs_mode) {
+                int wflag = 0;
+                float sx, sy;
+                wavespeed2d<float>(of, gm1, gamma, sx, sy, &wflag);
+                if (wflag) latch_error(ctl, wflag, (int)gi);
+                mx = fmaxf(mx, sx);
+                my = fmaxf(my, sy);
+            }
+        }
+    }
+    if (!p.rhs_mode) {
+        mx = warp_max(mx);
+        my = warp_max(my);
+        if (lane == 0) {
+            s_red[warp] = mx;
+            s_red[WPB + warp] = my;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float vx = s_red[0], vy = s_red[WPB];
+            for (int w = 1; w < WPB; w++) {
+                vx = fmaxf(vx, s_red[w]);
+                vy = fmaxf(vy, s_red[WPB + w]);
+            }
+            const int so = (p.stage + 1) % 3;
+            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)vx));
+            atomicMax(&ctl->amax[so][1], (unsigned long long)__double_as_longlong((double)vy));
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true);
+        }
+    }
+}
+
+template <typename S>
+cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
+    const int ntx = (p.nx + WT - 1) / WT;
+    long ntiles = (long)ntx * p.ny;
+    long gx = (ntiles + WPB - 1) / WPB;
+    const long cap = (long)num_sms() * 2 * 4;
+    if (gx > cap) gx = cap;
+    xsweep2d_f32_kernel<S><<<(int)gx, WPB * 32, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = ysweep_f32_smem_bytes<S>();
+    e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
+    ysweep2d_f32_kernel<S><<<grid, WPB * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_stage2d(const Stage2D &p, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        return launch_stage2d_paired<float>(p, st);
+    } else {
     const int ntx = (p.nx + WT - 1) / WT;
     long ntiles = (long)ntx * p.ny;
     long gx = (ntiles + WPB - 1) / WPB;
@@ -494,6 +948,7 @@ cudaError_t launch_stage2d(const Stage2D &p, cudaStream_t st) {
     dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
     ysweep2d_kernel<T><<<grid, WPB * 32, smem, st>>>(p);
     return cudaGetLastError();
+    }
 }
 
 template <typename T>

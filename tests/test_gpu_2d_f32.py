@@ -1,0 +1,136 @@
+"""FP32 and mixed-precision 2D sweeps (paired splits, one field at a time)
+against the FP64 oracle, and the mixed form against the FP32 form.
+
+* FP32 RHS: Delta codes of both sweeps agree with the oracle on >= 99.9% of
+  entries; where every face of a cell agrees the RHS is within the FP32
+  rounding of the face fluxes amplified by the differences,
+  64 * 2^-24 * (max|F|/dx + max|G|/dy).
+* Mixed: the reconstruction is the FP32 one (codes identical on a
+  float-representable state, RHS within the FP32 bound of it), the face
+  fluxes enter both neighbours as one FP64 value, so periodic domain sums are
+  conserved to FP64 round-off; runs stay within the FP32 bounds of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_00037_gb300 import binding as B
+from paper_1808_00037_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ZG = (B.T7_BC_ZERO_GRADIENT,) * 4
+PER = (B.T7_BC_PERIODIC,) * 4
+
+
+def ctx(nx, ny, dx, dy, prec, bc):
+    return B.Context(B.T7_EULER2D, nx, dx, ny=ny, dy=dy, prec=prec, bc=bc)
+
+
+def case(name, nx, ny):
+    if name == "quadrants":
+        U, dx, dy, _ = I.quadrants_2d(4, nx, ny)
+        return U, dx, dy, ZG
+    U, dx, dy = I.random_smooth_2d(6, nx, ny)
+    return U, dx, dy, PER
+
+
+def flux_bound(U, dx, dy):
+    rho, u, v = U[0], U[1] / U[0], U[2] / U[0]
+    p = 0.4 * (U[3] - 0.5 * (U[1] * u + U[2] * v))
+    F = np.stack([U[1], U[1] * u + p, U[2] * u, u * (U[3] + p)])
+    G = np.stack([U[2], U[1] * v, U[2] * v + p, v * (U[3] + p)])
+    return 64 * 2.0**-24 * (np.abs(F).max() / dx + np.abs(G).max() / dy)
+
+
+@pytest.mark.parametrize("name", ["quadrants", "smooth"])
+@pytest.mark.parametrize("nx,ny", [(5, 7), (61, 37), (96, 64)])
+def test_rhs_2d_f32_against_oracle(name, nx, ny):
+    U, dx, dy, bc = case(name, nx, ny)
+    ro, _, (mxo, myo) = oracle.rhs_2d(U, dx, dy, bc=bc, want_masks=True)
+    c = ctx(nx, ny, dx, dy, B.T7_F32, bc)
+    rg, (mxg, myg) = c.euler_rhs(torch.tensor(U, dtype=torch.float32, device="cuda"), want_masks=True)
+    c.sync()
+    mxg, myg = mxg.cpu().numpy(), myg.cpu().numpy()
+    assert (mxg == mxo).mean() >= 0.999 and (myg == myo).mean() >= 0.999
+    okx = np.all(mxg == mxo, axis=(0, 1))  # [ny, nx+1]
+    oky = np.all(myg == myo, axis=(0, 1))  # [nx, ny+1]
+    cell_ok = okx[:, :-1] & okx[:, 1:] & (oky[:, :-1] & oky[:, 1:]).T
+    err = np.abs(rg.double().cpu().numpy() - ro)[:, cell_ok]
+    assert np.max(err) <= flux_bound(U, dx, dy)
+
+
+@pytest.mark.parametrize("name", ["quadrants", "smooth"])
+def test_rhs_2d_mixed_reconstruction_is_the_fp32_one(name):
+    nx, ny = 96, 64
+    U, dx, dy, bc = case(name, nx, ny)
+    Uf = U.astype(np.float32).astype(np.float64)
+    cm = ctx(nx, ny, dx, dy, B.T7_MIXED, bc)
+    c32 = ctx(nx, ny, dx, dy, B.T7_F32, bc)
+    rm, (mxm, mym) = cm.euler_rhs(torch.tensor(Uf, device="cuda"), want_masks=True)
+    r32, (mx32, my32) = c32.euler_rhs(torch.tensor(Uf, dtype=torch.float32, device="cuda"), want_masks=True)
+    torch.cuda.synchronize()
+    assert torch.equal(mxm, mx32) and torch.equal(mym, my32)
+    # the mixed form takes alpha from the FP64 state in FP64, the FP32 form in
+    # FP32: the split fluxes differ at FP32 rounding level, so the RHS agree to
+    # the FP32 bound, not bit for bit
+    assert float((rm - r32.double()).abs().max()) <= flux_bound(Uf, dx, dy)
+
+
+def test_2d_mixed_conserves_to_fp64_roundoff():
+    U, dx, dy, _ = I.quadrants_2d(5, 128, 96)
+    c = ctx(128, 96, dx, dy, B.T7_MIXED, PER)
+    Ug = torch.tensor(U, device="cuda")
+    s0 = Ug.sum(dim=(1, 2))
+    steps, _ = c.run(Ug, 0.4, max_steps=5)
+    assert steps == 5
+    s1 = Ug.sum(dim=(1, 2))
+    assert torch.all(torch.abs(s1 - s0) <= 1e-13 * torch.abs(Ug).sum(dim=(1, 2))), (s0, s1)
+
+
+def test_2d_mixed_runs_against_oracle():
+    U, dx, dy = I.random_smooth_2d(3, 64, 64)
+    Uo, _, to, _ = oracle.run_2d(U, dx, dy, cfl=0.4, t_end=0.05, bc=PER)
+    c = ctx(64, 64, dx, dy, B.T7_MIXED, PER)
+    Ug = torch.tensor(U, device="cuda")
+    _, tg = c.run(Ug, 0.4, t_end=0.05)
+    assert tg == to
+    got = Ug.cpu().numpy()
+    for k in range(4):
+        assert np.abs(got[k] - Uo[k]).sum() / np.abs(Uo[k]).sum() < 1e-5, k
+    U, dx, dy, _ = I.quadrants_2d(11, 96, 80)
+    Uo, _, _, _ = oracle.run_2d(U, dx, dy, cfl=0.4, max_steps=40)
+    c = ctx(96, 80, dx, dy, B.T7_MIXED, ZG)
+    Ug = torch.tensor(U, device="cuda")
+    c.run(Ug, 0.4, max_steps=40)
+    assert np.abs(Ug.cpu().numpy()[0] - Uo[0]).sum() / np.abs(Uo[0]).sum() < 1e-3
+
+
+def test_2d_f32_full_size_sampled():
+    """2048^2 quadrants (the benchmark size): the FP32 RHS on sampled cells is
+    within the FP32 bound of the oracle on 25 x 25 windows wherever the
+    sampled cell's eight Delta codes of each face agree."""
+    n = 2048
+    U, dx, dy, _ = I.quadrants_2d(4, n, n)
+    ax, ay = oracle.alpha_2d(U)
+    c = ctx(n, n, dx, dy, B.T7_F32, ZG)
+    rg, (mxg, myg) = c.euler_rhs(torch.tensor(U, dtype=torch.float32, device="cuda"), want_masks=True)
+    c.sync()
+    rg = rg.double().cpu().numpy()
+    rng = np.random.default_rng(2)
+    pts = [(0, 0), (n - 1, n - 1), (1023, 1024), (1024, 1023)] + [tuple(q) for q in rng.integers(0, n, (40, 2))]
+    bound = flux_bound(U, dx, dy)
+    W = 12
+    checked = 0
+    for (y, x) in pts:
+        y0, y1 = max(0, y - W), min(n, y + W + 1)
+        x0, x1 = max(0, x - W), min(n, x + W + 1)
+        win = np.ascontiguousarray(U[:, y0:y1, x0:x1])
+        ro, _, (mxo, myo) = oracle.rhs_2d(win, dx, dy, bc=ZG, alpha=(ax, ay), want_masks=True)
+        same = (np.array_equal(mxg[:, :, y, x:x + 2].cpu().numpy(), mxo[:, :, y - y0, x - x0:x - x0 + 2]) and
+                np.array_equal(myg[:, :, x, y:y + 2].cpu().numpy(), myo[:, :, x - x0, y - y0:y - y0 + 2]))
+        if same:
+            checked += 1
+            assert np.max(np.abs(rg[:, y, x] - ro[:, y - y0, x - x0])) <= bound, (y, x)
+    assert checked >= 40

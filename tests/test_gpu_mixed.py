@@ -3,7 +3,7 @@ flux difference and RK combination.
 
 * Its reconstruction is the FP32 kernel's: on the same (float-representable)
   state its stencil codes equal the FP32 path's exactly, and its RHS agrees
-  with the FP32 path's to FP32 rounding of the face fluxes.
+  with the FP32 path's within the FP32 bound (alpha is taken in FP64 here).
 * Against the FP64 oracle: codes agree on >= 99.9% of entries and the RHS on
   agreeing faces is within 64 * 2^-24 * max|F| / dx (the FP32 bound).
 * The face flux enters both neighbours as one FP64 value, so periodic domain
@@ -53,7 +53,9 @@ def test_mixed_rhs_reconstruction_is_the_fp32_one(name, sys, gen, bc, a):
     r32, m32 = c32.euler_rhs(torch.tensor(Uf, dtype=torch.float32, device="cuda"), want_masks=True)
     torch.cuda.synchronize()
     assert torch.equal(mm, m32)
-    bound = 4 * 2.0**-24 * flux_max(sys, Uf, a) / dx
+    # alpha comes from the FP64 state in FP64 here and in FP32 on the FP32
+    # path, so the split fluxes differ at FP32 rounding level: the FP32 bound
+    bound = 64 * 2.0**-24 * flux_max(sys, Uf, a) / dx
     assert float((rm - r32.double()).abs().max()) <= bound
 
 
@@ -130,4 +132,4 @@ def test_mixed_host_run_and_refusals():
     with pytest.raises(B.T7Error):
         c.batch_run(Ud, [0, 1600], [dx], t_end=0.01, cfl=0.5)
     with pytest.raises(B.T7Error):
-        B.Context(B.T7_EULER2D, 16, 0.1, ny=16, dy=0.1, prec=B.T7_MIXED)
+        c.teno7_reconstruct(torch.zeros(72, dtype=torch.float64, device="cuda"), 1, 1e-6)
