@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
     for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
     const T alpha = T(__longlong_as_double((long long)p.ctl->amax[p.slot_in][0]));
     const T gm1 = T(p.gamma - 1.0), eps = T(p.eps), CT = T(p.CT), dxT = T(p.dx);
+    const T kt = keep_all_factor(CT);
     const T *U = static_cast<const T *>(p.U);
     const T *V = static_cast<const T *>(p.v);
     T *out = static_cast<T *>(p.out);
@@ -203,8 +204,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
                 qp[k][t] = sp;
                 qm[k][t] = sm;
             }
-            word |= cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT) << (3 * k);
-            word |= cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT) << (3 * (3 + k));
+            word |= cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT, kt) << (3 * k);
+            word |= cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT, kt) << (3 * (3 + k));
         }
         const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);

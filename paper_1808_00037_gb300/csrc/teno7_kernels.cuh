@@ -99,11 +99,28 @@ __device__ __forceinline__ T coef(int idx) {
 }
 
 // --------------------------------------------------------------------------
+// Shortcut of the cutoff test.  If tau < kt (beta_min + eps), every
+// g_k = 1 + tau / (beta_k + eps) lies in [1, 1 + kt), so
+// chi_k = g_k^6 / sum_j g_j^6 >= 1 / (3 (1 + kt)^6).  With
+// 1 + kt = 0.9 (3 C_T)^(-1/6) that bound is C_T / 0.9^6 = 1.88 C_T: every
+// stencil is kept, and the divisions and powers need not be evaluated.  The
+// 10% margin in g (1.9x in chi) is far above the rounding of either
+// precision, so the bits are exactly the ones the full evaluation gives.
+// kt = 0 (the shortcut never applies) when C_T >= 1/3.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double keep_all_factor(double CT) {
+    return (CT > 0.0 && CT < 1.0 / 3.0) ? 0.9 * pow(3.0 * CT, -1.0 / 6.0) - 1.0 : 0.0;
+}
+__device__ __forceinline__ float keep_all_factor(float CT) {
+    return (CT > 0.f && CT < 1.f / 3.f) ? 0.9f * powf(3.f * CT, -1.f / 6.f) - 1.f : 0.f;
+}
+
+// --------------------------------------------------------------------------
 // Five-point smoothness measure and cutoff bits (d0 | d1<<1 | d2<<2) of one
-// window w0..w4 = f_{i-2} .. f_{i+2} in upwind order.
+// window w0..w4 = f_{i-2} .. f_{i+2} in upwind order; kt from keep_all_factor.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ unsigned cutoff_bits(double w0, double w1, double w2, double w3, double w4, double eps,
-                                                double CT) {
+                                                double CT, double kt) {
     // Eq. smooth_expl
     double s0a = w0 - 4.0 * w1 + 3.0 * w2;
     double s0b = w0 - 2.0 * w1 + w2;
@@ -116,6 +133,7 @@ __device__ __forceinline__ unsigned cutoff_bits(double w0, double w1, double w2,
     double b2 = 0.25 * (s2a * s2a) + (13.0 / 12.0) * (s2b * s2b);
     // Eq. tau5, Eq. TENO1 with C = 1, q = 6 (squared, squared again, times square)
     double tau = fabs(b0 - b2);
+    if (tau < kt * (fmin(fmin(b0, b1), b2) + eps)) return 7u;  // every stencil kept (see keep_all_factor)
     double g0 = 1.0 + tau / (b0 + eps);
     double g1 = 1.0 + tau / (b1 + eps);
     double g2 = 1.0 + tau / (b2 + eps);
@@ -130,7 +148,7 @@ __device__ __forceinline__ unsigned cutoff_bits(double w0, double w1, double w2,
 }
 
 __device__ __forceinline__ unsigned cutoff_bits(float w0, float w1, float w2, float w3, float w4, float eps,
-                                                float CT) {
+                                                float CT, float kt) {
     float s0a = fmaf(3.f, w2, fmaf(-4.f, w1, w0));
     float s0b = fmaf(-2.f, w1, w0) + w2;
     float s1a = w1 - w3;
@@ -146,6 +164,7 @@ __device__ __forceinline__ unsigned cutoff_bits(float w0, float w1, float w2, fl
     // see RO_FLOOR12 below)
     const float q = fmaxf(fmaxf(fabsf(w0), fabsf(w2)), fabsf(w4));
     eps = fmaxf(eps, (5.9604644775390625e-08f / 12.f) * (q * q));
+    if (tau < kt * (fminf(fminf(b0, b1), b2) + eps)) return 7u;  // every stencil kept (see keep_all_factor)
     float g0 = 1.f + __fdividef(tau, b0 + eps);
     float g1 = 1.f + __fdividef(tau, b1 + eps);
     float g2 = 1.f + __fdividef(tau, b2 + eps);
@@ -388,6 +407,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
     const size_t cs = A.cs;
     const int ntiles = (n + WT - 1) / WT;
     const T alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a, eps = A.eps, CT = A.CT;
+    const T kt = keep_all_factor(CT);
     DevCtl *ctl = A.ctl;
     T wsmax = T(0);
     for (int tile = tile0; tile < ntiles; tile += tstride) {
@@ -511,8 +531,8 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                     qm[k][t] = sm;
                 }
             }
-            const unsigned bp = cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT);
-            const unsigned bm = cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT);
+            const unsigned bp = cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT, kt);
+            const unsigned bm = cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT, kt);
             word |= bp << (3 * k);
             word |= bm << (3 * (M + k));
         }
@@ -745,7 +765,7 @@ constexpr float RO_FLOOR12 = 5.9604644775390625e-08f;  // 2^-24
 // x = g / g_max in (0, 1] so that nothing overflows.  Returns the codes
 // d0<<2 | d1<<1 | d2 of both splits.
 __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps12, float CT,
-                                        unsigned &cp, unsigned &cm) {
+                                        float kt, unsigned &cp, unsigned &cm) {
     const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
     const float2 s0b = __fadd2_rn(__ffma2_rn(f2(-2.f), w1, w0), w2);
     const float2 s1a = __ffma2_rn(f2(-1.f), w3, w1);
@@ -763,6 +783,12 @@ __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 
     const float qy = fmaxf(fmaxf(fabsf(w0.y), fabsf(w2.y)), fabsf(w4.y));
     const float2 ro = __fmul2_rn(f2(RO_FLOOR12), __fmul2_rn(make_float2(qx, qy), make_float2(qx, qy)));
     const float2 ee = make_float2(fmaxf(eps12, ro.x), fmaxf(eps12, ro.y));
+    // every stencil of both windows kept (see keep_all_factor)
+    if (tau.x < kt * (fminf(fminf(b0.x, b1.x), b2.x) + ee.x) && tau.y < kt * (fminf(fminf(b0.y, b1.y), b2.y) + ee.y)) {
+        cp = 7u;
+        cm = 7u;
+        return;
+    }
     const float2 d0 = __fadd2_rn(b0, ee), d1 = __fadd2_rn(b1, ee), d2 = __fadd2_rn(b2, ee);
     const float2 g0 = __ffma2_rn(tau, make_float2(rcp_approx(d0.x), rcp_approx(d0.y)), f2(1.f));
     const float2 g1 = __ffma2_rn(tau, make_float2(rcp_approx(d1.x), rcp_approx(d1.y)), f2(1.f));
@@ -859,6 +885,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     // (TENO5's epsilon of 1e-40 is below FLT_MIN: raise it to FLT_MIN so that
     // beta + eps is never flushed to zero by the approximate reciprocal)
     const float eps12 = SCH == SCH_TENO5 ? fmaxf(12.f * A.eps, 1.17549435e-38f) : 12.f * A.eps, CT = A.CT;
+    const float kt = keep_all_factor(CT);
     const float idx = 1.f / A.f_dx;
     const S *Us = reinterpret_cast<const S *>(A.Us);
     const S *U0 = reinterpret_cast<const S *>(A.U0);
@@ -998,7 +1025,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
 #pragma unroll
         for (int k = 0; k < M; k++) {
             unsigned cp, cm;
-            cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps12, CT, cp, cm);
+            cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps12, CT, kt, cp, cm);
             word |= (cp << (5 * k + 1)) | (cm << (5 * (3 + k) + 1));
         }
         unsigned D;
@@ -1249,6 +1276,7 @@ __global__ void __launch_bounds__(NT) recon_kernel(const Recon p) {
     const int s = blockIdx.x * TILE;
     const T *v = static_cast<const T *>(p.v);
     const T eps = T(p.eps), CT = T(p.CT);
+    const T kt = keep_all_factor(CT);
     for (int q = tid; q < 91; q += NT) s_coef[q] = coef<T>(q);
     for (int c = tid; c < NCELL; c += NT) {
         int l = s - HALO + c + 4;  // index into v (cell -4 is v[0])
@@ -1259,9 +1287,9 @@ __global__ void __launch_bounds__(NT) recon_kernel(const Recon p) {
     const int j = s - 2 + tid;
     unsigned bits;
     if (p.sign > 0)
-        bits = cutoff_bits(s_v[tid + 1], s_v[tid + 2], s_v[tid + 3], s_v[tid + 4], s_v[tid + 5], eps, CT);
+        bits = cutoff_bits(s_v[tid + 1], s_v[tid + 2], s_v[tid + 3], s_v[tid + 4], s_v[tid + 5], eps, CT, kt);
     else
-        bits = cutoff_bits(s_v[tid + 6], s_v[tid + 5], s_v[tid + 4], s_v[tid + 3], s_v[tid + 2], eps, CT);
+        bits = cutoff_bits(s_v[tid + 6], s_v[tid + 5], s_v[tid + 4], s_v[tid + 3], s_v[tid + 2], eps, CT, kt);
     s_bits[tid] = bits;
     if (p.d3 && j >= -2 && j <= n) p.d3[j + 2] = (uint8_t)bits;
     __syncthreads();

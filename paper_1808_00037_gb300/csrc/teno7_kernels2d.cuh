@@ -38,7 +38,7 @@ __device__ __forceinline__ constexpr int rot(int c) {
 // gp(c, t) / gm(c, t): physical component c of the split fluxes of local cell
 // t; local cell t = 0 .. 7 is cell j-3+t of face j+1/2.
 template <typename T, int DIR, typename PR, typename GP, typename GM>
-__device__ __forceinline__ void face2d_bits(Face2D<T> &F, PR pr, GP gp, GM gm, T gm1, T eps, T CT) {
+__device__ __forceinline__ void face2d_bits(Face2D<T> &F, PR pr, GP gp, GM gm, T gm1, T eps, T CT, T kt) {
     const T unl = pr(0, 3), unr = pr(0, 4), utl = pr(1, 3), utr = pr(1, 4);
     const T Hl = pr(2, 3), Hr = pr(2, 4), sl = pr(3, 3), sr = pr(3, 4);
     F.un = (sl * unl + sr * unr) / (sl + sr);
@@ -74,8 +74,8 @@ __device__ __forceinline__ void face2d_bits(Face2D<T> &F, PR pr, GP gp, GM gm, T
             F.qp[k][t] = sp;
             F.qm[k][t] = sm;
         }
-        const unsigned bp = cutoff_bits(F.qp[k][1], F.qp[k][2], F.qp[k][3], F.qp[k][4], F.qp[k][5], eps, CT);
-        const unsigned bm = cutoff_bits(F.qm[k][5], F.qm[k][4], F.qm[k][3], F.qm[k][2], F.qm[k][1], eps, CT);
+        const unsigned bp = cutoff_bits(F.qp[k][1], F.qp[k][2], F.qp[k][3], F.qp[k][4], F.qp[k][5], eps, CT, kt);
+        const unsigned bm = cutoff_bits(F.qm[k][5], F.qm[k][4], F.qm[k][3], F.qm[k][2], F.qm[k][1], eps, CT, kt);
         F.word |= bp << (3 * k);
         F.word |= bm << (3 * (4 + k));
     }
@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
     const T alpha = alpha_of<T>(ctl, p.slot_in, 0);
     const T gm1 = pick<T>(p.gamma - 1.0, p.f_gm1);
     const T eps = pick<T>(p.eps_x, p.f_eps_x), CT = pick<T>(p.CT, p.f_CT);
+    const T kt = keep_all_factor(CT);
     const T *Us = static_cast<const T *>(p.Us);
     T *R = static_cast<T *>(p.R);
     const int nx = p.nx, ny = p.ny;
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
         Face2D<T> F;
         face2d_bits<T, 0>(
             F, [&](int q, int t) { return spr[q][lane + t]; }, [&](int c, int t) { return sgp[c][lane + t]; },
-            [&](int c, int t) { return sgm[c][lane + t]; }, gm1, eps, CT);
+            [&](int c, int t) { return sgm[c][lane + t]; }, gm1, eps, CT, kt);
         const unsigned wl = __shfl_up_sync(0xffffffffu, F.word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, F.word, 1);
         T fh[4];
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
     const T alpha = alpha_of<T>(ctl, p.slot_in, 1);
     const T gamma = pick<T>(p.gamma, p.f_gamma), gm1 = pick<T>(p.gamma - 1.0, p.f_gm1);
     const T eps = pick<T>(p.eps_y, p.f_eps_y), CT = pick<T>(p.CT, p.f_CT);
+    const T kt = keep_all_factor(CT);
     const T *Us = static_cast<const T *>(p.Us);
     for (int q = tid; q < 91; q += blockDim.x) s_coef[q] = coef<T>(q);
 
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
         face2d_bits<T, 1>(
             F, [&](int q, int t) { return at(s_pr, q, lane + t, col); },
             [&](int c, int t) { return at(s_gp, c, lane + t, col); },
-            [&](int c, int t) { return at(s_gm, c, lane + t, col); }, gm1, eps, CT);
+            [&](int c, int t) { return at(s_gm, c, lane + t, col); }, gm1, eps, CT, kt);
         const unsigned wl = __shfl_up_sync(0xffffffffu, F.word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, F.word, 1);
         T fh[4];
@@ -530,8 +532,8 @@ __device__ __forceinline__ void cell2d_f32(const float U[4], float gm1, float al
 // codes_p / codes_m receive the four fields' Delta codes (5 bits each).
 template <int DIR, typename PR, typename GP, typename GM>
 __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsigned &codes_m, int &flag, PR pr,
-                                           GP gp, GM gm, const float (*s_cf)[8], float eps12, float CT, float gm1,
-                                           int lane) {
+                                           GP gp, GM gm, const float (*s_cf)[8], float eps12, float CT, float kt,
+                                           float gm1, int lane) {
     const float unl = pr(0, lane + 3), unr = pr(0, lane + 4), vtl = pr(1, lane + 3), vtr = pr(1, lane + 4);
     const float Hl = pr(2, lane + 3), Hr = pr(2, lane + 4), sl = pr(3, lane + 3), sr = pr(3, lane + 4);
     const float w = rcp_approx(sl + sr);
@@ -577,7 +579,7 @@ __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsig
             }
         }
         unsigned cp, cm;
-        cutoff2(P[1], P[2], P[3], P[4], P[5], eps12, CT, cp, cm);
+        cutoff2(P[1], P[2], P[3], P[4], P[5], eps12, CT, kt, cp, cm);
         const unsigned word = (cp << 1) | (cm << 6);
         const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
@@ -628,6 +630,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     fill_delta_table(s_cf);
     const float alpha = ctl->alpha_f[p.slot_in][0];
     const float gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_x, CT = p.f_CT;
+    const float kt = keep_all_factor(CT);
     const float idx = 1.f / p.f_dx;
     const double idxD = 1.0 / p.dx;
     const S *Us = static_cast<const S *>(p.Us);
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         int flag = 0;
         face2d_f32<0>(
             fh, cpk, cmk, flag, [&](int q, int i) { return spr[q][i]; }, [&](int cc, int i) { return sgp[cc][i]; },
-            [&](int cc, int i) { return sgm[cc][i]; }, s_cf, eps12, CT, gm1, lane);
+            [&](int cc, int i) { return sgm[cc][i]; }, s_cf, eps12, CT, kt, gm1, lane);
         const bool face_out = lane >= 1 && lane <= 30;
         if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= nx - 1) {
 #pragma unroll
@@ -742,6 +745,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
     const int x0 = blockIdx.x * YB_COLS, r0 = blockIdx.y * YB_ROWS;
     const float alpha = ctl->alpha_f[p.slot_in][1];
     const float gamma = p.f_gamma, gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_y, CT = p.f_CT;
+    const float kt = keep_all_factor(CT);
     const S *Us = static_cast<const S *>(p.Us);
     fill_delta_table(s_cf);
 
@@ -790,7 +794,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
         face2d_f32<1>(
             fh, cpk, cmk, flag, [&](int q, int i) { return at(s_pr, q, i, col); },
             [&](int cc, int i) { return at(s_gp, cc, i, col); }, [&](int cc, int i) { return at(s_gm, cc, i, col); },
-            s_cf, eps12, CT, gm1, lane);
+            s_cf, eps12, CT, kt, gm1, lane);
         const bool face_out = lane >= 1 && lane <= 30;
         if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= ny - 1) {
             uint8_t *ym = p.masks + (size_t)8 * ny * (nx + 1);
