@@ -157,6 +157,21 @@ t7_status t7_euler_rhs_adjoint(t7_ctx *ctx, const void *U, const void *v, void *
  * transposed, with L^T from t7_euler_rhs_adjoint at each stage.  Async. */
 t7_status t7_rk3_step_adjoint(t7_ctx *ctx, const void *U, double dt, void *lambda);
 
+/* Recorded steps, for reverse sweeps that replay a segment forward first
+ * (checkpointing).  A tape entry holds one step's stage states U1 and U2, the
+ * forward Delta codes of its three stage states and their three alphas.
+ * t7_tape_bytes: size of one entry for this context (a multiple of 256).
+ * t7_rk3_step_record: one SSP-RK3 step of fixed dt from U_in to U_out (device
+ *   [3][nx]; U_out may not alias U_in, which the adjoint needs later),
+ *   writing the entry `tape` (device, 256-byte aligned, caller-owned).  Async.
+ * t7_rk3_step_adjoint_recorded: the adjoint of that step -- the same map as
+ *   t7_rk3_step_adjoint -- from U_in and its entry, without recomputing the
+ *   stages: lambda (the adjoint of U_out) becomes the adjoint of U_in in
+ *   place.  Async.  Both take a 1D Euler TENO7-ext FP64 or FP32 context. */
+t7_status t7_tape_bytes(t7_ctx *ctx, size_t *bytes);
+t7_status t7_rk3_step_record(t7_ctx *ctx, const void *U_in, void *U_out, double dt, void *tape);
+t7_status t7_rk3_step_adjoint_recorded(t7_ctx *ctx, const void *U_in, const void *tape, double dt, void *lambda);
+
 /* Ragged batch of independent 1D Euler problems (shock tubes) of uneven
  * length, each advanced by its own SSP-RK3 loop with its own CFL step
  * dt = CFL dx_t / alpha_t(U^n) to t_end (or max_steps), all in ONE persistent

@@ -3,11 +3,14 @@
 ``CheckpointedRK3`` is a ``torch.autograd.Function``: its forward advances a
 state by ``nsteps`` SSP-RK3 steps of fixed size dt with the CUDA stage kernels
 (``t7_rk3_step``), keeping the state every ``every`` steps; its backward
-replays each segment from its checkpoint and maps the incoming gradient back
-step by step with the hand-written discrete adjoint (``t7_rk3_step_adjoint``:
-stage states recomputed, ``(dL/dU)^T`` applied by the adjoint kernel with the
-stencil selection and alpha frozen).  Memory: the checkpoints plus one
-segment of step states.
+replays each segment from its checkpoint with recorded steps
+(``t7_rk3_step_record``: stage states, forward stencil codes and alphas go to
+a tape) and maps the incoming gradient back step by step with the
+hand-written discrete adjoint of each recorded step
+(``t7_rk3_step_adjoint_recorded``: ``(dL/dU)^T`` applied by the adjoint kernel
+with the recorded selection and alpha frozen, accumulated straight into the
+RK3 adjoint buffers).  Memory: the checkpoints plus one segment of states and
+tape entries.
 
 ``sine_modes_gradient`` sets up the adjoint benchmark problem -- periodic [0,1),
 rho0 = 1 + sum_k a_k sin(2 pi k x), u0 = p0 = 1, J = sum_i rho_i^2 dx at the
@@ -63,16 +66,17 @@ def _make_function():
         def backward(fctx, grad_out):
             context, dt, nsteps, every = fctx.context, fctx.dt, fctx.nsteps, fctx.every
             lam = grad_out.detach().contiguous().clone()
+            # one segment's states and tape entries, reused for every segment
+            states = [torch.empty_like(fctx.cps[0]) for _ in range(every + 1)]
+            tapes = torch.empty((every, context.tape_bytes()), dtype=torch.uint8, device=lam.device)
             for seg in reversed(range(len(fctx.cps))):
                 start = seg * every
-                stop = min(start + every, nsteps)
-                U = fctx.cps[seg].clone()
-                states = []
-                for _ in range(start, stop):
-                    states.append(U.clone())
-                    context.rk3_step(U, dt)
-                for st in reversed(states):
-                    context.rk3_step_adjoint(st, dt, lam)
+                count = min(start + every, nsteps) - start
+                states[0].copy_(fctx.cps[seg])
+                for s in range(count):
+                    context.rk3_step_record(states[s], states[s + 1], dt, tapes[s])
+                for s in reversed(range(count)):
+                    context.rk3_step_adjoint_recorded(states[s], tapes[s], dt, lam)
             context.sync()
             return lam, None, None, None, None
 

@@ -69,6 +69,9 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_batch_run": ([vp, vp, vp, vp, i, d, d, i, i, vp, vp], i),
         "t7_euler_rhs_adjoint": ([vp, vp, vp, vp], i),
         "t7_rk3_step_adjoint": ([vp, vp, d, vp], i),
+        "t7_tape_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
+        "t7_rk3_step_record": ([vp, vp, vp, d, vp], i),
+        "t7_rk3_step_adjoint_recorded": ([vp, vp, vp, d, vp], i),
         "t7_batch_autotune": ([vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), vp], i),
     }
     for name, (args, res) in sigs.items():
@@ -218,6 +221,24 @@ class Context:
         """Map lam (adjoint of the step result) in place to the adjoint of U."""
         self._check(self.lib.t7_rk3_step_adjoint(self.h, _ptr(self._dev(U)), dt, _ptr(self._dev(lam))),
                     "t7_rk3_step_adjoint")
+        return lam
+
+    def tape_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        self._check(self.lib.t7_tape_bytes(self.h, ctypes.byref(b)), "t7_tape_bytes")
+        return b.value
+
+    def rk3_step_record(self, U_in, U_out, dt: float, tape):
+        """One fixed-dt step U_in -> U_out recording the stage data into `tape`
+        (a CUDA uint8 tensor of tape_bytes(), 256-byte aligned)."""
+        self._check(self.lib.t7_rk3_step_record(self.h, _ptr(self._dev(U_in)), _ptr(self._dev(U_out)), dt,
+                                                _ptr(tape)), "t7_rk3_step_record")
+        return U_out
+
+    def rk3_step_adjoint_recorded(self, U_in, tape, dt: float, lam):
+        """Adjoint of a recorded step: lam (adjoint of U_out) -> adjoint of U_in, in place."""
+        self._check(self.lib.t7_rk3_step_adjoint_recorded(self.h, _ptr(self._dev(U_in)), _ptr(tape), dt,
+                                                          _ptr(self._dev(lam))), "t7_rk3_step_adjoint_recorded")
         return lam
 
     # ------------------------------------------------------- ragged batch --

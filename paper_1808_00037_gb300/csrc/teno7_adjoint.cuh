@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
     __shared__ T s_coef[WPB][92];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
-    const T alpha = T(__longlong_as_double((long long)p.ctl->amax[p.slot_in][0]));
+    const T alpha = p.alpha_ptr ? T(*p.alpha_ptr) : T(__longlong_as_double((long long)p.ctl->amax[p.slot_in][0]));
+    const T sc = T(p.scale);
     const T gm1 = T(p.gamma - 1.0), eps = T(p.eps), CT = T(p.CT), dxT = T(p.dx);
     const T kt = keep_all_factor(CT);
     const T *U = static_cast<const T *>(p.U);
@@ -157,7 +158,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
     T (*sgm)[WC] = s_gm[warp];
     const T *scoef = s_coef[warp];
     __syncwarp();
-    for (int tile = blockIdx.x * WPB + warp; tile < ntiles; tile += gridDim.x * WPB) {
+    const int nw = blockDim.x >> 5;
+    for (int tile = blockIdx.x * nw + warp; tile < ntiles; tile += gridDim.x * nw) {
         const int c0 = tile * WT;
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
             for (int c = 0; c < 3; c++) {
                 const T vr = (j + 1 <= n - 1) ? V[(size_t)c * n + (j + 1)] : T(0);
                 const T vl = (j >= 0) ? V[(size_t)c * n + j] : T(0);
-                lF[c] = (vr - vl) / dxT;
+                lF[c] = sc * ((vr - vl) / dxT);
             }
             T lf[3], lR[3][3];
 #pragma unroll
@@ -316,12 +318,35 @@ __global__ void combine_kernel(T *out, const T *x, const T *y, const T *z, T c1,
     }
 }
 
+// out1 = a1 x + b1 y; out2 = a2 x + b2 y (if out2); x may be null.  out1 may
+// alias x or y (each element is read before it is written).
+template <typename T>
+__global__ void combine2_kernel(T *out1, T *out2, const T *x, const T *y, T a1, T b1, T a2, T b2, size_t N) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const T xv = x ? x[i] : T(0), yv = y[i];
+        out1[i] = a1 * xv + b1 * yv;
+        if (out2) out2[i] = a2 * xv + b2 * yv;
+    }
+}
+
+template <typename T>
+cudaError_t launch_combine2(void *out1, void *out2, const void *x, const void *y, double a1, double b1, double a2,
+                            double b2, size_t N, cudaStream_t st) {
+    int grid = (int)((N + 255) / 256);
+    if (grid > num_sms() * 8) grid = num_sms() * 8;
+    combine2_kernel<T><<<grid, 256, 0, st>>>(static_cast<T *>(out1), static_cast<T *>(out2),
+                                             static_cast<const T *>(x), static_cast<const T *>(y), T(a1), T(b1),
+                                             T(a2), T(b2), N);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_rhs_adjoint1d(const Adjoint1D &p, cudaStream_t st) {
     const int ntiles = (p.n + WT - 1) / WT;
-    int grid = (ntiles + WPB - 1) / WPB;
-    if (grid > num_sms() * 4) grid = num_sms() * 4;
-    rhs_adjoint1d_kernel<T><<<grid, WPB * 32, 0, st>>>(p);
+    const int nw = warps_per_cta(ntiles, true);
+    int grid = (ntiles + nw - 1) / nw;
+    if (grid > num_sms() * 4 * (WPB / nw)) grid = num_sms() * 4 * (WPB / nw);
+    rhs_adjoint1d_kernel<T><<<grid, nw * 32, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -9,11 +9,13 @@ namespace t7 {
 struct Adjoint1D {
     const void *U;         // state [3][n]
     const void *v;         // adjoint input [3][n]
-    void *out;             // (dL/dU)^T v, [3][n]; zeroed by the caller
+    void *out;             // accumulates scale (dL/dU)^T v, [3][n] (atomically)
     const uint8_t *masks;  // nullable: forward Delta codes [2][3][n+1]; else recomputed
     int n, bc_lo, bc_hi;
     double dx, eps, CT, gamma;
     DevCtl *ctl;
-    int slot_in;  // alpha of U (frozen)
+    int slot_in;               // alpha of U (frozen) ...
+    const double *alpha_ptr;   // ... or, if not null, read from here
+    double scale;              // out += scale (dL/dU)^T v
 };
 }  // namespace t7

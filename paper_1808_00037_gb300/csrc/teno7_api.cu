@@ -146,6 +146,7 @@ cudaError_t stage2d(t7_ctx *c, const t7::Stage2D &p) {
 cudaError_t alpha_launch(t7_ctx *c, const void *U) {
     if (c->g.sys == T7_EULER2D) {
         t7::Alpha2D a;
+        memset(&a, 0, sizeof(a));
         a.U = U;
         a.nx = c->g.nx;
         a.ny = c->g.ny;
@@ -155,6 +156,7 @@ cudaError_t alpha_launch(t7_ctx *c, const void *U) {
         return c->g.prec != T7_F32 ? t7::launch_alpha2d_f64(a, c->stream) : t7::launch_alpha2d_f32(a, c->stream);
     }
     t7::Alpha1D a;
+    memset(&a, 0, sizeof(a));  // alpha_rec stays null
     a.U = U;
     a.n = c->g.nx;
     a.sys = c->g.sys;
@@ -335,6 +337,7 @@ t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double
     if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
         return fail(c, T7_EINVAL, "t7_teno7_reconstruct: a TENO7-ext FP64 or FP32 context only");
     t7::Recon p;
+    memset(&p, 0, sizeof(p));
     p.v = v;
     p.fhat = fhat;
     p.d3 = d3;
@@ -490,7 +493,56 @@ static cudaError_t adj_apply(t7_ctx *c, const void *U, int slot, const uint8_t *
     a.gamma = c->g.gamma;
     a.ctl = c->ctl;
     a.slot_in = slot;
+    a.scale = 1.0;
     return c->g.prec == T7_F64 ? t7::launch_rhs_adjoint1d_f64(a, c->stream) : t7::launch_rhs_adjoint1d_f32(a, c->stream);
+}
+
+// out += scale (dL/dU)^T v at U with recorded alpha and masks (no zeroing)
+static cudaError_t adj_accumulate(t7_ctx *c, const void *U, const double *alpha, const uint8_t *masks, const void *v,
+                                  void *out, double scale) {
+    t7::Adjoint1D a;
+    memset(&a, 0, sizeof(a));
+    a.U = U;
+    a.v = v;
+    a.out = out;
+    a.masks = masks;
+    a.n = c->g.nx;
+    a.bc_lo = c->g.bc[0];
+    a.bc_hi = c->g.bc[1];
+    a.dx = c->g.dx;
+    a.eps = eps_of(c->g.eps_x, c->g.dx);
+    a.CT = c->g.CT;
+    a.gamma = c->g.gamma;
+    a.ctl = c->ctl;
+    a.alpha_ptr = alpha;
+    a.scale = scale;
+    return c->g.prec == T7_F64 ? t7::launch_rhs_adjoint1d_f64(a, c->stream) : t7::launch_rhs_adjoint1d_f32(a, c->stream);
+}
+
+static cudaError_t combine2(t7_ctx *c, void *out1, void *out2, const void *x, const void *y, double a1, double b1,
+                            double a2, double b2) {
+    const size_t N = c->ncell * c->m;
+    return c->g.prec == T7_F64 ? t7::launch_combine2_f64(out1, out2, x, y, a1, b1, a2, b2, N, c->stream)
+                               : t7::launch_combine2_f32(out1, out2, x, y, a1, b1, a2, b2, N, c->stream);
+}
+
+// Layout of one tape entry: U1, U2 (state-sized), the forward Delta codes of
+// the three stage states ([2][3][n+1] bytes each) and their three alphas.
+struct TapeLayout {
+    size_t u1, u2, masks[3], alpha, total;
+};
+static TapeLayout tape_layout(const t7_ctx *c) {
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    TapeLayout L;
+    const size_t sb = up(c->ncell * c->m * c->esize), mb = up((size_t)2 * c->m * (c->g.nx + 1));
+    L.u1 = 0;
+    L.u2 = sb;
+    L.masks[0] = 2 * sb;
+    L.masks[1] = 2 * sb + mb;
+    L.masks[2] = 2 * sb + 2 * mb;
+    L.alpha = 2 * sb + 3 * mb;
+    L.total = L.alpha + 256;
+    return L;
 }
 
 static cudaError_t combine(t7_ctx *c, void *out, const void *x, const void *y, const void *z, double c1, double c2,
@@ -564,6 +616,77 @@ t7_status t7_rk3_step_adjoint(t7_ctx *c, const void *U, double dt, void *lambda)
     if (e == cudaSuccess) e = adj_apply(c, Us[0], 0, mk[0], w, tmp);
     if (e == cudaSuccess) e = combine(c, lambda, acc, w, tmp, 1.0, 1.0, dt);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
+    return T7_OK;
+}
+
+t7_status t7_tape_bytes(t7_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return T7_EINVAL;
+    *bytes = tape_layout(c).total;
+    return T7_OK;
+}
+
+t7_status t7_rk3_step_record(t7_ctx *c, const void *U_in, void *U_out, double dt, void *tape) {
+    t7_status st = adj_check(c);
+    if (st) return st;
+    if (!U_in || !U_out || !tape || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step_record: bad argument");
+    if ((reinterpret_cast<uintptr_t>(tape) & 255u) != 0)
+        return fail(c, T7_EINVAL, "t7_rk3_step_record: tape must be 256-byte aligned");
+    const TapeLayout L = tape_layout(c);
+    unsigned char *t = static_cast<unsigned char *>(tape);
+    double *alpha = reinterpret_cast<double *>(t + L.alpha);
+    void *Ust[3] = {const_cast<void *>(U_in), t + L.u1, t + L.u2};
+    void *Uo[3] = {t + L.u1, t + L.u2, U_out};
+    cudaError_t e = cudaMemsetAsync(c->ctl->amax, 0, sizeof(c->ctl->amax), c->stream);
+    if (e == cudaSuccess) {
+        t7::Alpha1D a;
+        memset(&a, 0, sizeof(a));
+        a.U = U_in;
+        a.n = c->g.nx;
+        a.sys = c->g.sys;
+        a.gamma = c->g.gamma;
+        a.a = c->g.adv_speed;
+        a.ctl = c->ctl;
+        a.slot = 0;
+        a.alpha_rec = alpha;
+        e = c->g.prec == T7_F64 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+    }
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+        t7::Stage1D p = stage_params(c, Ust[k], k == 0 ? nullptr : U_in, Uo[k]);
+        p.rhs_mode = 0;
+        p.stage = k;
+        p.dt_fixed = dt;
+        p.f_dt_fixed = (float)dt;
+        p.slot_in = k;
+        p.masks = reinterpret_cast<uint8_t *>(t + L.masks[k]);
+        p.alpha_rec = k < 2 ? alpha + k + 1 : nullptr;
+        e = stage(c, p);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "recorded step");
+    return T7_OK;
+}
+
+t7_status t7_rk3_step_adjoint_recorded(t7_ctx *c, const void *U_in, const void *tape, double dt, void *lambda) {
+    t7_status st = adj_check(c);
+    if (st) return st;
+    if (!U_in || !tape || !lambda || !(dt > 0.0))
+        return fail(c, T7_EINVAL, "t7_rk3_step_adjoint_recorded: bad argument");
+    const TapeLayout L = tape_layout(c);
+    const unsigned char *t = static_cast<const unsigned char *>(tape);
+    const double *alpha = reinterpret_cast<const double *>(t + L.alpha);
+    const void *Us[3] = {U_in, t + L.u1, t + L.u2};
+    const uint8_t *mk[3];
+    for (int k = 0; k < 3; k++) mk[k] = t + L.masks[k];
+    void *A = c->adj[0], *W = c->adj[1], *T = c->adj[2];
+    // U3 = U/3 + 2/3 (U2 + dt L(U2)):  W = 2/3 lam + 2/3 dt L2^T lam,  A = lam/3
+    cudaError_t e = combine2(c, W, A, nullptr, lambda, 0.0, 2.0 / 3.0, 0.0, 1.0 / 3.0);
+    if (e == cudaSuccess) e = adj_accumulate(c, Us[2], alpha + 2, mk[2], lambda, W, (2.0 / 3.0) * dt);
+    // U2 = 3/4 U + 1/4 (U1 + dt L(U1)):  A += 3/4 W,  T = W/4 + dt/4 L1^T W
+    if (e == cudaSuccess) e = combine2(c, A, T, A, W, 1.0, 0.75, 0.0, 0.25);
+    if (e == cudaSuccess) e = adj_accumulate(c, Us[1], alpha + 1, mk[1], W, T, 0.25 * dt);
+    // U1 = U + dt L(U):  lam = A + T + dt L0^T T
+    if (e == cudaSuccess) e = combine2(c, lambda, nullptr, A, T, 1.0, 1.0, 0.0, 0.0);
+    if (e == cudaSuccess) e = adj_accumulate(c, Us[0], alpha, mk[0], T, lambda, dt);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint of a recorded step");
     return T7_OK;
 }
 

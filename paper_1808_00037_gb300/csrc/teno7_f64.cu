@@ -16,4 +16,8 @@ cudaError_t launch_combine_f64(void *out, const void *x, const void *y, const vo
                                double c3, size_t N, cudaStream_t s) {
     return launch_combine<double>(out, x, y, z, c1, c2, c3, N, s);
 }
+cudaError_t launch_combine2_f64(void *out1, void *out2, const void *x, const void *y, double a1, double b1,
+                                double a2, double b2, size_t N, cudaStream_t s) {
+    return launch_combine2<double>(out1, out2, x, y, a1, b1, a2, b2, N, s);
+}
 }  // namespace t7

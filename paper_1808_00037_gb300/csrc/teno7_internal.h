@@ -43,7 +43,8 @@ struct Stage1D {
     int slot_in;     // alpha of Us
     // the same parameters rounded to float, for the FP32 kernels
     float f_dx, f_eps, f_CT, f_gamma, f_gm1, f_a, f_dt_fixed;
-    int scheme;      // 0: TENO7-ext, 1: TENO5 baseline
+    int scheme;         // 0: TENO7-ext, 1: TENO5 baseline
+    double *alpha_rec;  // nullable: receives alpha of the output state (RK mode)
 };
 
 struct Alpha1D {
@@ -52,6 +53,7 @@ struct Alpha1D {
     double gamma, a;
     DevCtl *ctl;
     int slot;
+    double *alpha_rec;  // nullable: receives the finished alpha
 };
 
 // One stage of the 2D Euler system, dimension by dimension: the x sweep
@@ -118,6 +120,11 @@ cudaError_t launch_combine_f64(void *out, const void *x, const void *y, const vo
                                double c3, size_t N, cudaStream_t s);
 cudaError_t launch_combine_f32(void *out, const void *x, const void *y, const void *z, double c1, double c2,
                                double c3, size_t N, cudaStream_t s);
+// out1 = a1 x + b1 y; out2 (nullable) = a2 x + b2 y; x may be null
+cudaError_t launch_combine2_f64(void *out1, void *out2, const void *x, const void *y, double a1, double b1,
+                                double a2, double b2, size_t N, cudaStream_t s);
+cudaError_t launch_combine2_f32(void *out1, void *out2, const void *x, const void *y, double a1, double b1,
+                                double a2, double b2, size_t N, cudaStream_t s);
 
 // Finalization done by the last CTA of a launch (see DevCtl).
 enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_STEP = 2 };

@@ -331,7 +331,7 @@ __device__ __forceinline__ T poly5(const T *__restrict__ c, const T v0, const T 
 //                alpha(U^n) = amax[slot_out] (oracle's expression order)
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zero_slot, bool end_of_step,
-                                              bool plan_step, bool two_d = false) {
+                                              bool plan_step, bool two_d = false, double *alpha_rec = nullptr) {
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
     if (prev != gridDim.x * gridDim.y - 1) return;
@@ -340,6 +340,7 @@ __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zer
     const double ay = two_d ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][1], 0ull)) : 0.0;
     ctl->alpha_f[slot_out][0] = (float)a;
     ctl->alpha_f[slot_out][1] = (float)ay;
+    if (alpha_rec) *alpha_rec = a;  // recorded for a later adjoint
     ctl->amax[zero_slot][0] = 0ull;
     ctl->amax[zero_slot][1] = 0ull;
     if (end_of_step) {
@@ -557,7 +558,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                 const T fp = poly5(scoef + 5 * rp, qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5]);
                 const T fm = poly5(scoef + 5 * rm, qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1]);
                 f[k] = fp + fm;
-                if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
+                if (A.masks && face_out && j >= -1 && j <= n - 1) {
                     A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)bp;
                     A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)bm;
                 }
@@ -588,7 +589,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
             else
                 fm = poly7(scoef + 7 * mm, qm[k][6], qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], qm[k][0]);
             f[k] = fp + fm;
-            if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
+            if (A.masks && face_out && j >= -1 && j <= n - 1) {
                 A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dp;
                 A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] = (uint8_t)Dm;
             }
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     DevCtl *ctl = p.ctl;
     const bool fixed = p.dt_fixed > 0.0;
     if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (SCH == SCH_TENO5) {
         for (int q = lane; q < 35; q += 32) s_coef[warp][q] = coef5<T>(q);
     } else {
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     A.ctl = ctl;
     __syncwarp();
     T wsmax = tiles1d<T, SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
-                                   blockIdx.x * WPB + warp, gridDim.x * WPB);
+                                   blockIdx.x * nw + warp, gridDim.x * nw);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -719,10 +720,11 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
         if (threadIdx.x == 0) {
             T v = s_red[0];
 #pragma unroll
-            for (int w = 1; w < WPB; w++) v = fmax(v, s_red[w]);
+            for (int w = 1; w < nw; w++) v = fmax(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
+                          p.alpha_rec);
         }
     }
 }
@@ -834,8 +836,8 @@ constexpr unsigned SLOT_PLUS = 0x00007FFFu; // slots 0..2 ('+' split)
 // Delta-indexed coefficient table: row D holds Table co2's row for Table co3's
 // choice at D ("no exist" rows get f11); filled by a 256-thread CTA.
 __device__ __forceinline__ void fill_delta_table(float (*s_cf)[8]) {
-    const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
-    if (row < 32) {
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+        const int row = q >> 3, t = q & 7;
         int m = lut_select(row);
         if (m == 15) m = 11;
         s_cf[row][t] = t < 7 ? coef<float>(7 * m + t) : 0.f;
@@ -845,8 +847,8 @@ __device__ __forceinline__ void fill_delta_table(float (*s_cf)[8]) {
 // TENO5 counterpart: row D (only bits 3..1 = d0, d1, d2 are ever set) holds
 // the Table co1 row of the code on taps 1..5 of the seven-tap layout.
 __device__ __forceinline__ void fill_delta_table5(float (*s_cf)[8]) {
-    const int row = threadIdx.x >> 3, t = threadIdx.x & 7;
-    if (row < 32) {
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+        const int row = q >> 3, t = q & 7;
         const unsigned code = ((row >> 3) & 1) | (((row >> 2) & 1) << 1) | (((row >> 1) & 1) << 2);
         int r = sel5(code);
         if (r == 7) r = 0;
@@ -1088,7 +1090,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                 f[k] = s.x + s.y;
             }
         }
-        if (A.rhs_mode && A.masks && face_out && j >= -1 && j <= n - 1) {
+        if (A.masks && face_out && j >= -1 && j <= n - 1) {
 #pragma unroll
             for (int k = 0; k < M; k++) {
                 const unsigned sp = (D >> (5 * k)) & 31u, sm = (D >> (5 * (3 + k))) & 31u;
@@ -1184,7 +1186,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     DevCtl *ctl = p.ctl;
     const bool fixed = p.dt_fixed > 0.0;
     if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (SCH == SCH_TENO5)
         fill_delta_table5(s_cf);
     else
@@ -1214,7 +1216,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     A.ctl = ctl;
     __syncthreads();
     float wsmax = tiles1d_f32<SYS, SCH, S>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
-                                           blockIdx.x * WPB + warp, gridDim.x * WPB);
+                                           blockIdx.x * nw + warp, gridDim.x * nw);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -1223,10 +1225,11 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
         if (threadIdx.x == 0) {
             float v = s_red[0];
 #pragma unroll
-            for (int w = 1; w < WPB; w++) v = fmaxf(v, s_red[w]);
+            for (int w = 1; w < nw; w++) v = fmaxf(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
+                          p.alpha_rec);
         }
     }
 }
@@ -1261,7 +1264,7 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
         T v = s_red[0];
         for (int w = 1; w < 8; w++) v = fmax(v, s_red[w]);
         atomicMax(&p.ctl->amax[p.slot][0], (unsigned long long)__double_as_longlong((double)v));
-        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true);
+        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true, false, p.alpha_rec);
     }
 }
 
@@ -1333,27 +1336,40 @@ inline int num_sms() {
     return sms;
 }
 
+// Warps per CTA of the 1D stage and adjoint kernels: WPB, or -- for the
+// FP64-pipe-bound kernels (spread = true) -- halved while that would leave SMs
+// without a CTA, so small problems run one warp tile per SM instead of eight
+// tiles on a few SMs (GB300's FP64 rate per SM is low; FP32 stage kernels at
+// small sizes are launch-bound and keep WPB).  The kernels take it from
+// blockDim.
+inline int warps_per_cta(int ntiles, bool spread) {
+    int nw = WPB;
+    while (spread && nw > 1 && (ntiles + nw - 1) / nw < num_sms()) nw >>= 1;
+    return nw;
+}
+
 // FP32 paired-split stage kernels; S = float (FP32 state) or double (mixed).
 template <typename S>
 cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     const int ntiles = (p.n + WT - 1) / WT;
-    const int resident = num_sms() * T7_F32_MINB * 4;  // a few waves of resident CTAs
-    int grid = (ntiles + WPB - 1) / WPB;
+    const int nw = warps_per_cta(ntiles, false);
+    const int resident = num_sms() * T7_F32_MINB * 4 * (WPB / nw);  // a few waves of resident CTAs
+    int grid = (ntiles + nw - 1) / nw;
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
     switch (p.sys) {
         case SYS_ADV:
-            if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
             break;
         case SYS_BURGERS:
-            if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
             break;
         case SYS_EULER1D:
-            if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5, S><<<grid, WPB * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT, S><<<grid, WPB * 32, 0, st>>>(p);
+            if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
+            else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -1366,23 +1382,24 @@ cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
         return launch_stage1d_paired<float>(p, st);
     } else {
         const int ntiles = (p.n + WT - 1) / WT;
-        const int resident = num_sms() * 4;  // a few waves of resident CTAs
-        int grid = (ntiles + WPB - 1) / WPB;
+        const int nw = warps_per_cta(ntiles, true);
+        const int resident = num_sms() * 4 * (WPB / nw);  // a few waves of resident CTAs
+        int grid = (ntiles + nw - 1) / nw;
         if (grid > resident) grid = resident;
         if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
         const bool t5 = p.scheme == SCH_TENO5;
         switch (p.sys) {
             case SYS_ADV:
-                if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_kernel<T, SYS_ADV, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, nw * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_ADV, SCH_TENO7EXT><<<grid, nw * 32, 0, st>>>(p);
                 break;
             case SYS_BURGERS:
-                if (t5) stage1d_kernel<T, SYS_BURGERS, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_kernel<T, SYS_BURGERS, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                if (t5) stage1d_kernel<T, SYS_BURGERS, SCH_TENO5><<<grid, nw * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_BURGERS, SCH_TENO7EXT><<<grid, nw * 32, 0, st>>>(p);
                 break;
             case SYS_EULER1D:
-                if (t5) stage1d_kernel<T, SYS_EULER1D, SCH_TENO5><<<grid, WPB * 32, 0, st>>>(p);
-                else stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT><<<grid, WPB * 32, 0, st>>>(p);
+                if (t5) stage1d_kernel<T, SYS_EULER1D, SCH_TENO5><<<grid, nw * 32, 0, st>>>(p);
+                else stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT><<<grid, nw * 32, 0, st>>>(p);
                 break;
             default: return cudaErrorInvalidValue;
         }

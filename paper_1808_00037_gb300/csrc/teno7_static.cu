@@ -80,6 +80,7 @@ extern "C" t7_status t7_rk3_step_static(const t7_grid *g, void *U, double dt, vo
         return report(errbuf, errlen, T7_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
 
     t7::Alpha1D a;
+    memset(&a, 0, sizeof(a));  // alpha_rec stays null
     a.U = U;
     a.n = g->nx;
     a.sys = g->sys;

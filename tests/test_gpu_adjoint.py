@@ -117,3 +117,34 @@ def test_sine_mode_gradient_full_config(prec):
         fd = (A.sine_modes_objective(ap, 4096, 2000, dt) - A.sine_modes_objective(am, 4096, 2000, dt)) / (2 * h)
         tol = 1e-6 if prec == B.T7_F64 else 2e-3
         assert abs(g[k] - fd) <= tol * scale, (k, g[k], fd, scale)
+
+
+@pytest.mark.parametrize("prec", [B.T7_F64, B.T7_F32])
+def test_recorded_step_and_its_adjoint(prec):
+    """t7_rk3_step_record advances exactly like t7_rk3_step (bit for bit), and
+    t7_rk3_step_adjoint_recorded gives the same map as t7_rk3_step_adjoint
+    (FP64 to 1e-12, FP32 to 1e-4 of the result's scale; the two differ in
+    summation order only), on smooth periodic data and on Shu-Osher."""
+    dtype = torch.float64 if prec == B.T7_F64 else torch.float32
+    rng = np.random.default_rng(21)
+    for (U, dx), bc in ((I.random_euler_smooth(4, 512)[:2], (0, 0)), (I.shu_osher(400), (1, 1))):
+        n = U.shape[1]
+        c = B.Context(B.T7_EULER1D, n, dx, prec=prec, bc=(bc[0], bc[1], 0, 0))
+        Ud = torch.tensor(U, dtype=dtype, device="cuda")
+        dt = c.cfl_dt(Ud, 0.5)
+        ref = Ud.clone()
+        c.rk3_step(ref, dt)
+        tape = torch.zeros(c.tape_bytes(), dtype=torch.uint8, device="cuda")
+        out = torch.empty_like(Ud)
+        c.rk3_step_record(Ud, out, dt, tape)
+        c.sync()
+        assert torch.equal(out, ref)
+        lam = torch.tensor(rng.normal(size=U.shape), dtype=dtype, device="cuda")
+        l_old = lam.clone()
+        c.rk3_step_adjoint(Ud, dt, l_old)
+        l_new = lam.clone()
+        c.rk3_step_adjoint_recorded(Ud, tape, dt, l_new)
+        c.sync()
+        scale = float(l_old.abs().max())
+        tol = 1e-12 if prec == B.T7_F64 else 1e-4
+        assert float((l_new - l_old).abs().max()) <= tol * scale
