@@ -759,14 +759,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // below 1e-3 for pure noise, while jumps above ~1e-4 Q are measured as
 // before.  (FP64 round-off is ~1e-32 Q^2, far below dx^3: FP64 keeps
 // epsilon = dx^3.)
-constexpr float RO_FLOOR12 = 5.9604644775390625e-08f;  // 2^-24
+constexpr float RO_FLOOR12 = 5.9604644775390625e-08f;  // 2^-24 (epsilon of 12 beta)
+constexpr float RO_FLOOR4 = RO_FLOOR12 / 3.f;           // the same floor for 4 beta
 
 // Cutoff codes of a '+' window (.x) and a '-' window (.y), w0..w4 in upwind
-// order.  beta is scaled by 12 (3 a^2 + 13 b^2) with eps12 = 12 eps, which
+// order.  beta is scaled by 4 (a^2 + 13/3 b^2) with eps4 = 4 eps, which
 // leaves gamma unchanged; chi_k is evaluated as x_k^6 / sum x^6 with
 // x = g / g_max in (0, 1] so that nothing overflows.  Returns the codes
 // d0<<2 | d1<<1 | d2 of both splits.
-__device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps12, float CT,
+__device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps4, float CT,
                                         float kt, unsigned &cp, unsigned &cm) {
     const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
     const float2 s0b = __fadd2_rn(__ffma2_rn(f2(-2.f), w1, w0), w2);
@@ -774,19 +775,26 @@ __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 
     const float2 s1b = __fadd2_rn(__ffma2_rn(f2(-2.f), w2, w1), w3);
     const float2 s2a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w3, w4));
     const float2 s2b = __fadd2_rn(__ffma2_rn(f2(-2.f), w3, w2), w4);
-    const float2 b0 = __ffma2_rn(f2(3.f), __fmul2_rn(s0a, s0a), __fmul2_rn(f2(13.f), __fmul2_rn(s0b, s0b)));
-    const float2 b1 = __ffma2_rn(f2(3.f), __fmul2_rn(s1a, s1a), __fmul2_rn(f2(13.f), __fmul2_rn(s1b, s1b)));
-    const float2 b2 = __ffma2_rn(f2(3.f), __fmul2_rn(s2a, s2a), __fmul2_rn(f2(13.f), __fmul2_rn(s2b, s2b)));
+    const float2 b0 = __ffma2_rn(s0b, __fmul2_rn(f2(13.f / 3.f), s0b), __fmul2_rn(s0a, s0a));
+    const float2 b1 = __ffma2_rn(s1b, __fmul2_rn(f2(13.f / 3.f), s1b), __fmul2_rn(s1a, s1a));
+    const float2 b2 = __ffma2_rn(s2b, __fmul2_rn(f2(13.f / 3.f), s2b), __fmul2_rn(s2a, s2a));
     const float2 td = __ffma2_rn(f2(-1.f), b2, b0);
     const float2 tau = make_float2(fabsf(td.x), fabsf(td.y));
+    const float bmx = fminf(fminf(b0.x, b1.x), b2.x), bmy = fminf(fminf(b0.y, b1.y), b2.y);
+    // every stencil of both windows kept (see keep_all_factor); tested first
+    // with the unfloored epsilon, since the floor below only raises it
+    if (tau.x < kt * (bmx + eps4) && tau.y < kt * (bmy + eps4)) {
+        cp = 7u;
+        cm = 7u;
+        return;
+    }
     // epsilon no smaller than the FP32 round-off level of the window (see
     // RO_FLOOR12), so that rounding noise cannot trigger the cutoff
     const float qx = fmaxf(fmaxf(fabsf(w0.x), fabsf(w2.x)), fabsf(w4.x));
     const float qy = fmaxf(fmaxf(fabsf(w0.y), fabsf(w2.y)), fabsf(w4.y));
-    const float2 ro = __fmul2_rn(f2(RO_FLOOR12), __fmul2_rn(make_float2(qx, qy), make_float2(qx, qy)));
-    const float2 ee = make_float2(fmaxf(eps12, ro.x), fmaxf(eps12, ro.y));
-    // every stencil of both windows kept (see keep_all_factor)
-    if (tau.x < kt * (fminf(fminf(b0.x, b1.x), b2.x) + ee.x) && tau.y < kt * (fminf(fminf(b0.y, b1.y), b2.y) + ee.y)) {
+    const float2 ro = __fmul2_rn(f2(RO_FLOOR4), __fmul2_rn(make_float2(qx, qy), make_float2(qx, qy)));
+    const float2 ee = make_float2(fmaxf(eps4, ro.x), fmaxf(eps4, ro.y));
+    if (tau.x < kt * (bmx + ee.x) && tau.y < kt * (bmy + ee.y)) {
         cp = 7u;
         cm = 7u;
         return;
@@ -886,7 +894,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     const float alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a;
     // (TENO5's epsilon of 1e-40 is below FLT_MIN: raise it to FLT_MIN so that
     // beta + eps is never flushed to zero by the approximate reciprocal)
-    const float eps12 = SCH == SCH_TENO5 ? fmaxf(12.f * A.eps, 1.17549435e-38f) : 12.f * A.eps, CT = A.CT;
+    const float eps4 = SCH == SCH_TENO5 ? fmaxf(4.f * A.eps, 1.17549435e-38f) : 4.f * A.eps, CT = A.CT;
     const float kt = keep_all_factor(CT);
     const float idx = 1.f / A.f_dx;
     const S *Us = reinterpret_cast<const S *>(A.Us);
@@ -1027,7 +1035,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
 #pragma unroll
         for (int k = 0; k < M; k++) {
             unsigned cp, cm;
-            cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps12, CT, kt, cp, cm);
+            cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps4, CT, kt, cp, cm);
             word |= (cp << (5 * k + 1)) | (cm << (5 * (3 + k) + 1));
         }
         unsigned D;

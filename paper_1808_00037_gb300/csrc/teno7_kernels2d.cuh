@@ -532,7 +532,7 @@ __device__ __forceinline__ void cell2d_f32(const float U[4], float gm1, float al
 // codes_p / codes_m receive the four fields' Delta codes (5 bits each).
 template <int DIR, typename PR, typename GP, typename GM>
 __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsigned &codes_m, int &flag, PR pr,
-                                           GP gp, GM gm, const float (*s_cf)[8], float eps12, float CT, float kt,
+                                           GP gp, GM gm, const float (*s_cf)[8], float eps4, float CT, float kt,
                                            float gm1, int lane) {
     const float unl = pr(0, lane + 3), unr = pr(0, lane + 4), vtl = pr(1, lane + 3), vtr = pr(1, lane + 4);
     const float Hl = pr(2, lane + 3), Hr = pr(2, lane + 4), sl = pr(3, lane + 3), sr = pr(3, lane + 4);
@@ -579,7 +579,7 @@ __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsig
             }
         }
         unsigned cp, cm;
-        cutoff2(P[1], P[2], P[3], P[4], P[5], eps12, CT, kt, cp, cm);
+        cutoff2(P[1], P[2], P[3], P[4], P[5], eps4, CT, kt, cp, cm);
         const unsigned word = (cp << 1) | (cm << 6);
         const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     fill_delta_table(s_cf);
     const float alpha = ctl->alpha_f[p.slot_in][0];
-    const float gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_x, CT = p.f_CT;
+    const float gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_x, CT = p.f_CT;
     const float kt = keep_all_factor(CT);
     const float idx = 1.f / p.f_dx;
     const double idxD = 1.0 / p.dx;
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         int flag = 0;
         face2d_f32<0>(
             fh, cpk, cmk, flag, [&](int q, int i) { return spr[q][i]; }, [&](int cc, int i) { return sgp[cc][i]; },
-            [&](int cc, int i) { return sgm[cc][i]; }, s_cf, eps12, CT, kt, gm1, lane);
+            [&](int cc, int i) { return sgm[cc][i]; }, s_cf, eps4, CT, kt, gm1, lane);
         const bool face_out = lane >= 1 && lane <= 30;
         if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= nx - 1) {
 #pragma unroll
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
     const size_t N = (size_t)nx * ny;
     const int x0 = blockIdx.x * YB_COLS, r0 = blockIdx.y * YB_ROWS;
     const float alpha = ctl->alpha_f[p.slot_in][1];
-    const float gamma = p.f_gamma, gm1 = p.f_gm1, eps12 = 12.f * p.f_eps_y, CT = p.f_CT;
+    const float gamma = p.f_gamma, gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_y, CT = p.f_CT;
     const float kt = keep_all_factor(CT);
     const S *Us = static_cast<const S *>(p.Us);
     fill_delta_table(s_cf);
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
         face2d_f32<1>(
             fh, cpk, cmk, flag, [&](int q, int i) { return at(s_pr, q, i, col); },
             [&](int cc, int i) { return at(s_gp, cc, i, col); }, [&](int cc, int i) { return at(s_gm, cc, i, col); },
-            s_cf, eps12, CT, kt, gm1, lane);
+            s_cf, eps4, CT, kt, gm1, lane);
         const bool face_out = lane >= 1 && lane <= 30;
         if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= ny - 1) {
             uint8_t *ym = p.masks + (size_t)8 * ny * (nx + 1);
