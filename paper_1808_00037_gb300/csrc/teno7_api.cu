@@ -176,10 +176,11 @@ cudaError_t alpha_init(t7_ctx *c, const void *U) {
 }
 
 
-// three stage launches; dt_fixed > 0 fixes the step, otherwise CFL on device
-cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed) {
+// three stage launches; dt_fixed > 0 fixes the step, otherwise CFL on device.
+// out_last (nullable) receives the step's result instead of U (U keeps U^n).
+cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed, void *out_last = nullptr) {
     void *bufs_in[3] = {U, c->U1, c->U2};
-    void *bufs_out[3] = {c->U1, c->U2, U};
+    void *bufs_out[3] = {c->U1, c->U2, out_last ? out_last : U};
     if (c->g.sys == T7_EULER2D) {
         for (int k = 0; k < 3; k++) {
             t7::Stage2D p = stage2d_params(c, bufs_in[k], k == 0 ? nullptr : U, bufs_out[k], c->R);
@@ -405,10 +406,11 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
     return T7_OK;
 }
 
-t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out) {
-    t7_status st = check_sys(c);
-    if (st) return st;
-    if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
+// t7_run's loop; final_out (nullable, only with t_end = inf) receives the
+// result of the last step directly (e.g. mapped host memory).
+static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out,
+                          void *final_out) {
+    t7_status st;
     cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, c->g.dx, c->g.dy, max_steps, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ctl");
     e = alpha_launch(c, U);
@@ -419,8 +421,10 @@ t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, in
     int launched = 0;
     while (launched < max_steps) {
         int k = max_steps - launched < chunk ? max_steps - launched : chunk;
-        for (int q = 0; q < k; q++)
-            if ((e = rk3(c, U, -1.0)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+        for (int q = 0; q < k; q++) {
+            void *last = (final_out && launched + q == max_steps - 1) ? final_out : nullptr;
+            if ((e = rk3(c, U, -1.0, last)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+        }
         launched += k;
         if (isfinite(t_end)) {
             if ((e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(t7::DevCtl), cudaMemcpyDeviceToHost, c->stream)) !=
@@ -437,15 +441,37 @@ t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, in
     return st;
 }
 
+t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out) {
+    t7_status st = check_sys(c);
+    if (st) return st;
+    if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
+    return run_core(c, U, cfl, t_end, max_steps, steps_out, t_out, nullptr);
+}
+
 t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out) {
     t7_status st = check_sys(c);
     if (st) return st;
-    if (!U_host) return fail(c, T7_EINVAL, "t7_run_host: null array");
+    if (!U_host || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0))
+        return fail(c, T7_EINVAL, "t7_run_host: bad argument");
     size_t bytes = c->ncell * c->m * c->esize;
     cudaError_t e = cudaMemcpyAsync(c->Uhost, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "H2D copy");
-    st = t7_run(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out);
+    // Page-locked host arrays are device-accessible: when the number of steps
+    // is known (t_end = inf), the last stage writes the result straight into
+    // the host array over the CPU-GPU link, overlapped with its own compute,
+    // instead of a copy after the run.
+    cudaPointerAttributes at;
+    memset(&at, 0, sizeof(at));
+    if (cudaPointerGetAttributes(&at, U_host) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer && isinf(t_end) && max_steps >= 1) {
+        st = run_core(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out, at.devicePointer);
+        return st;
+    }
+    st = run_core(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out, nullptr);
     if (st != T7_OK && st != T7_ENONPHYSICAL && st != T7_ENONFINITE) return st;
     e = cudaMemcpyAsync(U_host, c->Uhost, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "D2H copy");

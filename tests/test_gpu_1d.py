@@ -322,3 +322,20 @@ def test_f32_fine_tube_stays_close_to_f64(tube):
         assert tt == pytest.approx(0.1, abs=1e-12)
         out[prec] = host(Ug)
     assert rel_l1(out[B.T7_F32][0], out[B.T7_F64][0]) < 2e-4
+
+
+@pytest.mark.parametrize("prec,dtype", [(B.T7_F64, torch.float64), (B.T7_F32, torch.float32),
+                                        (B.T7_MIXED, torch.float64)])
+def test_run_host_pinned_direct_write_matches_device_run(prec, dtype):
+    """A page-locked host array with a known step count takes the path where
+    the last stage writes the result into the host array directly: the result
+    is bit-identical to the device run (1 and 5 steps; FP64, FP32, mixed)."""
+    U, dx = I.shu_osher(1600)
+    for steps in (1, 5):
+        c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1), prec=prec)
+        Ud = dev(U, dtype)
+        sd, td = c.run(Ud, 0.5, max_steps=steps)
+        Uh = torch.tensor(U, dtype=dtype).pin_memory()
+        sh, th = c.run_host(Uh, 0.5, max_steps=steps)
+        assert (sd, td) == (sh, th) == (steps, td)
+        assert torch.equal(Ud.cpu(), Uh)
