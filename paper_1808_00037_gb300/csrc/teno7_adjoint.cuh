@@ -13,8 +13,9 @@
 //   lambda_G = L^T lambda_q,  lambda_L += lambda_q G^T    (projection)
 //   lambda_U += (A^T (lambda_G+ + lambda_G-) + alpha (lambda_G+ - lambda_G-))/2
 //                                                        (G+- = (F +- alpha U)/2)
-// and the frame's dependence on the two face cells through the Roe average,
-// differentiated with a 6-direction dual number.  Contributions to the 8
+// and the frame's dependence on the two face cells through the Roe average:
+// L and R as 2-direction dual numbers in (u~, H~), then the Roe average's
+// derivatives by hand (roe_chain).  Contributions to the 8
 // stencil cells are scattered with atomicAdd.
 #pragma once
 #include "teno7_adjoint_params.h"
@@ -69,47 +70,60 @@ __device__ __forceinline__ Dual<T, D> operator*(T a, const Dual<T, D> &b) {
     for (int k = 0; k < D; k++) r.d[k] = a * b.d[k];
     return r;
 }
+// (one division for the derivatives: they need not round like the value)
 template <typename T, int D>
 __device__ __forceinline__ Dual<T, D> operator/(const Dual<T, D> &a, const Dual<T, D> &b) {
     Dual<T, D> r;
     r.v = a.v / b.v;
+    const T ib = T(1) / b.v;
 #pragma unroll
-    for (int k = 0; k < D; k++) r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v;
+    for (int k = 0; k < D; k++) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
     return r;
 }
 template <typename T, int D>
 __device__ __forceinline__ Dual<T, D> dsqrt(const Dual<T, D> &a) {
     Dual<T, D> r;
     r.v = sq_root(a.v);
+    const T h = T(0.5) / r.v;
 #pragma unroll
-    for (int k = 0; k < D; k++) r.d[k] = a.d[k] / (T(2) * r.v);
+    for (int k = 0; k < D; k++) r.d[k] = a.d[k] * h;
     return r;
 }
 
-// Roe frame of 1D Euler as a function of the two face cells (6 inputs):
-// L (3x3, rows), R (3x3, columns) with derivatives.
+// Roe frame of 1D Euler at a face.  The frame depends on the two face cells
+// only through the Roe-averaged velocity and enthalpy (u~, H~), so L and R are
+// carried as dual numbers in those two directions; roe_chain then maps
+// (lambda_u~, lambda_H~) back to the six cell variables through the Roe
+// average.  Values are computed in the forward kernels' operation order.
 template <typename T>
-__device__ __forceinline__ void frame1d_dual(const T UL[3], const T UR[3], T gm1, Dual<T, 6> L[3][3],
-                                             Dual<T, 6> R[3][3]) {
-    using D6 = Dual<T, 6>;
-    D6 x[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        x[k] = dconst<T, 6>(k < 3 ? UL[k] : UR[k - 3]);
-        x[k].d[k] = T(1);
-    }
-    const D6 half = dconst<T, 6>(T(0.5)), g = dconst<T, 6>(gm1), one = dconst<T, 6>(T(1));
-    const D6 ul = x[1] / x[0], ur = x[4] / x[3];
-    const D6 pl = g * (x[2] - half * x[1] * ul), pr = g * (x[5] - half * x[4] * ur);
-    const D6 Hl = (x[2] + pl) / x[0], Hr = (x[5] + pr) / x[3];
-    const D6 sl = dsqrt(x[0]), sr = dsqrt(x[3]);
-    const D6 ut = (sl * ul + sr * ur) / (sl + sr);
-    const D6 Ht = (sl * Hl + sr * Hr) / (sl + sr);
-    const D6 c2 = g * (Ht - half * ut * ut);
-    const D6 c = dsqrt(c2);
-    const D6 b1 = g / c2;
-    const D6 b2 = half * ut * ut * b1;
-    const D6 mh = dconst<T, 6>(T(-0.5));
+struct RoeFace {
+    T ul, ur, Hl, Hr, sl, sr, rl, rr, ut, Ht;
+};
+
+template <typename T>
+__device__ __forceinline__ void frame1d_dual(const T UL[3], const T UR[3], T gm1, Dual<T, 2> L[3][3],
+                                             Dual<T, 2> R[3][3], RoeFace<T> &rf) {
+    using D2 = Dual<T, 2>;
+    rf.rl = UL[0];
+    rf.rr = UR[0];
+    rf.ul = UL[1] / UL[0];
+    rf.ur = UR[1] / UR[0];
+    const T pl = gm1 * (UL[2] - T(0.5) * UL[1] * rf.ul), pr = gm1 * (UR[2] - T(0.5) * UR[1] * rf.ur);
+    rf.Hl = (UL[2] + pl) / UL[0];
+    rf.Hr = (UR[2] + pr) / UR[0];
+    rf.sl = sq_root(UL[0]);
+    rf.sr = sq_root(UR[0]);
+    rf.ut = (rf.sl * rf.ul + rf.sr * rf.ur) / (rf.sl + rf.sr);
+    rf.Ht = (rf.sl * rf.Hl + rf.sr * rf.Hr) / (rf.sl + rf.sr);
+    D2 ut = dconst<T, 2>(rf.ut), Ht = dconst<T, 2>(rf.Ht);
+    ut.d[0] = T(1);
+    Ht.d[1] = T(1);
+    const D2 half = dconst<T, 2>(T(0.5)), g = dconst<T, 2>(gm1), one = dconst<T, 2>(T(1));
+    const D2 c2 = g * (Ht - half * ut * ut);
+    const D2 c = dsqrt(c2);
+    const D2 b1 = g / c2;
+    const D2 b2 = half * ut * ut * b1;
+    const D2 mh = dconst<T, 2>(T(-0.5));
     R[0][0] = one;
     R[0][1] = one;
     R[0][2] = one;
@@ -124,12 +138,30 @@ __device__ __forceinline__ void frame1d_dual(const T UL[3], const T UR[3], T gm1
     L[0][2] = half * b1;
     L[1][0] = one - b2;
     L[1][1] = b1 * ut;
-    L[1][2] = dconst<T, 6>(T(0)) - b1;
+    L[1][2] = dconst<T, 2>(T(0)) - b1;
     L[2][0] = half * (b2 - ut / c);
     L[2][1] = mh * (b1 * ut - one / c);
     L[2][2] = half * b1;
 }
 
+// (lambda_u~, lambda_H~) -> lambda of (rho, m, E) of the left (lx[0..2]) and
+// right (lx[3..5]) cells: u~ = (sl ul + sr ur)/(sl + sr), H~ likewise, with
+// s = sqrt(rho), u = m/rho, H = (E + p)/rho, p = (g-1)(E - m u/2).
+template <typename T>
+__device__ __forceinline__ void roe_chain(const RoeFace<T> &rf, T lut, T lHt, T gm1, T lx[6]) {
+    const T iS = T(1) / (rf.sl + rf.sr);
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const T s = side ? rf.sr : rf.sl, u = side ? rf.ur : rf.ul, H = side ? rf.Hr : rf.Hl;
+        const T rho = side ? rf.rr : rf.rl;
+        const T irho = T(1) / rho;
+        const T lu = lut * s * iS, lH = lHt * s * iS;
+        const T ls = (lut * (u - rf.ut) + lHt * (H - rf.Ht)) * iS;
+        lx[3 * side + 0] = -lu * u * irho + lH * (T(0.5) * gm1 * u * u - H) * irho + ls * (T(0.5) / s);
+        lx[3 * side + 1] = (lu - lH * gm1 * u) * irho;
+        lx[3 * side + 2] = lH * (T(1) + gm1) * irho;
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void add_to(T *p, T v) {
@@ -142,6 +174,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
     __shared__ T s_gp[WPB][3][WC];
     __shared__ T s_gm[WPB][3][WC];
     __shared__ T s_coef[WPB][92];
+    __shared__ T s_uH[WPB][2][WC];  // velocity and total enthalpy of each staged cell
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
     const T alpha = p.alpha_ptr ? T(*p.alpha_ptr) : T(__longlong_as_double((long long)p.ctl->amax[p.slot_in][0]));
@@ -178,6 +211,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
                 sgp[k][c] = T(0.5) * (F[k] + alpha * Uc[k]);
                 sgm[k][c] = T(0.5) * (F[k] - alpha * Uc[k]);
             }
+            s_uH[warp][0][c] = u;
+            s_uH[warp][1][c] = (Uc[2] + pr) / Uc[0];
         }
         __syncwarp();
         const int j = c0 - 2 + lane;  // face j+1/2
@@ -188,8 +223,9 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
             UL[k] = sU[k][lane + 3];
             UR[k] = sU[k][lane + 4];
         }
-        Dual<T, 6> Ld[3][3], Rd[3][3];
-        frame1d_dual<T>(UL, UR, gm1, Ld, Rd);
+        Dual<T, 2> Ld[3][3], Rd[3][3];
+        RoeFace<T> rf;
+        frame1d_dual<T>(UL, UR, gm1, Ld, Rd, rf);
         T qp[3][7], qm[3][7];
         unsigned word = 0;
 #pragma unroll
@@ -206,8 +242,10 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
                 qp[k][t] = sp;
                 qm[k][t] = sm;
             }
-            word |= cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT, kt) << (3 * k);
-            word |= cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT, kt) << (3 * (3 + k));
+            if (!p.masks) {  // recorded masks make the cutoff unnecessary
+                word |= cutoff_bits(qp[k][1], qp[k][2], qp[k][3], qp[k][4], qp[k][5], eps, CT, kt) << (3 * k);
+                word |= cutoff_bits(qm[k][5], qm[k][4], qm[k][3], qm[k][2], qm[k][1], eps, CT, kt) << (3 * (3 + k));
+            }
         }
         const unsigned wl = __shfl_up_sync(0xffffffffu, word, 1);
         const unsigned wr = __shfl_down_sync(0xffffffffu, word, 1);
@@ -270,10 +308,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
                     }
                 }
                 // G+- = (F +- alpha U)/2  ->  lambda_U = (A^T (lgp + lgm) + alpha (lgp - lgm))/2
-                const T r0 = sU[0][lane + t], m0 = sU[1][lane + t], E0 = sU[2][lane + t];
-                const T u = m0 / r0;
-                const T pr = gm1 * (E0 - T(0.5) * m0 * u);
-                const T H = (E0 + pr) / r0;
+                const T u = s_uH[warp][0][lane + t], H = s_uH[warp][1][lane + t];
                 const T gam = gm1 + T(1);
                 const T s0 = lgp[0] + lgm[0], s1 = lgp[1] + lgm[1], s2 = lgp[2] + lgm[2];
                 // A = [[0,1,0],[(g-3)/2 u^2,(3-g)u,g-1],[u((g-1)/2 u^2 - H), H-(g-1)u^2, g u]]
@@ -287,17 +322,19 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
 #pragma unroll
                 for (int c = 0; c < 3; c++) add_to(&out[(size_t)c * n + cell], lu[c]);
             }
-            // frame: lambda_(UL, UR) = sum lambda_L dL/dx + lambda_R dR/dx
-            T lx[6];
+            // frame: lambda_(u~, H~) = sum lambda_L dL/d. + lambda_R dR/d., then to the cells
+            T lroe[2];
 #pragma unroll
-            for (int d = 0; d < 6; d++) {
+            for (int d = 0; d < 2; d++) {
                 T acc = T(0);
 #pragma unroll
                 for (int a = 0; a < 3; a++)
 #pragma unroll
                     for (int b = 0; b < 3; b++) acc = acc + lL[a][b] * Ld[a][b].d[d] + lR[a][b] * Rd[a][b].d[d];
-                lx[d] = acc;
+                lroe[d] = acc;
             }
+            T lx[6];
+            roe_chain(rf, lroe[0], lroe[1], gm1, lx);
             const int cl = ghost_map(j, n, p.bc_lo, p.bc_hi), cr = ghost_map(j + 1, n, p.bc_lo, p.bc_hi);
 #pragma unroll
             for (int c = 0; c < 3; c++) {
