@@ -142,11 +142,13 @@ def reference_arm(args, world, rank):
     val = n * steps / dt / 1e9
     line = {
         "impl": "reference", "metric": "TENO7 RK3 Gcell-updates/s (1D Euler, tiled Shu-Osher)", "value": val,
-        "unit": "Gcell-steps/s", "n_gpus": 0, "steps": steps, "warmup": args.warmup,
+        "unit": "Gcell-steps/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"Shu-Osher profile tiled x{tiles} (N={n}, dx=1/160), zero-gradient, CFL 0.5",
-                   "sample_of": f"N={N1 * TILES}"},
+        "config": {"workload": f"Shu-Osher profile (1600 cells on [-5,5], dx=1/160) tiled x{TILES}, "
+                               f"N={N1 * TILES} cells, zero-gradient ends, CFL 0.5, device-side dt",
+                   "sample": f"the same profile tiled x{tiles} (N={n}) on the host cores",
+                   "parallelism": "host, one thread"},
         "cpu_baseline": {"value": val, "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{steps} RK3 steps on {n} cells (single-threaded C oracle)"},
         "e2e": {"value": val, "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -383,7 +385,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tiles", type=int, default=TILES)
-    ap.add_argument("--ref-tiles", type=int, default=8)
+    ap.add_argument("--ref-tiles", type=int, default=64)
     ap.add_argument("--f64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
