@@ -835,6 +835,36 @@ __device__ __forceinline__ float wavespeed1d_fast(const float *Uc, float gm1, fl
     return fabsf(u) + c;
 }
 
+// Conversions between the FP64 state and the FP32 reconstruction of the
+// mixed-precision form, by integer operations on the bit patterns, so that
+// they use the integer pipe rather than the FP64 pipe (whose rate on GB300 is
+// 1/64 of FP32).  to_f32: truncation toward zero (exact for every double
+// that a float represents; |x| < 2^-126 flushes to a signed zero; overflow
+// gives infinity, NaN stays NaN).  to_f64: exact for normal floats and zeros
+// (subnormal floats flush to a signed zero).  Overloads on float are the
+// identity, for the FP32 state.
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+    unsigned f = sign | (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    if (e < 897u) f = sign;
+    if (e > 1150u) f = sign | ((e == 2047u && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u);
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ double to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu, sign = u & 0x80000000u;
+    unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + (896u << 20)), lo = u << 29;
+    if (e == 0u) {
+        hi = sign;
+        lo = 0u;
+    }
+    if (e == 255u) hi = sign | 0x7ff00000u | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Slot masks of the 6 x 5-bit word (see above).
 constexpr unsigned SLOT_HI = 0x21084210u;   // bit 4 of every slot
 constexpr unsigned SLOT_MID = 0x1CE739CEu;  // bits 3..1 of every slot
@@ -917,8 +947,8 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (gb < 0 || gb >= n) gb = ghost_map(gb, n, A.bc_lo, A.bc_hi);
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            ua[k] = (float)Us[(size_t)k * cs + ga];
-            ub[k] = (lane < WS - 32) ? (float)Us[(size_t)k * cs + gb] : 0.f;
+            ua[k] = to_f32(Us[(size_t)k * cs + ga]);
+            ub[k] = (lane < WS - 32) ? to_f32(Us[(size_t)k * cs + gb]) : 0.f;
         }
     };
     int tile = tile0;
@@ -1126,7 +1156,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
             float of[M];
 #pragma unroll
             for (int k = 0; k < M; k++) {
-                const double d = (double)fprev[k] - (double)fh[k];
+                const double d = to_f64(fprev[k]) - to_f64(fh[k]);
                 if (A.rhs_mode) {
                     o[k] = d * idxD;
                 } else {
@@ -1139,7 +1169,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                         o[k] = fma(2.0 / 3.0, v, (1.0 / 3.0) * (double)u0r[k]);
                 }
                 out[(size_t)k * cs + i] = (S)o[k];
-                of[k] = (float)o[k];
+                of[k] = to_f32(o[k]);
             }
             if (!A.rhs_mode) {
                 int wflag = 0;

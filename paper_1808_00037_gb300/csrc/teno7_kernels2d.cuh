@@ -653,8 +653,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         if (gb < 0 || gb >= nx) gb = ghost_map(gb, nx, p.bc[0], p.bc[1]);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            ua[k] = (float)row[(size_t)k * N + ga];
-            ub[k] = (lane < WS - 32) ? (float)row[(size_t)k * N + gb] : 0.f;
+            ua[k] = to_f32(row[(size_t)k * N + ga]);
+            ub[k] = (lane < WS - 32) ? to_f32(row[(size_t)k * N + gb]) : 0.f;
         }
     };
     const long tstride = (long)gridDim.x * WPB;
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if constexpr (MIXED)
-                    R[(size_t)k * N + (size_t)y * nx + j] = ((double)fprev[k] - (double)fh[k]) * idxD;
+                    R[(size_t)k * N + (size_t)y * nx + j] = (to_f64(fprev[k]) - to_f64(fh[k])) * idxD;
                 else
                     R[(size_t)k * N + (size_t)y * nx + j] = (fprev[k] - fh[k]) * idx;
             }
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             int y = r0 - 5 + r;
             if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ust[sI][k] = (float)Us[(size_t)k * N + (size_t)y * nx + x];
+            for (int k = 0; k < 4; k++) Ust[sI][k] = to_f32(Us[(size_t)k * N + (size_t)y * nx + x]);
         }
     }
 #pragma unroll
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if constexpr (MIXED)
-                    s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = ((double)fprev[k] - (double)fh[k]) * idyD;
+                    s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = (to_f64(fprev[k]) - to_f64(fh[k])) * idyD;
                 else
                     s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = (fprev[k] - fh[k]) * idy;
             }
@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
                     }
                 }
                 out[(size_t)k * N + gi] = o;
-                of[k] = (float)o;
+                of[k] = to_f32(o);
             }
             if (!p.rhs_mode) {
                 int wflag = 0;
