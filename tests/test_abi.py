@@ -75,3 +75,18 @@ def test_create_rejects_bad_scheme_without_touching_the_device():
     g = B.t7_grid(B.T7_EULER2D, B.T7_F64, 64, 64, 0.1, 0.1, bc, 1.4, 1.0, 1e-5, -1.0, -1.0, B.T7_TENO5)
     assert lib.t7_create(ctypes.byref(g), None, ctypes.byref(h)) == B.T7_EINVAL
     assert not h.value
+
+
+def test_create_rejects_empty_and_oversized_grids_without_touching_the_device():
+    """nx or ny < 1, a 1D grid with ny != 1, and grids whose m * nx * ny exceeds
+    the 32-bit index range the kernels use are refused with T7_EINVAL before
+    any allocation."""
+    from paper_1808_00037_gb300 import binding as B
+    lib = B.load()
+    bc = (ctypes.c_int * 4)(0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    for sys_, nx, ny in ((B.T7_EULER1D, 0, 1), (B.T7_EULER1D, 16, 2), (B.T7_EULER2D, 16, 0),
+                         (B.T7_EULER1D, 715_827_883, 1), (B.T7_EULER2D, 23_171, 23_171)):
+        g = B.t7_grid(sys_, B.T7_F32, nx, ny, 0.1, 0.1, bc, 1.4, 1.0, 1e-5, -1.0, -1.0)
+        assert lib.t7_create(ctypes.byref(g), None, ctypes.byref(h)) == B.T7_EINVAL, (sys_, nx, ny)
+        assert not h.value

@@ -339,3 +339,31 @@ def test_run_host_pinned_direct_write_matches_device_run(prec, dtype):
         sh, th = c.run_host(Uh, 0.5, max_steps=steps)
         assert (sd, td) == (sh, th) == (steps, td)
         assert torch.equal(Ud.cpu(), Uh)
+
+
+@pytest.mark.parametrize("prec,dtype", [(B.T7_F32, torch.float32), (B.T7_MIXED, torch.float64)])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 29, 30, 31, 58, 59, 87])
+def test_small_and_ragged_sizes_f32_and_mixed(prec, dtype, n):
+    """Sizes around the 29-cell warp tile (empty tail, one cell past a tile,
+    fewer cells than a stencil) on smooth periodic Euler data and on a
+    zero-gradient Sod tube: the FP32 and mixed RHS match the oracle within the
+    FP32 bound on cells whose faces' codes agree, and a 3-step run stays within
+    the smooth-case tolerance 1e-5 (smooth) or the shock-case bound 2e-3 (Sod)
+    of the oracle's, relative L1."""
+    for U, dx, bc, tol in ((*I.random_euler_smooth(5, n)[:2], (0, 0), 1e-5),
+                           (*I.riemann_tube(n, *I.SOD)[:2], (1, 1), 2e-3)):
+        ro, _, mo = oracle.rhs_1d(oracle.SYS_EULER1D, U, dx, bc=bc, want_masks=True)
+        c = ctx(oracle.SYS_EULER1D, n, dx, bc=bc, prec=prec)
+        rg, mg = c.euler_rhs(dev(U, dtype), want_masks=True)
+        c.sync()
+        mg = mg.cpu().numpy()
+        face_ok = np.all(mg == mo, axis=(0, 1))
+        cell_ok = face_ok[:-1] & face_ok[1:]
+        rho, u, pr = I.cons_to_prim_1d(U)
+        fmax = np.max(np.abs(np.stack([U[1], U[1] * u + pr, u * (U[2] + pr)])))
+        assert np.max(np.abs(host(rg) - ro)[:, cell_ok], initial=0.0) <= 64 * 2.0**-24 * fmax / dx
+        Uo, so, _, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=math.inf, cfl=0.5, bc=bc, max_steps=3)
+        Ug = dev(U, dtype)
+        sg, _ = c.run(Ug, 0.5, max_steps=3)
+        assert sg == so == 3
+        assert np.abs(host(Ug) - Uo).sum() <= tol * np.abs(Uo).sum()
