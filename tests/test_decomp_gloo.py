@@ -80,3 +80,84 @@ def test_partition_covers_domain():
             assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
             sizes = [h - l for l, h in ranges]
             assert max(sizes) - min(sizes) <= 1
+
+
+def _case2d(name):
+    if name == "quadrants":
+        U, dx, dy, _ = I.quadrants_2d(3, 26, 30)
+        return U, dx, dy, False, 6
+    U, dx, dy = I.random_smooth_2d(4, 24, 28)
+    return U, dx, dy, True, 6
+
+
+def _worker2d(rank, world, port, name):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        U, dx, dy, periodic, nsteps = _case2d(name)
+        bcx = (0, 0) if periodic else (1, 1)
+        lo, hi = decomp.partition(U.shape[1], world, rank)
+
+        def rhs(P, alpha):
+            return oracle.rhs_2d(P, dx, dy, bc=(bcx[0], bcx[1], 1, 1), alpha=alpha)[0]
+
+        Ul, steps, t = decomp.rk3_run_2d(U[:, lo:hi], rhs, oracle.alpha_2d, dx=dx, dy=dy, cfl=0.4,
+                                         t_end=np.inf, max_steps=nsteps, periodic_y=periodic)
+        sums = decomp.global_sums(Ul)
+        parts = [None] * world
+        dist.all_gather_object(parts, (lo, Ul, steps, t))
+        if rank == 0:
+            bc = (0, 0, 0, 0) if periodic else (1, 1, 1, 1)
+            Uo, so, to, st = oracle.run_2d(U, dx, dy, cfl=0.4, max_steps=nsteps, bc=bc)
+            full = np.concatenate([p[1] for p in sorted(parts, key=lambda p: p[0])], axis=1)
+            assert all(p[2] == so and p[3] == to for p in parts)
+            assert np.array_equal(full, Uo)
+            assert np.allclose(sums, Uo.reshape(4, -1).sum(axis=1), rtol=1e-14, atol=0)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("name", ["quadrants", "smooth-periodic"])
+def test_2d_slab_decomposition_bit_identical(world, name):
+    """2D split along y: 4 halo rows per side, both alphas all-reduced at every
+    stage, the CFL step cfl / (ax/dx + ay/dy); gathered result bit-identical to
+    the unsplit oracle run; FP64 all-reduced domain sums equal the full sums."""
+    mp.spawn(_worker2d, args=(world, _free_port(), name), nprocs=world, join=True)
+
+
+def _worker_tubes(rank, world, port):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        U, off, dx, _ = I.riemann_tube_batch(3, 12, 24, 96)
+        costs = [(off[t + 1] - off[t]) ** 2 for t in range(12)]  # cells x steps, steps ~ cells
+        mine = decomp.shard_tubes(costs, world)[rank]
+        out = {t: oracle.run_1d(oracle.SYS_EULER1D, U[:, off[t]:off[t + 1]], dx[t], t_end=0.02, cfl=0.5,
+                                bc=(1, 1))[0] for t in mine}
+        parts = [None] * world
+        dist.all_gather_object(parts, out)
+        if rank == 0:
+            got = {k: v for p in parts for k, v in p.items()}
+            assert sorted(got) == list(range(12))
+            for t in range(12):
+                ref = oracle.run_1d(oracle.SYS_EULER1D, U[:, off[t]:off[t + 1]], dx[t], t_end=0.02, cfl=0.5,
+                                    bc=(1, 1))[0]
+                assert np.array_equal(got[t], ref)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_tube_sharding_gathers_every_tube_once():
+    """Tubes sharded by cost over 3 gloo ranks, each run where it landed, the
+    gather (the only collective) returns every tube once and unchanged."""
+    mp.spawn(_worker_tubes, args=(3, _free_port()), nprocs=3, join=True)
+
+
+def test_shard_tubes_balance():
+    rng = np.random.default_rng(5)
+    for world in (1, 2, 3, 8):
+        costs = rng.integers(256, 8192, 500).astype(float) ** 2
+        shards = decomp.shard_tubes(costs, world)
+        flat = sorted(t for s in shards for t in s)
+        assert flat == list(range(500))
+        loads = [costs[s].sum() for s in shards]
+        assert max(loads) <= costs.sum() / world + costs.max()
