@@ -21,6 +21,11 @@
  * with Roe-averaged eigenvectors and global Lax-Friedrichs splitting
  * (Remark 3; Sec. "One dimensional Euler equations"), and the third-order SSP
  * Runge-Kutta method (Sec. "The fundamental of the spatial solution").
+ * A scheme switch (or_set_scheme) replaces pass 2 by the fifth-order TENO
+ * baseline the paper compares with: each face's own three bits select a
+ * Table co1 polynomial (epsilon 1e-40 as given with Eq. TENO1).
+ * The 2D form (or_rhs_2d, or_run_2d) applies the same face procedure
+ * dimension by dimension, each direction in its own characteristic frame.
  *
  * Build with -O2 -ffp-contract=off and without fast-math, so that each
  * expression is evaluated exactly as written, one IEEE operation at a time.
