@@ -372,6 +372,44 @@ def bench_mixed(args, torch, B, U0, dx, res, dist, world):
     return out
 
 
+def bench_advection(args, torch, B, dist, world):
+    """Scalar advection u_t + u_x = 0, sin(pi x) on [-1, 1], periodic, N = 2^24
+    cells, CFL 0.2 (the advection configuration's data at a timed size): the
+    lightest system (m = 1), for its HBM fraction -- 8 m s bytes per
+    cell-step, one stage reads U (and U^n) and writes the stage state."""
+    n = 1 << 24
+    U0, dx, _ = I.advection_sine(n)
+    hbm_peak, peak_kind = peaks()
+    out = {"workload": f"advection sin(pi x) on [-1,1], N={n}, periodic, CFL 0.2"}
+    for name, prec, dtype, steps in (("f32", B.T7_F32, torch.float32, args.steps),
+                                     ("f64", B.T7_F64, torch.float64, max(2, args.steps // 10))):
+        ctx = B.Context(B.T7_SCALAR_ADVECTION, n, dx, prec=prec, bc=(0, 0, 0, 0), adv_speed=1.0)
+        U = torch.tensor(U0, dtype=dtype, device="cuda")
+        ctx.run(U, 0.2, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(ctx.stream)
+        done, _ = ctx.run(U, 0.2, max_steps=steps)
+        end.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        assert done == steps
+        s_ = 4 if name == "f32" else 8
+        gbs = 8 * s_ * n * steps / (ms * 1e-3) / 1e9
+        out[name] = {"value": n * steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s",
+                     "ms_per_step": ms / steps, "steps": steps,
+                     "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                             "peak_kind": peak_kind, "bytes_per_cell_step": 8 * s_}}
+        ctx.close()
+        del U
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -415,9 +453,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-teno5", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-advection", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
-    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint"], default=None,
+    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint", "advection"], default=None,
                     help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -439,6 +478,10 @@ def main():
     if args.only == "adjoint":
         if rank == 0:
             print(json.dumps({"only": "adjoint", **bench_adjoint(args, torch, B)}), flush=True)
+        return 0
+    if args.only == "advection":
+        if rank == 0:
+            print(json.dumps({"only": "advection", **bench_advection(args, torch, B, dist, world)}), flush=True)
         return 0
     if args.only in ("2d", "batch"):
         r2 = (bench_2d if args.only == "2d" else bench_batch)(args, torch, B, dist, world, rank)
@@ -511,6 +554,7 @@ def main():
         return 0
     res5 = None if args.no_teno5 else bench_teno5(args, torch, B, U0, dx, res, dist, world)
     resm = None if args.no_mixed else bench_mixed(args, torch, B, U0, dx, res, dist, world)
+    resv = None if args.no_advection else bench_advection(args, torch, B, dist, world)
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
     resa = None if (args.no_adjoint or rank != 0) else bench_adjoint(args, torch, B)
@@ -555,7 +599,7 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "mixed": resm, "teno5": res5, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
+        "f64": res["f64"], "mixed": resm, "teno5": res5, "advection": resv, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
