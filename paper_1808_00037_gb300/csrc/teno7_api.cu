@@ -37,6 +37,13 @@ struct t7_ctx {
     void *adj[3];          // adjoint work vectors (allocated on first use)
     uint8_t *adj_masks[3]; // FP32: forward masks of the three stage states
     t7::DevCtl *ctl_host;  // pinned mirror for status reads
+    // CUDA graph of one chunk of RK3 steps of t7_run (small 1D problems, where
+    // launch overhead dominates): captured on an internal stream for the
+    // state pointer g_U, replayed behind events on the context's stream
+    cudaStream_t gstream;
+    cudaEvent_t g_in, g_out;
+    cudaGraphExec_t gexec;
+    void *g_U;
     char err[512];
 };
 
@@ -311,6 +318,10 @@ t7_status t7_destroy(t7_ctx *c) {
     }
     if (c->ctl) cudaFree(c->ctl);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->g_in) cudaEventDestroy(c->g_in);
+    if (c->g_out) cudaEventDestroy(c->g_out);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;
     return T7_OK;
 }
@@ -406,6 +417,51 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
     return T7_OK;
 }
 
+// Steps per t7_run chunk, and the size up to which a chunk runs as one CUDA
+// graph (below it a stage launch lasts a few microseconds and launch overhead
+// dominates; above it the 3 launches per step cost nothing measurable).
+constexpr int RUN_CHUNK = 64;
+constexpr size_t GRAPH_MAX_VALUES = size_t(1) << 21;
+
+// One chunk of RUN_CHUNK steps of U as a replayed graph (captured on first use
+// for this U).  Returns false, with no work enqueued, if the graph cannot be
+// made; the caller then launches the steps one by one.
+static bool run_chunk_graph(t7_ctx *c, void *U) {
+    if (!c->gstream) {
+        if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->g_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->g_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    if (!c->gexec || c->g_U != U) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        cudaStream_t user = c->stream;
+        c->stream = c->gstream;
+        cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        for (int q = 0; q < RUN_CHUNK && e == cudaSuccess; q++) e = rk3(c, U, -1.0);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+        c->stream = user;
+        if (e != cudaSuccess || e2 != cudaSuccess || !g ||
+            cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            c->gexec = nullptr;
+            cudaGetLastError();
+            return false;
+        }
+        cudaGraphDestroy(g);
+        c->g_U = U;
+    }
+    return cudaEventRecord(c->g_in, c->stream) == cudaSuccess &&
+           cudaStreamWaitEvent(c->gstream, c->g_in, 0) == cudaSuccess &&
+           cudaGraphLaunch(c->gexec, c->gstream) == cudaSuccess &&
+           cudaEventRecord(c->g_out, c->gstream) == cudaSuccess &&
+           cudaStreamWaitEvent(c->stream, c->g_out, 0) == cudaSuccess;
+}
+
 // t7_run's loop; final_out (nullable, only with t_end = inf) receives the
 // result of the last step directly (e.g. mapped host memory).
 static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out,
@@ -417,13 +473,16 @@ static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha");
     // Steps are launched in chunks; between chunks the host polls whether the
     // device-side clock has reached t_end (a step past it is a no-op anyway).
-    const int chunk = 64;
+    const bool graphs = is_1d(c->g.sys) && c->ncell * c->m <= GRAPH_MAX_VALUES;
     int launched = 0;
     while (launched < max_steps) {
-        int k = max_steps - launched < chunk ? max_steps - launched : chunk;
-        for (int q = 0; q < k; q++) {
-            void *last = (final_out && launched + q == max_steps - 1) ? final_out : nullptr;
-            if ((e = rk3(c, U, -1.0, last)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+        int k = max_steps - launched < RUN_CHUNK ? max_steps - launched : RUN_CHUNK;
+        const bool last_chunk = final_out && launched + k == max_steps;
+        if (!(graphs && k == RUN_CHUNK && !last_chunk && run_chunk_graph(c, U))) {
+            for (int q = 0; q < k; q++) {
+                void *last = (final_out && launched + q == max_steps - 1) ? final_out : nullptr;
+                if ((e = rk3(c, U, -1.0, last)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+            }
         }
         launched += k;
         if (isfinite(t_end)) {
