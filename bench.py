@@ -173,6 +173,40 @@ def _oracle_sample(budget_s, tiles=4):
     return n * steps, time.perf_counter() - t0
 
 
+def _oracle_per_form(budget_s=1.5):
+    """Single-threaded oracle rates on samples of the other forms' workloads
+    (each about budget_s seconds): scalar advection (sin(pi x), 4096 cells),
+    2D quadrants (256^2 cells of the 2048^2 recipe) and ragged tubes (the
+    first tubes of the 4096-tube batch, their own dx)."""
+    import oracle
+    oracle.build()
+    out = {}
+    U, dx, _ = I.advection_sine(4096)
+    cells, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        U, s, _, _ = oracle.run_1d(oracle.SYS_ADVECTION, U, dx, t_end=math.inf, cfl=0.2, max_steps=20)
+        cells += U.shape[1] * s
+    out["advection"] = {"value": cells / (time.perf_counter() - t0) / 1e9, "unit": "Gcell-steps/s",
+                        "sample": "sin(pi x), 4096 cells, CFL 0.2"}
+    U, dx, dy, _ = I.quadrants_2d(2024, 256, 256)
+    cells, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        U, s, _, _ = oracle.run_2d(U, dx, dy, cfl=0.4, max_steps=1)
+        cells += 256 * 256 * s
+    out["euler2d"] = {"value": cells / (time.perf_counter() - t0) / 1e9, "unit": "Gcell-steps/s",
+                      "sample": "four-quadrant data, 256^2 cells"}
+    Ub, off, dxs, _ = I.riemann_tube_batch(7, 64)
+    cells, t0, t = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and t < 64:
+        Ut = Ub[:, off[t]:off[t + 1]]
+        _, s, _, _ = oracle.run_1d(oracle.SYS_EULER1D, Ut, dxs[t], t_end=math.inf, cfl=0.5, bc=(1, 1), max_steps=5)
+        cells += Ut.shape[1] * s
+        t += 1
+    out["batch"] = {"value": cells / (time.perf_counter() - t0) / 1e9, "unit": "Gcell-steps/s",
+                    "sample": f"5 steps of each of the first {t} tubes of the batch recipe"}
+    return out
+
+
 def cpu_baseline(budget_s=10.0, allcore_s=1.25):
     """The oracle on the host cores: single-threaded for budget_s, then one
     independent copy of the sample per core (processes started with spawn) for
@@ -190,7 +224,7 @@ def cpu_baseline(budget_s=10.0, allcore_s=1.25):
     return {"value": total / span / 1e9, "unit": "Gcell-steps/s", "cores": ncores, "kind": "oracle",
             "sample": f"the Shu-Osher profile tiled x4 (N={N1 * 4}), one independent copy per core, "
                       f"{allcore_s} s each (wall {wall:.1f} s with process start-up)",
-            "single_thread": one}
+            "single_thread": one, "single_thread_other_forms": _oracle_per_form()}
 
 
 def bench_2d(args, torch, B, dist, world, rank):
