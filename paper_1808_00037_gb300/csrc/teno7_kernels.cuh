@@ -124,16 +124,19 @@ __device__ __forceinline__ unsigned cutoff_bits(double w0, double w1, double w2,
     // Eq. smooth_expl
     double s0a = w0 - 4.0 * w1 + 3.0 * w2;
     double s0b = w0 - 2.0 * w1 + w2;
-    double s1a = w1 - w3;
-    double s1b = w1 - 2.0 * w2 + w3;
     double s2a = 3.0 * w2 - 4.0 * w3 + w4;
     double s2b = w2 - 2.0 * w3 + w4;
     double b0 = 0.25 * (s0a * s0a) + (13.0 / 12.0) * (s0b * s0b);
-    double b1 = 0.25 * (s1a * s1a) + (13.0 / 12.0) * (s1b * s1b);
     double b2 = 0.25 * (s2a * s2a) + (13.0 / 12.0) * (s2b * s2b);
     // Eq. tau5, Eq. TENO1 with C = 1, q = 6 (squared, squared again, times square)
     double tau = fabs(b0 - b2);
-    if (tau < kt * (fmin(fmin(b0, b1), b2) + eps)) return 7u;  // every stencil kept (see keep_all_factor)
+    // every stencil kept (see keep_all_factor); beta_min >= 0, so tau < kt eps
+    // already suffices and beta_1 is not needed
+    if (tau < kt * eps) return 7u;
+    double s1a = w1 - w3;
+    double s1b = w1 - 2.0 * w2 + w3;
+    double b1 = 0.25 * (s1a * s1a) + (13.0 / 12.0) * (s1b * s1b);
+    if (tau < kt * (fmin(fmin(b0, b1), b2) + eps)) return 7u;
     double g0 = 1.0 + tau / (b0 + eps);
     double g1 = 1.0 + tau / (b1 + eps);
     double g2 = 1.0 + tau / (b2 + eps);
@@ -771,15 +774,22 @@ __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 
                                         float kt, unsigned &cp, unsigned &cm) {
     const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
     const float2 s0b = __fadd2_rn(__ffma2_rn(f2(-2.f), w1, w0), w2);
-    const float2 s1a = __ffma2_rn(f2(-1.f), w3, w1);
-    const float2 s1b = __fadd2_rn(__ffma2_rn(f2(-2.f), w2, w1), w3);
     const float2 s2a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w3, w4));
     const float2 s2b = __fadd2_rn(__ffma2_rn(f2(-2.f), w3, w2), w4);
     const float2 b0 = __ffma2_rn(s0b, __fmul2_rn(f2(13.f / 3.f), s0b), __fmul2_rn(s0a, s0a));
-    const float2 b1 = __ffma2_rn(s1b, __fmul2_rn(f2(13.f / 3.f), s1b), __fmul2_rn(s1a, s1a));
     const float2 b2 = __ffma2_rn(s2b, __fmul2_rn(f2(13.f / 3.f), s2b), __fmul2_rn(s2a, s2a));
     const float2 td = __ffma2_rn(f2(-1.f), b2, b0);
     const float2 tau = make_float2(fabsf(td.x), fabsf(td.y));
+    // every stencil kept (see keep_all_factor): beta_min >= 0, so tau < kt eps
+    // already suffices, before beta_1 is formed
+    if (tau.x < kt * eps4 && tau.y < kt * eps4) {
+        cp = 7u;
+        cm = 7u;
+        return;
+    }
+    const float2 s1a = __ffma2_rn(f2(-1.f), w3, w1);
+    const float2 s1b = __fadd2_rn(__ffma2_rn(f2(-2.f), w2, w1), w3);
+    const float2 b1 = __ffma2_rn(s1b, __fmul2_rn(f2(13.f / 3.f), s1b), __fmul2_rn(s1a, s1a));
     const float bmx = fminf(fminf(b0.x, b1.x), b2.x), bmy = fminf(fminf(b0.y, b1.y), b2.y);
     // every stencil of both windows kept (see keep_all_factor); tested first
     // with the unfloored epsilon, since the floor below only raises it
