@@ -424,15 +424,17 @@ constexpr int RUN_CHUNK = 64;
 constexpr size_t GRAPH_MAX_VALUES = size_t(1) << 21;
 
 // One chunk of RUN_CHUNK steps of U as a replayed graph (captured on first use
-// for this U).  Returns false, with no work enqueued, if the graph cannot be
-// made; the caller then launches the steps one by one.
-static bool run_chunk_graph(t7_ctx *c, void *U) {
+// for this U).  Returns 1 when the chunk was enqueued; 0, with no work
+// enqueued, if the graph cannot be made or launched (the caller then launches
+// the steps one by one); -1 if the chunk was launched but could not be ordered
+// before later work on the context's stream.
+static int run_chunk_graph(t7_ctx *c, void *U) {
     if (!c->gstream) {
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->g_in, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->g_out, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
-            return false;
+            return 0;
         }
     }
     if (!c->gexec || c->g_U != U) {
@@ -450,16 +452,21 @@ static bool run_chunk_graph(t7_ctx *c, void *U) {
             if (g) cudaGraphDestroy(g);
             c->gexec = nullptr;
             cudaGetLastError();
-            return false;
+            return 0;
         }
         cudaGraphDestroy(g);
         c->g_U = U;
     }
-    return cudaEventRecord(c->g_in, c->stream) == cudaSuccess &&
-           cudaStreamWaitEvent(c->gstream, c->g_in, 0) == cudaSuccess &&
-           cudaGraphLaunch(c->gexec, c->gstream) == cudaSuccess &&
-           cudaEventRecord(c->g_out, c->gstream) == cudaSuccess &&
-           cudaStreamWaitEvent(c->stream, c->g_out, 0) == cudaSuccess;
+    if (cudaEventRecord(c->g_in, c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->gstream, c->g_in, 0) != cudaSuccess ||
+        cudaGraphLaunch(c->gexec, c->gstream) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaEventRecord(c->g_out, c->gstream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, c->g_out, 0) != cudaSuccess)
+        return -1;
+    return 1;
 }
 
 // t7_run's loop; final_out (nullable, only with t_end = inf) receives the
@@ -478,7 +485,9 @@ static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_
     while (launched < max_steps) {
         int k = max_steps - launched < RUN_CHUNK ? max_steps - launched : RUN_CHUNK;
         const bool last_chunk = final_out && launched + k == max_steps;
-        if (!(graphs && k == RUN_CHUNK && !last_chunk && run_chunk_graph(c, U))) {
+        const int g = (graphs && k == RUN_CHUNK && !last_chunk) ? run_chunk_graph(c, U) : 0;
+        if (g < 0) return cuda_fail(c, cudaGetLastError(), "ordering a graph chunk");
+        if (g == 0) {
             for (int q = 0; q < k; q++) {
                 void *last = (final_out && launched + q == max_steps - 1) ? final_out : nullptr;
                 if ((e = rk3(c, U, -1.0, last)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
