@@ -207,3 +207,22 @@ def test_2d_uniform_steady(orc):
     for bc in ((0, 0, 0, 0), (1, 1, 1, 1)):
         r, _, _ = orc.rhs_2d(U, 0.1, 0.1, bc=bc)
         assert np.all(r == 0.0)
+
+
+def test_shu_osher_self_convergence(orc):
+    """Shu-Osher has no exact solution (the paper compares with a fine WENO-JS
+    run); the oracle's own solutions at N = 200, 400, 800 to t = 1.8 approach
+    its N = 1600 solution (sampled at the coarse cell centres), each doubling
+    at least halving the mean density error."""
+    sols = {}
+    for n in (200, 400, 800, 1600):
+        U, dx = I.shu_osher(n)
+        Uf, _, t, st = orc.run_1d(orc.SYS_EULER1D, U, dx, t_end=1.8, cfl=0.5, bc=(1, 1))
+        assert st == 0 and t == 1.8
+        sols[n] = Uf[0]
+    errs = []
+    for n in (200, 400, 800):
+        r = 1600 // n
+        f = sols[1600].reshape(n, r)
+        errs.append(np.abs(sols[n] - 0.5 * (f[:, r // 2 - 1] + f[:, r // 2])).mean())
+    assert errs[1] < 0.5 * errs[0] and errs[2] < 0.5 * errs[1], errs
