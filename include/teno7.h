@@ -185,8 +185,16 @@ t7_status t7_rk3_step_adjoint_recorded(t7_ctx *ctx, const void *U_in, const void
  *                advanced in place
  *   offsets      host, ntubes + 1 ascending, offsets[0] = 0, offsets[ntubes] = nx
  *   dx           host, per-tube cell width (epsilon = dx^3 per tube)
- *   group_warps  1, 2, 4 or 8 warps per tube; 0 = the value chosen by
- *                t7_batch_autotune (8 if never tuned)
+ *   group_warps  1, 2, 4 or 8: that many warps per tube, for every tube;
+ *                -1, -2, -4 or -8: the same group size, but the costliest
+ *                tubes -- those whose estimated cost (cells^2) is above half
+ *                of one group's share of the whole batch -- run first on
+ *                whole 8-warp CTAs, so that no single tube sets the run time
+ *                (with -8 there is nothing to split off);
+ *                0: as -G with G chosen by t7_batch_autotune (8 if never
+ *                tuned).  Any other value: T7_EINVAL.
+ *                The results do not depend on this argument: every tube's
+ *                arithmetic is the same for every group size.
  *   steps_out, t_out  host or NULL, per tube
  * Synchronises.  Returns non-physical / non-finite states met in any tube. */
 t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const double *dx, int ntubes, double t_end,
@@ -196,7 +204,11 @@ t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const doubl
  * for group_warps = 1, 2, 4, 8 on a device copy of U (U is not modified),
  * keeps the fastest in the context for later t7_batch_run calls, and returns
  * it in *group_out (nullable); ms_out (nullable, 4 floats) receives the trial
- * times.  Synchronises. */
+ * times.  Synchronises.  Trials of 10 or more steps are needed for the
+ * ranking to hold over a whole run: smaller groups run more tubes at once,
+ * whose joint working set (3 state copies per tube) can outgrow L2, and
+ * that cost only shows once each tube has taken several steps -- over 2 or
+ * 3 steps every group size streams its tubes in from DRAM alike. */
 t7_status t7_batch_autotune(t7_ctx *ctx, const void *U, const int64_t *offsets, const double *dx, int ntubes,
                             double cfl, int trial_steps, int *group_out, float *ms_out);
 

@@ -256,7 +256,7 @@ class Context:
                     "t7_batch_run")
         return steps, t
 
-    def batch_autotune(self, U, offsets, dx, cfl: float, trial_steps: int = 3):
+    def batch_autotune(self, U, offsets, dx, cfl: float, trial_steps: int = 20):
         """Pick group_warps (warps per tube) by timing trial steps; U is not modified.
         Returns (group_warps, trial milliseconds for 1, 2, 4, 8)."""
         off = np.ascontiguousarray(offsets, dtype=np.int64)

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -34,6 +35,7 @@ struct t7_ctx {
     int *b_order, *b_steps, *b_queue;
     int b_cap;
     int b_group;           // warps per tube chosen by t7_batch_autotune (0: not tuned)
+    std::vector<double> b_cost;  // estimated cost (cells^2) of the tubes in processing order
     void *adj[3];          // adjoint work vectors (allocated on first use)
     uint8_t *adj_masks[3]; // FP32: forward masks of the three stage states
     t7::DevCtl *ctl_host;  // pinned mirror for status reads
@@ -267,9 +269,8 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     if (!(g->CT > 0.0 && g->CT < 1.0)) return T7_EINVAL;
     if (g->scheme != T7_TENO7EXT && g->scheme != T7_TENO5) return T7_EINVAL;
     if (g->scheme == T7_TENO5 && !is_1d(g->sys)) return T7_EINVAL;  // the baseline runs the 1D systems
-    t7_ctx *c = new (std::nothrow) t7_ctx;
+    t7_ctx *c = new (std::nothrow) t7_ctx();  // value-initialised: every pointer and count zero
     if (!c) return T7_ENOMEM;
-    memset(c, 0, sizeof(*c));
     c->g = *g;
     c->m = nvars(g->sys);
     c->esize = g->prec == T7_F32 ? 4 : 8;
@@ -785,7 +786,15 @@ t7_status t7_rk3_step_adjoint_recorded(t7_ctx *c, const void *U_in, const void *
 }
 
 // ---------------------------------------------------------------- batch ----
-static t7_status batch_prepare(t7_ctx *c, const int64_t *offsets, const double *dx, int ntubes) {
+// Uploads the batch metadata and the processing order.  A tube's cost is
+// estimated as cells x steps, its step count as min(max_steps,
+// t_end alpha / (CFL dx)) with alpha the tube's wave speed in U (one pass of
+// batch1d_alpha_kernel): both the cell count and the wave speed, which varies
+// by more than an order of magnitude across random Riemann data, decide it.
+// With t_end infinite (the autotuner's fixed-step trials) every tube takes
+// max_steps steps and no pass is needed.
+static t7_status batch_prepare(t7_ctx *c, const void *U, const int64_t *offsets, const double *dx, int ntubes,
+                               double t_end, double cfl, int max_steps) {
     if (ntubes > c->b_cap) {
         cudaFree(c->b_off);
         cudaFree(c->b_dx);
@@ -802,32 +811,76 @@ static t7_status batch_prepare(t7_ctx *c, const int64_t *offsets, const double *
             cudaMalloc((void **)&c->b_t, sizeof(double) * ntubes) != cudaSuccess ||
             cudaMalloc((void **)&c->b_order, sizeof(int) * ntubes) != cudaSuccess ||
             cudaMalloc((void **)&c->b_steps, sizeof(int) * ntubes) != cudaSuccess ||
-            cudaMalloc((void **)&c->b_queue, sizeof(int)) != cudaSuccess) {
+            cudaMalloc((void **)&c->b_queue, 2 * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, T7_ENOMEM, "batch metadata allocation failed");
         }
         c->b_cap = ntubes;
     }
-    // costliest first: work ~ cells x steps ~ n^2 for comparable wave speeds
-    std::vector<int> order(ntubes);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const double na = (double)(offsets[a + 1] - offsets[a]), nb = (double)(offsets[b + 1] - offsets[b]);
-        return na * na > nb * nb;
-    });
     std::vector<long long> off(offsets, offsets + ntubes + 1);
     cudaError_t e;
-    if ((e = cudaMemcpy(c->b_off, off.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice)) !=
+    if ((e = cudaMemcpyAsync(c->b_off, off.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->b_dx, dx, sizeof(double) * ntubes, cudaMemcpyHostToDevice, c->stream)) !=
+            cudaSuccess)
+        return cuda_fail(c, e, "batch metadata copy");
+    const bool timed = std::isfinite(t_end);
+    std::vector<double> alpha(ntubes, 0.0);
+    if (timed) {
+        t7::Batch1D p;
+        memset(&p, 0, sizeof(p));
+        p.U = const_cast<void *>(U);
+        p.offsets = c->b_off;
+        p.ntubes = ntubes;
+        p.Ntot = c->g.nx;
+        p.gamma = c->g.gamma;
+        // the per-tube alphas go to b_t, which the batch launch overwrites with final times
+        e = c->g.prec == T7_F64 ? t7::launch_batch1d_alpha_f64(p, c->b_t, c->stream)
+                                : t7::launch_batch1d_alpha_f32(p, c->b_t, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(alpha.data(), c->b_t, sizeof(double) * ntubes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batch wave speeds");
+    }
+    std::vector<double> cost(ntubes);
+    for (int t = 0; t < ntubes; t++) {
+        double steps = (double)max_steps;
+        if (timed) {
+            const double s = t_end * alpha[t] / (cfl * dx[t]);
+            if (std::isfinite(s)) steps = std::min(steps, std::max(1.0, std::ceil(s)));
+        }
+        cost[t] = (double)(offsets[t + 1] - offsets[t]) * steps;
+    }
+    // costliest first
+    std::vector<int> order(ntubes);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    c->b_cost.assign(ntubes, 0.0);
+    for (int q = 0; q < ntubes; q++) c->b_cost[q] = cost[order[q]];  // in processing order
+    if ((e = cudaMemcpyAsync(c->b_order, order.data(), sizeof(int) * ntubes, cudaMemcpyHostToDevice, c->stream)) !=
             cudaSuccess ||
-        (e = cudaMemcpy(c->b_dx, dx, sizeof(double) * ntubes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c->b_order, order.data(), sizeof(int) * ntubes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "batch metadata copy");
     return T7_OK;
 }
 
+// Tubes whose estimated cost exceeds half of a group's fair share of the whole
+// batch run on whole CTAs (the leading tubes of the costliest-first order), so
+// that the longest tube does not set the run time on a small group.
+static int batch_nbig(t7_ctx *c, int ntubes, int group) {
+    if (group >= 8 || ntubes < 1) return 0;
+    const int ngroups = c->g.prec == T7_F64 ? t7::batch1d_groups_f64(group) : t7::batch1d_groups_f32(group);
+    double total = 0.0;
+    for (int q = 0; q < ntubes; q++) total += c->b_cost[q];
+    const double share = total / (ngroups > 0 ? ngroups : 1);
+    int nbig = 0;
+    while (nbig < ntubes && c->b_cost[nbig] > 0.5 * share) nbig++;
+    return nbig;
+}
+
 static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, double cfl, int max_steps,
-                                int group) {
-    cudaError_t e = cudaMemsetAsync(c->b_queue, 0, sizeof(int), c->stream);
+                                int group, bool whole_cta_phase) {
+    cudaError_t e = cudaMemsetAsync(c->b_queue, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     t7::Batch1D p;
     memset(&p, 0, sizeof(p));
@@ -847,6 +900,7 @@ static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, do
     p.CT = c->g.CT;
     p.max_steps = max_steps;
     p.group_warps = group;
+    p.nbig = whole_cta_phase ? batch_nbig(c, ntubes, group) : 0;
     p.queue = c->b_queue;
     p.steps_out = c->b_steps;
     p.t_out = c->b_t;
@@ -874,11 +928,12 @@ t7_status t7_batch_run(t7_ctx *c, void *U, const int64_t *offsets, const double 
     t7_status st = batch_check(c, U, offsets, dx, ntubes);
     if (st) return st;
     if (!(cfl > 0.0) || !(t_end >= 0.0) || max_steps < 0) return fail(c, T7_EINVAL, "t7_batch_run: bad argument");
-    int group = group_warps > 0 ? group_warps : (c->b_group > 0 ? c->b_group : 8);
+    const int gw = group_warps < 0 ? -group_warps : group_warps;
+    int group = gw > 0 ? gw : (c->b_group > 0 ? c->b_group : 8);
     if (group != 1 && group != 2 && group != 4 && group != 8)
-        return fail(c, T7_EINVAL, "t7_batch_run: group_warps must be 1, 2, 4 or 8");
-    if ((st = batch_prepare(c, offsets, dx, ntubes))) return st;
-    cudaError_t e = batch_launch(c, U, ntubes, t_end, cfl, max_steps, group);
+        return fail(c, T7_EINVAL, "t7_batch_run: group_warps must be 0, +-1, +-2, +-4 or +-8");
+    if ((st = batch_prepare(c, U, offsets, dx, ntubes, t_end, cfl, max_steps))) return st;
+    cudaError_t e = batch_launch(c, U, ntubes, t_end, cfl, max_steps, group, group_warps <= 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "batch launch");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
     if (steps_out && (e = cudaMemcpy(steps_out, c->b_steps, sizeof(int) * ntubes, cudaMemcpyDeviceToHost)) !=
@@ -894,7 +949,7 @@ t7_status t7_batch_autotune(t7_ctx *c, const void *U, const int64_t *offsets, co
     t7_status st = batch_check(c, (void *)U, offsets, dx, ntubes);
     if (st) return st;
     if (!(cfl > 0.0) || trial_steps < 1) return fail(c, T7_EINVAL, "t7_batch_autotune: bad argument");
-    if ((st = batch_prepare(c, offsets, dx, ntubes))) return st;
+    if ((st = batch_prepare(c, U, offsets, dx, ntubes, INFINITY, cfl, trial_steps))) return st;
     const size_t bytes = c->ncell * c->m * c->esize;
     const int groups[4] = {1, 2, 4, 8};
     float best = 0.f;
@@ -906,7 +961,7 @@ t7_status t7_batch_autotune(t7_ctx *c, const void *U, const int64_t *offsets, co
         // every candidate advances the same copy of the state by trial_steps steps
         cudaError_t e = cudaMemcpyAsync(c->Uhost, U, bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-        if (e == cudaSuccess) e = batch_launch(c, c->Uhost, ntubes, INFINITY, cfl, trial_steps, groups[gi]);
+        if (e == cudaSuccess) e = batch_launch(c, c->Uhost, ntubes, INFINITY, cfl, trial_steps, groups[gi], false);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

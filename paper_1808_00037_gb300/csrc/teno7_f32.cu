@@ -12,6 +12,10 @@ cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s) { return launch
 cudaError_t launch_stage2d_mixed(const Stage2D &p, cudaStream_t s) { return launch_stage2d_paired<double>(p, s); }
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s) { return launch_alpha2d<float>(p, s); }
 cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s) { return launch_batch1d<float>(p, s); }
+cudaError_t launch_batch1d_alpha_f32(const Batch1D &p, double *a, cudaStream_t s) {
+    return launch_batch1d_alpha<float>(p, a, s);
+}
+int batch1d_groups_f32(int group_warps) { return batch1d_groups<float>(group_warps); }
 cudaError_t launch_rhs_adjoint1d_f32(const Adjoint1D &p, cudaStream_t s) { return launch_rhs_adjoint1d<float>(p, s); }
 cudaError_t launch_combine_f32(void *out, const void *x, const void *y, const void *z, double c1, double c2,
                                double c3, size_t N, cudaStream_t s) {

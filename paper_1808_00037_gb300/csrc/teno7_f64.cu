@@ -11,6 +11,10 @@ cudaError_t launch_recon_f64(const Recon &p, cudaStream_t s) { return launch_rec
 cudaError_t launch_stage2d_f64(const Stage2D &p, cudaStream_t s) { return launch_stage2d<double>(p, s); }
 cudaError_t launch_alpha2d_f64(const Alpha2D &p, cudaStream_t s) { return launch_alpha2d<double>(p, s); }
 cudaError_t launch_batch1d_f64(const Batch1D &p, cudaStream_t s) { return launch_batch1d<double>(p, s); }
+cudaError_t launch_batch1d_alpha_f64(const Batch1D &p, double *a, cudaStream_t s) {
+    return launch_batch1d_alpha<double>(p, a, s);
+}
+int batch1d_groups_f64(int group_warps) { return batch1d_groups<double>(group_warps); }
 cudaError_t launch_rhs_adjoint1d_f64(const Adjoint1D &p, cudaStream_t s) { return launch_rhs_adjoint1d<double>(p, s); }
 cudaError_t launch_combine_f64(void *out, const void *x, const void *y, const void *z, double c1, double c2,
                                double c3, size_t N, cudaStream_t s) {

@@ -103,7 +103,8 @@ struct Batch1D {
     double t_end, cfl, gamma, CT;
     int max_steps;
     int group_warps;           // warps per tube (1, 2, 4 or 8)
-    int *queue;                // device work counter, zero before the launch
+    int nbig;                  // the first nbig tubes of `order` run on whole CTAs (all 8 warps)
+    int *queue;                // device work counters [2] (whole-CTA, then group tubes), zero before the launch
     int *steps_out;            // device, per tube
     double *t_out;             // device, per tube
     DevCtl *ctl;               // error word
@@ -111,6 +112,13 @@ struct Batch1D {
 
 cudaError_t launch_batch1d_f64(const Batch1D &p, cudaStream_t s);
 cudaError_t launch_batch1d_f32(const Batch1D &p, cudaStream_t s);
+// concurrent groups of `group_warps` warps the batch kernel runs (CTAs x groups per CTA)
+int batch1d_groups_f64(int group_warps);
+int batch1d_groups_f32(int group_warps);
+// per-tube wave speed max(|u| + c) of p.U into alpha_out[ntubes] (device);
+// reads p.U, p.offsets, p.ntubes, p.Ntot, p.gamma
+cudaError_t launch_batch1d_alpha_f64(const Batch1D &p, double *alpha_out, cudaStream_t s);
+cudaError_t launch_batch1d_alpha_f32(const Batch1D &p, double *alpha_out, cudaStream_t s);
 
 // Discrete adjoint of the 1D Euler right-hand side (teno7_adjoint.cuh).
 struct Adjoint1D;

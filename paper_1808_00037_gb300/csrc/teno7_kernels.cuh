@@ -1509,7 +1509,6 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
     __shared__ int s_tube[WPB];
     constexpr bool F64 = sizeof(T) == 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = p.group_warps, group = warp / G, wg = warp % G;
     for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
     if constexpr (!F64) fill_delta_table(s_cf);
     __syncthreads();
@@ -1518,6 +1517,12 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
     T *W2 = static_cast<T *>(p.W2);
     const size_t cs = (size_t)p.Ntot;
     const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0);
+
+    // The CTA's warps form groups of G warps (group = warp / G, rank wg within
+    // it); the first nbig tubes of the order (the costliest) are run first with
+    // the whole CTA as one group, so that no single tube outlasts the rest of
+    // the batch on a small group.
+    int G = WPB, group = 0, wg = warp;
 
     // group max over its G warps; every lane of the group gets the result
     auto group_max = [&](T v) -> T {
@@ -1530,13 +1535,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
         return m;
     };
 
-    for (;;) {
-        if (wg == 0 && lane == 0) s_tube[group] = atomicAdd(p.queue, 1);
-        group_sync(group, G);
-        const int q = s_tube[group];
-        group_sync(group, G);
-        if (q >= p.ntubes) break;
-        const int tube = p.order[q];
+    auto run_tube = [&](int tube) {
         const long long off = p.offsets[tube];
         const int n = (int)(p.offsets[tube + 1] - off);
         const double dx = p.dx[tube];
@@ -1603,13 +1602,86 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
             p.steps_out[tube] = steps;
             p.t_out[tube] = t;
         }
+    };
+
+    // phase 1: whole-CTA groups over order[0 .. nbig)
+    for (;;) {
+        if (warp == 0 && lane == 0) s_tube[0] = atomicAdd(p.queue + 1, 1);
+        __syncthreads();
+        const int q = s_tube[0];
+        __syncthreads();
+        if (q >= p.nbig) break;
+        run_tube(p.order[q]);
     }
+    // phase 2: groups of p.group_warps warps over order[nbig .. ntubes)
+    G = p.group_warps;
+    group = warp / G;
+    wg = warp % G;
+    for (;;) {
+        if (wg == 0 && lane == 0) s_tube[group] = p.nbig + atomicAdd(p.queue, 1);
+        group_sync(group, G);
+        const int q = s_tube[group];
+        group_sync(group, G);
+        if (q >= p.ntubes) break;
+        run_tube(p.order[q]);
+    }
+}
+
+// Per-tube wave speed max(|u| + c) of the state, the alpha that sets the
+// tube's first CFL step (Remark 3).  One CTA of 8 warps per tube; non-physical
+// cells are skipped here (the batch kernel itself reports them).
+template <typename T>
+__global__ void __launch_bounds__(256) batch1d_alpha_kernel(const Batch1D p, double *alpha_out) {
+    __shared__ T s_red[8];
+    const T *U = static_cast<const T *>(p.U);
+    const size_t cs = (size_t)p.Ntot;
+    const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0);
+    for (int tube = blockIdx.x; tube < p.ntubes; tube += gridDim.x) {
+        const long long off = p.offsets[tube];
+        const int n = (int)(p.offsets[tube + 1] - off);
+        T a = T(0);
+        for (int i = threadIdx.x; i < n; i += 256) {
+            T Uc[3] = {U[off + i], U[cs + off + i], U[2 * cs + off + i]};
+            int f = 0;
+            const T w = wavespeed1d<T, SYS_EULER1D>(Uc, gm1, gamma, T(0), &f);
+            if (!f) a = fmax(a, w);
+        }
+        a = warp_max(a);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T m = s_red[0];
+            for (int w = 1; w < 8; w++) m = fmax(m, s_red[w]);
+            alpha_out[tube] = (double)m;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch1d_alpha(const Batch1D &p, double *alpha_out, cudaStream_t st) {
+    if (p.ntubes < 1) return cudaSuccess;
+    const int grid = p.ntubes < num_sms() * 8 ? p.ntubes : num_sms() * 8;
+    batch1d_alpha_kernel<T><<<grid, 256, 0, st>>>(p, alpha_out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int batch1d_groups(int group_warps) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch1d_kernel<T>, WPB * 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    if (per_sm < 1) per_sm = 1;
+    return num_sms() * per_sm * (WPB / (group_warps > 0 ? group_warps : WPB));
 }
 
 template <typename T>
 cudaError_t launch_batch1d(const Batch1D &p, cudaStream_t st) {
     if (p.group_warps != 1 && p.group_warps != 2 && p.group_warps != 4 && p.group_warps != 8)
         return cudaErrorInvalidValue;
+    if (p.nbig < 0 || p.nbig > p.ntubes) return cudaErrorInvalidValue;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch1d_kernel<T>, WPB * 32, 0);
     if (e != cudaSuccess) return e;

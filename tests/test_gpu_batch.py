@@ -139,3 +139,38 @@ def test_batch_autotune_leaves_state_and_rejects_bad_offsets():
     with pytest.raises(B.T7Error) as ei:
         c.batch_run(Ug, bad, dx, 0.1, 0.5)
     assert ei.value.status == B.T7_EINVAL
+
+
+def test_batch_whole_cta_phase_f64_bitexact():
+    """The two-phase schedule (group_warps < 0): 1500 short tubes (30-90 cells)
+    and 3 long ones (1200-1500) to t = 0.02 or 12 steps.  With G = 4 only the
+    long tubes run first on whole CTAs; with G = 1 most short tubes do too, so
+    both phases and the hand-over between them carry tubes.  Every tube is
+    bit-identical to the oracle (state, steps, final time), so no tube is
+    skipped or advanced twice."""
+    Us, offs, dxs, _ = I.riemann_tube_batch(11, 1500, 30, 90)
+    Ul, offl, dxl, _ = I.riemann_tube_batch(12, 3, 1200, 1500)
+    cut = int(offs[700])
+    U = np.concatenate([Us[:, :cut], Ul, Us[:, cut:]], axis=1)
+    n = np.concatenate([np.diff(offs)[:700], np.diff(offl), np.diff(offs)[700:]])
+    off = np.concatenate([[0], np.cumsum(n)])
+    dx = np.concatenate([dxs[:700], dxl, dxs[700:]])
+    Uo, so, to = oracle_tubes(U, off, dx, 0.02, 0.5, max_steps=12)
+    assert 0 < np.sum(so < 12) < len(so)  # some tubes stop at t_end, others at max_steps
+    for group in (-4, -1):
+        c = ctx(U.shape[1])
+        Ug = torch.tensor(U, dtype=torch.float64, device="cuda")
+        steps, t = c.batch_run(Ug, off, dx, 0.02, 0.5, max_steps=12, group_warps=group)
+        assert np.array_equal(steps, so) and np.array_equal(t, to), group
+        assert np.array_equal(Ug.cpu().numpy(), Uo), group
+
+
+@pytest.mark.parametrize("group", [3, -3, 16, -16])
+def test_batch_rejects_bad_group(group):
+    U, off, dx, _ = small_batch()
+    c = ctx(U.shape[1])
+    Ug = torch.tensor(U, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.T7Error) as ei:
+        c.batch_run(Ug, off, dx, 0.1, 0.5, group_warps=group)
+    assert ei.value.status == B.T7_EINVAL
+    assert np.array_equal(Ug.cpu().numpy(), U)
