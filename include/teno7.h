@@ -136,8 +136,10 @@ t7_status t7_rk3_step(t7_ctx *ctx, void *U, double dt);
  * t_end may be +inf.  Synchronises; steps_out / t_out (host, nullable). */
 t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out);
 
-/* As t7_run on a HOST array U_host ([m][nx], context precision): copies it to
- * the context's device state, runs, copies the result back.  Synchronises. */
+/* As t7_run on a HOST array U_host ([m][nx], context precision; pageable or
+ * page-locked): copies it to the context's device state, runs, copies the
+ * result back.  With t_end = +inf (a known step count) on a 1D system the
+ * result leaves in parts while the last stage computes.  Synchronises. */
 t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out);
 

@@ -46,6 +46,10 @@ struct t7_ctx {
     cudaEvent_t g_in, g_out;
     cudaGraphExec_t gexec;
     void *g_U;
+    // t7_run_host with a known step count: the last stage is launched in parts
+    // and each finished part is copied to the host array on cstream
+    cudaStream_t cstream;
+    cudaEvent_t c_ev[8], c_done;
     char err[512];
 };
 
@@ -185,11 +189,57 @@ cudaError_t alpha_init(t7_ctx *c, const void *U) {
 }
 
 
+// The last stage of a step (1D) in OUT_PARTS launches over consecutive
+// ranges of warp tiles; each finished range of cells is copied from U to the
+// host array host_out ([m][nx], pageable or page-locked) on the copy stream
+// while the next range computes, so the result leaves the device at the
+// CPU-GPU link's rate, overlapped with the stage's own compute.  All launches
+// are queued before the copies, so that a copy to pageable memory that blocks
+// the host does not hold back the compute.  The context's stream waits for the
+// copies.
+constexpr int OUT_PARTS = 8;
+cudaError_t last_stage_to_host(t7_ctx *c, t7::Stage1D p, void *host_out) {
+    cudaError_t e = cudaSuccess;
+    if (!c->cstream) {
+        if ((e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        for (int k = 0; k < OUT_PARTS; k++)
+            if ((e = cudaEventCreateWithFlags(&c->c_ev[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&c->c_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    const int nx = c->g.nx;
+    const int ntiles = (nx + t7::TILE_CELLS - 1) / t7::TILE_CELLS;
+    const int parts = ntiles < OUT_PARTS ? ntiles : OUT_PARTS;
+    int lo[OUT_PARTS], hi[OUT_PARTS];
+    for (int k = 0; k < parts; k++) {
+        lo[k] = (int)((long long)ntiles * k / parts);
+        hi[k] = (int)((long long)ntiles * (k + 1) / parts);
+        p.tile_lo = lo[k];
+        p.tile_hi = hi[k];
+        p.partial = k < parts - 1;
+        if ((e = stage(c, p)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->c_ev[k], c->stream)) != cudaSuccess) return e;
+    }
+    const size_t es = c->esize, row = (size_t)nx * es;
+    for (int k = 0; k < parts; k++) {
+        const size_t c0 = (size_t)lo[k] * t7::TILE_CELLS;
+        size_t c1 = (size_t)hi[k] * t7::TILE_CELLS;
+        if (c1 > (size_t)nx) c1 = (size_t)nx;
+        if ((e = cudaStreamWaitEvent(c->cstream, c->c_ev[k], 0)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy2DAsync(static_cast<char *>(host_out) + c0 * es, row,
+                                   static_cast<const char *>(p.out) + c0 * es, row, (c1 - c0) * es, (size_t)c->m,
+                                   cudaMemcpyDeviceToHost, c->cstream)) != cudaSuccess)
+            return e;
+    }
+    if ((e = cudaEventRecord(c->c_done, c->cstream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(c->stream, c->c_done, 0);
+}
+
 // three stage launches; dt_fixed > 0 fixes the step, otherwise CFL on device.
-// out_last (nullable) receives the step's result instead of U (U keeps U^n).
-cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed, void *out_last = nullptr) {
+// host_out (nullable, 1D): the step's result is also copied to this host array
+// (see last_stage_to_host).
+cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed, void *host_out = nullptr) {
     void *bufs_in[3] = {U, c->U1, c->U2};
-    void *bufs_out[3] = {c->U1, c->U2, out_last ? out_last : U};
+    void *bufs_out[3] = {c->U1, c->U2, U};
     if (c->g.sys == T7_EULER2D) {
         for (int k = 0; k < 3; k++) {
             t7::Stage2D p = stage2d_params(c, bufs_in[k], k == 0 ? nullptr : U, bufs_out[k], c->R);
@@ -210,7 +260,7 @@ cudaError_t rk3(t7_ctx *c, void *U, double dt_fixed, void *out_last = nullptr) {
         p.dt_fixed = dt_fixed;
         p.f_dt_fixed = (float)dt_fixed;
         p.slot_in = k;
-        cudaError_t e = stage(c, p);
+        cudaError_t e = (k == 2 && host_out) ? last_stage_to_host(c, p, host_out) : stage(c, p);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -323,6 +373,10 @@ t7_status t7_destroy(t7_ctx *c) {
     if (c->g_in) cudaEventDestroy(c->g_in);
     if (c->g_out) cudaEventDestroy(c->g_out);
     if (c->gstream) cudaStreamDestroy(c->gstream);
+    for (int k = 0; k < 8; k++)
+        if (c->c_ev[k]) cudaEventDestroy(c->c_ev[k]);
+    if (c->c_done) cudaEventDestroy(c->c_done);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     delete c;
     return T7_OK;
 }
@@ -470,10 +524,10 @@ static int run_chunk_graph(t7_ctx *c, void *U) {
     return 1;
 }
 
-// t7_run's loop; final_out (nullable, only with t_end = inf) receives the
-// result of the last step directly (e.g. mapped host memory).
+// t7_run's loop; host_out (nullable, 1D, only with t_end = inf) receives a
+// copy of the result of the last step, made while its last stage computes.
 static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out,
-                          void *final_out) {
+                          void *host_out) {
     t7_status st;
     cudaError_t e = t7::launch_ctl_begin(c->ctl, t_end, cfl, c->g.dx, c->g.dy, max_steps, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ctl");
@@ -485,12 +539,12 @@ static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_
     int launched = 0;
     while (launched < max_steps) {
         int k = max_steps - launched < RUN_CHUNK ? max_steps - launched : RUN_CHUNK;
-        const bool last_chunk = final_out && launched + k == max_steps;
+        const bool last_chunk = host_out && launched + k == max_steps;
         const int g = (graphs && k == RUN_CHUNK && !last_chunk) ? run_chunk_graph(c, U) : 0;
         if (g < 0) return cuda_fail(c, cudaGetLastError(), "ordering a graph chunk");
         if (g == 0) {
             for (int q = 0; q < k; q++) {
-                void *last = (final_out && launched + q == max_steps - 1) ? final_out : nullptr;
+                void *last = (host_out && launched + q == max_steps - 1) ? host_out : nullptr;
                 if ((e = rk3(c, U, -1.0, last)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
             }
         }
@@ -526,20 +580,11 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
     size_t bytes = c->ncell * c->m * c->esize;
     cudaError_t e = cudaMemcpyAsync(c->Uhost, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "H2D copy");
-    // Page-locked host arrays are device-accessible: when the number of steps
-    // is known (t_end = inf), the last stage writes the result straight into
-    // the host array over the CPU-GPU link, overlapped with its own compute,
-    // instead of a copy after the run.
-    cudaPointerAttributes at;
-    memset(&at, 0, sizeof(at));
-    if (cudaPointerGetAttributes(&at, U_host) != cudaSuccess) {
-        cudaGetLastError();
-        at.type = cudaMemoryTypeUnregistered;
-    }
-    if (at.type == cudaMemoryTypeHost && at.devicePointer && isinf(t_end) && max_steps >= 1) {
-        st = run_core(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out, at.devicePointer);
-        return st;
-    }
+    // With a known number of steps (t_end = inf) in 1D, the last step's last
+    // stage is launched in parts and each finished part is copied back while
+    // the rest computes; otherwise the result is copied after the run.
+    if (is_1d(c->g.sys) && isinf(t_end) && max_steps >= 1)
+        return run_core(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out, U_host);
     st = run_core(c, c->Uhost, cfl, t_end, max_steps, steps_out, t_out, nullptr);
     if (st != T7_OK && st != T7_ENONPHYSICAL && st != T7_ENONFINITE) return st;
     e = cudaMemcpyAsync(U_host, c->Uhost, bytes, cudaMemcpyDeviceToHost, c->stream);

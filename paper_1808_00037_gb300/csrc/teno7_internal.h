@@ -29,6 +29,10 @@ struct DevCtl {
 };
 
 // One launch of the fused 1D stage kernel.
+// Cells a warp tile of the 1D stage kernels updates (the stage launches'
+// tile_lo / tile_hi count these tiles).
+constexpr int TILE_CELLS = 29;
+
 struct Stage1D {
     const void *Us;  // stage input state [m][n] (stencil reads)
     const void *U0;  // U^n (pointwise reads; stages 1 and 2 only)
@@ -45,6 +49,8 @@ struct Stage1D {
     float f_dx, f_eps, f_CT, f_gamma, f_gm1, f_a, f_dt_fixed;
     int scheme;         // 0: TENO7-ext, 1: TENO5 baseline
     double *alpha_rec;  // nullable: receives alpha of the output state (RK mode)
+    int tile_lo, tile_hi;  // warp tiles [tile_lo, tile_hi) of the domain (29 cells each; tile_hi <= 0: all)
+    int partial;           // RK mode: one part of a stage split over several launches, not its last
 };
 
 struct Alpha1D {

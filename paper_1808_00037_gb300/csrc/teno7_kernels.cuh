@@ -378,6 +378,7 @@ constexpr int WT = 29;   // cells updated per warp tile
 constexpr int WS = 39;   // cells staged per warp tile
 constexpr int WC = 40;   // padded row length
 constexpr int WPB = 8;   // warps per CTA
+static_assert(WT == TILE_CELLS, "the host's tile size must match the kernels'");
 
 template <typename T>
 struct TileArgs {
@@ -399,7 +400,7 @@ struct TileArgs {
 
 template <typename T, int SYS, int SCH = SCH_TENO7EXT>
 __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)[WC], T (*sgm)[WC], T (*spr)[WC],
-                                     const T *scoef, int tile0, int tstride) {
+                                     const T *scoef, int tile0, int tstride, int tile_end = 0x7fffffff) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;  // u, H, sqrt(rho)
     constexpr bool F64 = sizeof(T) == 8;
@@ -409,7 +410,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
     T *out = A.out;
     const int n = A.n;
     const size_t cs = A.cs;
-    const int ntiles = (n + WT - 1) / WT;
+    const int ntiles = min((n + WT - 1) / WT, tile_end);  // tiles tile0, tile0 + tstride, ... below it
     const T alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a, eps = A.eps, CT = A.CT;
     const T kt = keep_all_factor(CT);
     DevCtl *ctl = A.ctl;
@@ -714,7 +715,8 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     A.ctl = ctl;
     __syncwarp();
     T wsmax = tiles1d<T, SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
-                                   blockIdx.x * nw + warp, gridDim.x * nw);
+                                   p.tile_lo + blockIdx.x * nw + warp, gridDim.x * nw,
+                                   p.tile_hi > 0 ? p.tile_hi : 0x7fffffff);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -726,8 +728,8 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
             for (int w = 1; w < nw; w++) v = fmax(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
-                          p.alpha_rec);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed && !p.partial,
+                          p.stage == 2 && !fixed && !p.partial, false, p.alpha_rec);
         }
     }
 }
@@ -926,7 +928,7 @@ __device__ __forceinline__ unsigned slot_code(unsigned s) {
 template <int SYS, int SCH = SCH_TENO7EXT, typename S = float>
 __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*sU)[WC], float (*sgp)[WC],
                                              float (*sgm)[WC], float (*spr)[WC], const float (*s_cf)[8], int tile0,
-                                             int tstride) {
+                                             int tstride, int tile_end = 0x7fffffff) {
     constexpr bool MIXED = sizeof(S) == 8;
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -943,7 +945,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     const double idxD = 1.0 / A.dx, cD = A.dtD * idxD;
     const int n = A.n;
     const size_t cs = A.cs;
-    const int ntiles = (n + WT - 1) / WT;
+    const int ntiles = min((n + WT - 1) / WT, tile_end);  // tiles tile0, tile0 + tstride, ... below it
     DevCtl *ctl = A.ctl;
     float wsmax = 0.f;
     // Software pipelining: the raw state of a warp tile's staged cells (lane
@@ -1264,7 +1266,8 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     A.ctl = ctl;
     __syncthreads();
     float wsmax = tiles1d_f32<SYS, SCH, S>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
-                                           blockIdx.x * nw + warp, gridDim.x * nw);
+                                           p.tile_lo + blockIdx.x * nw + warp, gridDim.x * nw,
+                                           p.tile_hi > 0 ? p.tile_hi : 0x7fffffff);
 
     if (!p.rhs_mode) {
         wsmax = warp_max(wsmax);
@@ -1276,8 +1279,8 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
             for (int w = 1; w < nw; w++) v = fmaxf(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
-                          p.alpha_rec);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed && !p.partial,
+                          p.stage == 2 && !fixed && !p.partial, false, p.alpha_rec);
         }
     }
 }
@@ -1396,10 +1399,20 @@ inline int warps_per_cta(int ntiles, bool spread) {
     return nw;
 }
 
+// Warp tiles a stage launch covers: [tile_lo, tile_hi) of the domain's tiles
+// (tile_hi <= 0: to the end); 0 if the range is empty or out of the domain.
+inline int stage_tiles(const Stage1D &p) {
+    const int all = (p.n + WT - 1) / WT;
+    const int hi = p.tile_hi > 0 ? p.tile_hi : all;
+    if (p.tile_lo < 0 || hi > all || hi <= p.tile_lo) return 0;
+    return hi - p.tile_lo;
+}
+
 // FP32 paired-split stage kernels; S = float (FP32 state) or double (mixed).
 template <typename S>
 cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
-    const int ntiles = (p.n + WT - 1) / WT;
+    const int ntiles = stage_tiles(p);
+    if (ntiles < 1) return cudaErrorInvalidValue;
     const int nw = warps_per_cta(ntiles, false);
     const int resident = num_sms() * T7_F32_MINB * 4 * (WPB / nw);  // a few waves of resident CTAs
     int grid = (ntiles + nw - 1) / nw;
@@ -1429,7 +1442,8 @@ cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         return launch_stage1d_paired<float>(p, st);
     } else {
-        const int ntiles = (p.n + WT - 1) / WT;
+        const int ntiles = stage_tiles(p);
+        if (ntiles < 1) return cudaErrorInvalidValue;
         const int nw = warps_per_cta(ntiles, true);
         const int resident = num_sms() * 4 * (WPB / nw);  // a few waves of resident CTAs
         int grid = (ntiles + nw - 1) / nw;

@@ -326,10 +326,11 @@ def test_f32_fine_tube_stays_close_to_f64(tube):
 
 @pytest.mark.parametrize("prec,dtype", [(B.T7_F64, torch.float64), (B.T7_F32, torch.float32),
                                         (B.T7_MIXED, torch.float64)])
-def test_run_host_pinned_direct_write_matches_device_run(prec, dtype):
-    """A page-locked host array with a known step count takes the path where
-    the last stage writes the result into the host array directly: the result
-    is bit-identical to the device run (1 and 5 steps; FP64, FP32, mixed)."""
+def test_run_host_known_steps_matches_device_run(prec, dtype):
+    """A host array with a known step count takes the path where the last
+    stage runs in parts and each finished part is copied back while the rest
+    computes: the result is bit-identical to the device run (1 and 5 steps;
+    FP64, FP32, mixed; page-locked and pageable arrays)."""
     U, dx = I.shu_osher(1600)
     for steps in (1, 5):
         c = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1), prec=prec)
@@ -338,6 +339,27 @@ def test_run_host_pinned_direct_write_matches_device_run(prec, dtype):
         Uh = torch.tensor(U, dtype=dtype).pin_memory()
         sh, th = c.run_host(Uh, 0.5, max_steps=steps)
         assert (sd, td) == (sh, th) == (steps, td)
+        assert torch.equal(Ud.cpu(), Uh)
+        Un = np.ascontiguousarray(U.astype(np.float64 if dtype == torch.float64 else np.float32))
+        sn, tn = c.run_host(Un, 0.5, max_steps=steps)
+        assert (sn, tn) == (sd, td)
+        assert np.array_equal(Ud.cpu().numpy(), Un)
+
+
+@pytest.mark.parametrize("n", [1, 5, 29, 30, 100, 232, 233, 4096 * 29 + 3])
+def test_run_host_parts_at_small_and_ragged_sizes(n):
+    """Fewer warp tiles than parts, a part boundary on a ragged tail, and a
+    domain whose tile count is not a multiple of the part count: the copied
+    result and the step count match the device run bit for bit (FP32 and
+    FP64, zero-gradient Sod data, 3 steps)."""
+    U, dx, _ = I.riemann_tube(n, *I.SOD)
+    for prec, dtype, npd in ((B.T7_F32, torch.float32, np.float32), (B.T7_F64, torch.float64, np.float64)):
+        c = ctx(oracle.SYS_EULER1D, n, dx, bc=(1, 1), prec=prec)
+        Ud = dev(U, dtype)
+        sd, td = c.run(Ud, 0.5, max_steps=3)
+        Uh = torch.tensor(U, dtype=dtype).pin_memory()
+        sh, th = c.run_host(Uh, 0.5, max_steps=3)
+        assert (sh, th) == (sd, td) == (3, td)
         assert torch.equal(Ud.cpu(), Uh)
 
 
