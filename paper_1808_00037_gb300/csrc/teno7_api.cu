@@ -282,12 +282,6 @@ t7_status collect(t7_ctx *c) {
     return T7_OK;
 }
 
-t7_status check_1d(t7_ctx *c) {
-    if (!c) return T7_EINVAL;
-    if (!is_1d(c->g.sys)) return fail(c, T7_EINVAL, "this entry point takes a 1D system");
-    return T7_OK;
-}
-
 t7_status check_sys(t7_ctx *c) {
     if (!c) return T7_EINVAL;
     return T7_OK;
@@ -328,12 +322,11 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     size_t bytes = c->ncell * c->m * c->esize;
-    cudaError_t e;
-    if ((e = cudaMalloc(&c->U1, bytes)) != cudaSuccess || (e = cudaMalloc(&c->U2, bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&c->Uhost, bytes)) != cudaSuccess ||
-        (g->sys == T7_EULER2D && (e = cudaMalloc(&c->R, bytes)) != cudaSuccess) ||
-        (e = cudaMalloc((void **)&c->ctl, sizeof(t7::DevCtl))) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&c->ctl_host, sizeof(t7::DevCtl))) != cudaSuccess) {
+    if (cudaMalloc(&c->U1, bytes) != cudaSuccess || cudaMalloc(&c->U2, bytes) != cudaSuccess ||
+        cudaMalloc(&c->Uhost, bytes) != cudaSuccess ||
+        (g->sys == T7_EULER2D && cudaMalloc(&c->R, bytes) != cudaSuccess) ||
+        cudaMalloc((void **)&c->ctl, sizeof(t7::DevCtl)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->ctl_host, sizeof(t7::DevCtl)) != cudaSuccess) {
         t7_destroy(c);
         cudaGetLastError();
         return T7_ENOMEM;
@@ -342,8 +335,9 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     memset(&init, 0, sizeof(init));
     init.err_index = 0x7fffffff;
     init.max_steps = 0;
-    if ((e = cudaMemcpy(c->ctl, &init, sizeof(init), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    if (cudaMemcpy(c->ctl, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
         t7_destroy(c);
+        cudaGetLastError();
         return T7_ECUDA;
     }
     snprintf(c->err, sizeof(c->err), "no error");
