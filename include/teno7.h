@@ -96,6 +96,9 @@ typedef struct t7_ctx t7_ctx;
  * (3 state-sized buffers + a control block).  On success *out owns it. */
 t7_status t7_create(const t7_grid *grid, void *stream, t7_ctx **out);
 t7_status t7_destroy(t7_ctx *ctx);
+/* Later calls run on `stream`.  Work already queued on the previous stream is
+ * ordered before them (the new stream waits on an event recorded on the old
+ * one), so the switch needs no synchronisation by the caller. */
 t7_status t7_set_stream(t7_ctx *ctx, void *stream);
 /* Last error message of this context (never NULL). */
 const char *t7_last_error(const t7_ctx *ctx);

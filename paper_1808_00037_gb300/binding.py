@@ -115,6 +115,12 @@ class Context:
             raise T7Error(st, "t7_create failed")
         self.h = h
 
+    def set_stream(self, stream):
+        """Run later calls on `stream` (a torch.cuda.Stream); work queued on the
+        previous stream is ordered before them."""
+        self._check(self.lib.t7_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "t7_set_stream")
+        self.stream = stream
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.t7_destroy(self.h)

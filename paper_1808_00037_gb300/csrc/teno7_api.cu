@@ -50,6 +50,7 @@ struct t7_ctx {
     // and each finished part is copied to the host array on cstream
     cudaStream_t cstream;
     cudaEvent_t c_ev[8], c_done;
+    cudaEvent_t sw_ev;     // t7_set_stream: orders the new stream after the old one
     char err[512];
 };
 
@@ -371,13 +372,23 @@ t7_status t7_destroy(t7_ctx *c) {
         if (c->c_ev[k]) cudaEventDestroy(c->c_ev[k]);
     if (c->c_done) cudaEventDestroy(c->c_done);
     if (c->cstream) cudaStreamDestroy(c->cstream);
+    if (c->sw_ev) cudaEventDestroy(c->sw_ev);
     delete c;
     return T7_OK;
 }
 
 t7_status t7_set_stream(t7_ctx *c, void *stream) {
     if (!c) return T7_EINVAL;
-    c->stream = (cudaStream_t)stream;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s == c->stream) return T7_OK;
+    // the context's buffers may still be in use by work queued on the old
+    // stream: the new stream waits for it
+    cudaError_t e = cudaSuccess;
+    if (!c->sw_ev) e = cudaEventCreateWithFlags(&c->sw_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->sw_ev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->sw_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "t7_set_stream: ordering the new stream after the old one");
+    c->stream = s;
     return T7_OK;
 }
 

@@ -389,3 +389,39 @@ def test_small_and_ragged_sizes_f32_and_mixed(prec, dtype, n):
         sg, _ = c.run(Ug, 0.5, max_steps=3)
         assert sg == so == 3
         assert np.abs(host(Ug) - Uo).sum() <= tol * np.abs(Uo).sum()
+
+
+def test_streams_switching_and_error_text():
+    """A context created on one side stream and switched to another mid-run
+    (50 asynchronous fixed-dt steps on each, no synchronisation in between)
+    gives the default-stream result bit for bit; a refused call reports its
+    reason through t7_last_error; closing twice is harmless."""
+    U, dx = I.shu_osher(1600)
+    for prec, dtype in ((B.T7_F32, torch.float32), (B.T7_F64, torch.float64)):
+        c0 = ctx(oracle.SYS_EULER1D, 1600, dx, bc=(1, 1), prec=prec)
+        Ua = dev(U, dtype)
+        for _ in range(100):
+            c0.rk3_step(Ua, 1e-3)
+        c0.sync()
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        Ub = dev(U, dtype)
+        torch.cuda.synchronize()
+        c = B.Context(B.T7_EULER1D, 1600, dx, prec=prec, bc=(1, 1, 0, 0), stream=s1)
+        for _ in range(50):
+            c.rk3_step(Ub, 1e-3)
+        c.set_stream(s2)
+        for _ in range(50):
+            c.rk3_step(Ub, 1e-3)
+        c.sync()
+        assert torch.equal(Ua, Ub)
+        # a graph-chunk run (small state) after the switch: same as on the default stream
+        Ua2, Ub2 = dev(U, dtype), dev(U, dtype)
+        torch.cuda.synchronize()
+        sa, ta = c0.run(Ua2, 0.5, max_steps=130)
+        sb, tb = c.run(Ub2, 0.5, max_steps=130)
+        assert (sa, ta) == (sb, tb) and torch.equal(Ua2, Ub2)
+        with pytest.raises(B.T7Error) as ei:
+            c.rk3_step(Ub, -1.0)
+        assert ei.value.status == B.T7_EINVAL and "bad argument" in str(ei.value)
+        c.close()
+        c.close()
