@@ -618,7 +618,8 @@ def main():
 
     if rank != 0:
         return 0
-    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    # the oracle on the host cores: on rank 0 of a one-GPU run only
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
     main_res = res["f32"]
     line = {
         "metric": "TENO7 RK3 Gcell-updates/s (1D Euler, tiled Shu-Osher)", "value": main_res["value"],
