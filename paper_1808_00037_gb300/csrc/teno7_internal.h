@@ -28,11 +28,11 @@ struct DevCtl {
     unsigned blocks_done;
 };
 
-// One launch of the fused 1D stage kernel.
 // Cells a warp tile of the 1D stage kernels updates (the stage launches'
 // tile_lo / tile_hi count these tiles).
 constexpr int TILE_CELLS = 29;
 
+// One launch of the fused 1D stage kernel.
 struct Stage1D {
     const void *Us;  // stage input state [m][n] (stencil reads)
     const void *U0;  // U^n (pointwise reads; stages 1 and 2 only)

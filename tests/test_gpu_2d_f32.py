@@ -134,3 +134,24 @@ def test_2d_f32_full_size_sampled():
             checked += 1
             assert np.max(np.abs(rg[:, y, x] - ro[:, y - y0, x - x0])) <= bound, (y, x)
     assert checked >= 40
+
+
+def test_2d_f32_runs_against_oracle():
+    """FP32 runs: smooth periodic 64 x 64 to t = 0.05 within 1e-5 relative L1
+    of the oracle in every variable (the smooth-case tolerance), and 40 steps
+    of 96 x 80 quadrant data within 1e-3 in density."""
+    U, dx, dy = I.random_smooth_2d(3, 64, 64)
+    Uo, _, to, _ = oracle.run_2d(U, dx, dy, cfl=0.4, t_end=0.05, bc=PER)
+    c = ctx(64, 64, dx, dy, B.T7_F32, PER)
+    Ug = torch.tensor(U, dtype=torch.float32, device="cuda")
+    _, tg = c.run(Ug, 0.4, t_end=0.05)
+    assert tg == pytest.approx(to, rel=1e-12)
+    got = Ug.double().cpu().numpy()
+    for k in range(4):
+        assert np.abs(got[k] - Uo[k]).sum() / np.abs(Uo[k]).sum() < 1e-5, k
+    U, dx, dy, _ = I.quadrants_2d(11, 96, 80)
+    Uo, _, _, _ = oracle.run_2d(U, dx, dy, cfl=0.4, max_steps=40)
+    c = ctx(96, 80, dx, dy, B.T7_F32, ZG)
+    Ug = torch.tensor(U, dtype=torch.float32, device="cuda")
+    c.run(Ug, 0.4, max_steps=40)
+    assert np.abs(Ug.double().cpu().numpy()[0] - Uo[0]).sum() / np.abs(Uo[0]).sum() < 1e-3
