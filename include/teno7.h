@@ -28,7 +28,12 @@
  *   - Calls are asynchronous on the context's stream unless stated.  Device-
  *     side errors (non-physical or non-finite states) are latched in the
  *     control block and returned by the next synchronising call (t7_sync,
- *     t7_cfl_dt, t7_run, t7_run_host), which clears them.
+ *     t7_cfl_dt, t7_run, t7_run_host), which clears them.  A cell holding
+ *     Inf or NaN gives T7_ENONFINITE; a finite one with rho <= 0 or p <= 0, or
+ *     a Roe frame with c^2 <= 0, gives T7_ENONPHYSICAL, which wins when both
+ *     occurred (a state that went non-physical and then produced NaN).
+ *     t7_last_error() names the lowest flat cell index (1D: i; 2D: y nx + x;
+ *     batches: the index in the concatenated array) near which one was met.
  *   - A call never aborts the process; it returns a t7_status and, on
  *     failure, t7_last_error() describes the cause.
  */

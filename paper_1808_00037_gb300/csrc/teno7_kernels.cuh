@@ -254,8 +254,11 @@ __device__ __forceinline__ T wavespeed1d(const T *Uc, T gm1, T gamma, T a, int *
         p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
         c = __fsqrt_rn(gamma * p * ri);
     }
-    if (!(Uc[0] > T(0)) || !(p > T(0))) *flag |= ERR_NONPHYSICAL;
-    if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2])) *flag |= ERR_NONFINITE;
+    // a non-finite cell is reported as such; a finite one needs rho > 0, p > 0
+    if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2]))
+        *flag |= ERR_NONFINITE;
+    else if (!(Uc[0] > T(0)) || !(p > T(0)))
+        *flag |= ERR_NONPHYSICAL;
     return absval(u) + c;
 }
 
@@ -485,7 +488,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                 L[2 % M][0] = T(0.5) * (b2 - ut / cc);
                 L[2 % M][1 % M] = T(-0.5) * (b1 * ut - T(1) / cc);
                 L[2 % M][2 % M] = T(0.5) * b1;
-                if (!(c2 > T(0))) flag |= ERR_NONPHYSICAL;
+                if (!(c2 > T(0))) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
             } else {
                 const float w = __frcp_rn(sl + sr);
                 ut = (sl * ul + sr * ur) * w;
@@ -505,7 +508,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                 L[2 % M][0] = 0.5f * (b2 - uc);
                 L[2 % M][1 % M] = -0.5f * (b1 * ut - rc);
                 L[2 % M][2 % M] = 0.5f * b1;
-                if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+                if (!(c2 > 0.f)) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
             }
         } else {
             L[0][0] = T(1);
@@ -610,7 +613,8 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
             fh[0] = f[0];
         }
         if (flag && face_out && j >= -2 && j <= n)
-            latch_error(ctl, (flag & ERR_NONPHYSICAL) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), A.ebase + j);
+            latch_error(ctl, (flag & (ERR_NONPHYSICAL | ERR_NONFINITE)) | ((flag & ERR_NOEXIST) ? ERR_NONFINITE : 0),
+                        A.ebase + j);
 
         // ---- flux difference and RK stage ----------------------------------
         T fprev[M];
@@ -842,8 +846,10 @@ __device__ __forceinline__ float wavespeed1d_fast(const float *Uc, float gm1, fl
     const float p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
     const float c2 = gamma * p * ri;
     const float c = c2 * rsqrtf(c2);
-    if (!(Uc[0] > 0.f) || !(p > 0.f)) *flag |= ERR_NONPHYSICAL;
-    if (!isfinite(Uc[0] + Uc[1] + Uc[2])) *flag |= ERR_NONFINITE;
+    if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2]))
+        *flag |= ERR_NONFINITE;
+    else if (!(Uc[0] > 0.f) || !(p > 0.f))
+        *flag |= ERR_NONPHYSICAL;
     return fabsf(u) + c;
 }
 
@@ -1047,7 +1053,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
             L2[2 % M][0] = f2(0.5f * (b2 - uc));
             L2[2 % M][1 % M] = f2(-0.5f * (b1 * ut - rc));
             L2[2 % M][2 % M] = f2(0.5f * b1);
-            if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+            if (!(c2 > 0.f)) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
         }
 
         float2 P[M][7];

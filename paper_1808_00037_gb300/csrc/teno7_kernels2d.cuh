@@ -17,6 +17,15 @@
 
 namespace t7 {
 
+// Flat index y * nx + x of the cell a fault is reported at.  A face flag
+// names the face's left (x sweep) or lower (y sweep) cell, clamped into the
+// grid: x sweep flat_cell(y, j, nx), y sweep flat_cell(j, x, nx, ny).
+__device__ __forceinline__ int flat_cell(int y, int x, int nx, int ny = 0x7fffffff) {
+    x = x < 0 ? 0 : (x >= nx ? nx - 1 : x);
+    y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+    return y * nx + x;
+}
+
 // Per-face state of one 2D sweep: characteristic projections of the 8 stencil
 // cells, Roe state, cutoff word ('+' codes at bits 3k, '-' at 3(4+k)).
 template <typename T>
@@ -56,7 +65,7 @@ __device__ __forceinline__ void face2d_bits(Face2D<T> &F, PR pr, GP gp, GM gm, T
         {-vt, T(0), T(1), T(0)},
         {T(0.5) * (b2 - un / c), T(-0.5) * (b1 * un - T(1) / c), T(-0.5) * (b1 * vt), T(0.5) * b1},
     };
-    F.flag = (c2 > T(0)) ? 0 : ERR_NONPHYSICAL;
+    F.flag = (c2 > T(0)) ? 0 : (isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE);
     F.word = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -169,8 +178,11 @@ __device__ __forceinline__ void wavespeed2d(const T U[4], T gm1, T gamma, T &sx,
     const T v = U[2] / U[0];
     const T p = gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
     const T c = sq_root(gamma * p / U[0]);
-    if (!(U[0] > T(0)) || !(p > T(0))) *flag |= ERR_NONPHYSICAL;
-    if (!isfinite(U[0]) || !isfinite(U[1]) || !isfinite(U[2]) || !isfinite(U[3])) *flag |= ERR_NONFINITE;
+    // a non-finite cell is reported as such; a finite one needs rho > 0, p > 0
+    if (!isfinite(U[0]) || !isfinite(U[1]) || !isfinite(U[2]) || !isfinite(U[3]))
+        *flag |= ERR_NONFINITE;
+    else if (!(U[0] > T(0)) || !(p > T(0)))
+        *flag |= ERR_NONPHYSICAL;
     sx = absval(u) + c;
     sy = absval(v) + c;
 }
@@ -248,7 +260,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
                 p.masks[((size_t)sk * ny + y) * (nx + 1) + (j + 1)] = (uint8_t)D[sk];
         }
         if (F.flag && face_out && j >= -2 && j <= nx)
-            latch_error(ctl, (F.flag & ERR_NONPHYSICAL) | ((F.flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), j);
+            latch_error(ctl, (F.flag & (ERR_NONPHYSICAL | ERR_NONFINITE)) | ((F.flag & ERR_NOEXIST) ? ERR_NONFINITE : 0),
+                        flat_cell(y, j, nx));
         T fprev[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
@@ -347,7 +360,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
             for (int sk = 0; sk < 8; sk++) ym[((size_t)sk * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)D[sk];
         }
         if (F.flag && face_out && j >= -2 && j <= ny)
-            latch_error(ctl, (F.flag & ERR_NONPHYSICAL) | ((F.flag & ERR_NOEXIST) ? ERR_NONFINITE : 0), j);
+            latch_error(ctl, (F.flag & (ERR_NONPHYSICAL | ERR_NONFINITE)) | ((F.flag & ERR_NOEXIST) ? ERR_NONFINITE : 0),
+                        flat_cell(j, x, nx, ny));
         T fprev[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
@@ -545,7 +559,7 @@ __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsig
     const float rc = rsqrtf(c2);
     const float c = c2 * rc;
     const float b1 = gm1 * (rc * rc), b2 = q2 * b1, uc = un * rc;
-    if (!(c2 > 0.f)) flag |= ERR_NONPHYSICAL;
+    if (!(c2 > 0.f)) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
     // rows of L in the rotated component order (rho, normal, tangential, E);
     // row 2 (shear) is (-vt, 0, 1, 0)
     const float L0[4] = {0.5f * (b2 + uc), -0.5f * (b1 * un + rc), -0.5f * (b1 * vt), 0.5f * b1};
@@ -699,7 +713,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
                 p.masks[((size_t)(4 + k) * ny + y) * (nx + 1) + (j + 1)] = (uint8_t)((cmk >> (5 * k)) & 31u);
             }
         }
-        if (flag && face_out && j >= -2 && j <= nx) latch_error(ctl, flag, j);
+        if (flag && face_out && j >= -2 && j <= nx) latch_error(ctl, flag, flat_cell(y, j, nx));
         float fprev[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
@@ -804,7 +818,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
                 ym[((size_t)(4 + k) * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)((cmk >> (5 * k)) & 31u);
             }
         }
-        if (flag && face_out && j >= -2 && j <= ny) latch_error(ctl, flag, j);
+        if (flag && face_out && j >= -2 && j <= ny) latch_error(ctl, flag, flat_cell(j, x, nx, ny));
         float fprev[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
