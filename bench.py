@@ -52,7 +52,7 @@ FLOPS_PER_CELL_STAGE = {"f32": 808.0, "f64": 776.0}
 # DRAM bytes per stage launch per cell measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, averaged over the three stage launches of one RK3
 # step at N = 16,777,600) for the current kernels; None when not captured.
-TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.51, "f64": 61.78}
+TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.49, "f64": 61.80}
 
 
 def peaks():
