@@ -957,7 +957,9 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     // Software pipelining: the raw state of a warp tile's staged cells (lane
     // and lane + 32) is loaded one tile ahead, and U^n of the tile's own cells
     // at the start of the tile, so DRAM latency overlaps the face work.
-    float ua[M], ub[M];
+    // (held in the state type and rounded to float only when the tile is
+    // used, so that a mixed-precision load is not waited for at once)
+    S ua[M], ub[M];
     auto load_tile = [&](int tile) {
         const int c0 = tile * WT;
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
@@ -965,8 +967,8 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (gb < 0 || gb >= n) gb = ghost_map(gb, n, A.bc_lo, A.bc_hi);
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            ua[k] = to_f32(Us[(size_t)k * cs + ga]);
-            ub[k] = (lane < WS - 32) ? to_f32(Us[(size_t)k * cs + gb]) : 0.f;
+            ua[k] = Us[(size_t)k * cs + ga];
+            ub[k] = (lane < WS - 32) ? Us[(size_t)k * cs + gb] : S(0);
         }
     };
     int tile = tile0;
@@ -981,11 +983,20 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
 #pragma unroll
             for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * cs + (ic < 0 ? 0 : ic)];
         }
+        // mixed: the FP64 stage input of the tile's own cells, which the RK
+        // update needs unrounded, loaded here so that its latency overlaps the
+        // face work (the staged copy is rounded to float)
+        S usr[M];
+        if (MIXED && !A.rhs_mode) {
+            const int ic = jc < n ? jc : n - 1;
+#pragma unroll
+            for (int k = 0; k < M; k++) usr[k] = Us[(size_t)k * cs + (ic < 0 ? 0 : ic)];
+        }
         float Ucur[2][M];
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            Ucur[0][k] = ua[k];
-            Ucur[1][k] = ub[k];
+            Ucur[0][k] = to_f32(ua[k]);
+            Ucur[1][k] = to_f32(ub[k]);
         }
         if (tile + tstride < ntiles) load_tile(tile + tstride);
 #pragma unroll
@@ -1178,7 +1189,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                 if (A.rhs_mode) {
                     o[k] = d * idxD;
                 } else {
-                    const double v = fma(cD, d, (double)Us[(size_t)k * cs + i]);
+                    const double v = fma(cD, d, (double)usr[k]);
                     if (A.stage == 0)
                         o[k] = v;
                     else if (A.stage == 1)

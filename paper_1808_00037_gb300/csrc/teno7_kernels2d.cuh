@@ -657,7 +657,9 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     float (*sgm)[WC] = s_gm[warp];
     float (*spr)[WC] = s_pr[warp];
     __syncthreads();
-    float ua[4], ub[4];
+    // one tile ahead, held in the state type and rounded to float only when
+    // the tile is used (a mixed-precision load is then not waited for at once)
+    S ua[4], ub[4];
     auto load_tile = [&](long tile) {
         const int y = (int)(tile / ntx);
         const int c0 = (int)(tile % ntx) * WT;
@@ -667,8 +669,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         if (gb < 0 || gb >= nx) gb = ghost_map(gb, nx, p.bc[0], p.bc[1]);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            ua[k] = to_f32(row[(size_t)k * N + ga]);
-            ub[k] = (lane < WS - 32) ? to_f32(row[(size_t)k * N + gb]) : 0.f;
+            ua[k] = row[(size_t)k * N + ga];
+            ub[k] = (lane < WS - 32) ? row[(size_t)k * N + gb] : S(0);
         }
     };
     const long tstride = (long)gridDim.x * WPB;
@@ -680,8 +682,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         float cur[2][4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            cur[0][k] = ua[k];
-            cur[1][k] = ub[k];
+            cur[0][k] = to_f32(ua[k]);
+            cur[1][k] = to_f32(ub[k]);
         }
         if (tile + tstride < ntiles) load_tile(tile + tstride);
 #pragma unroll
@@ -765,8 +767,10 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
 
     // ---- stage rows r0-5 .. r0+33 of columns x0 .. x0+31 (coalesced along x);
     // all of a thread's loads are issued before any is used
+    // (in the state type: a mixed-precision value is rounded to float only
+    // when it is used)
     constexpr int NSTG = (YB_STAGE * YB_COLS + WPB * 32 - 1) / (WPB * 32);
-    float Ust[NSTG][4];
+    S Ust[NSTG][4];
 #pragma unroll
     for (int sI = 0; sI < NSTG; sI++) {
         const int q = tid + sI * WPB * 32;
@@ -775,7 +779,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             int y = r0 - 5 + r;
             if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ust[sI][k] = to_f32(Us[(size_t)k * N + (size_t)y * nx + x]);
+            for (int k = 0; k < 4; k++) Ust[sI][k] = Us[(size_t)k * N + (size_t)y * nx + x];
         }
     }
 #pragma unroll
@@ -783,8 +787,10 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
         const int q = tid + sI * WPB * 32;
         const int r = q / YB_COLS, col = q % YB_COLS;
         if (q < YB_STAGE * YB_COLS && x0 + col < nx) {
-            float pr[4], gp[4], gm[4];
-            cell2d_f32<1>(Ust[sI], gm1, alpha, pr, gp, gm);
+            float uf[4], pr[4], gp[4], gm[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) uf[k] = to_f32(Ust[sI][k]);
+            cell2d_f32<1>(uf, gm1, alpha, pr, gp, gm);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 s_pr[(k * YB_STAGE + r) * YB_LD + col] = pr[k];
