@@ -90,3 +90,30 @@ def test_create_rejects_empty_and_oversized_grids_without_touching_the_device():
         g = B.t7_grid(sys_, B.T7_F32, nx, ny, 0.1, 0.1, bc, 1.4, 1.0, 1e-5, -1.0, -1.0)
         assert lib.t7_create(ctypes.byref(g), None, ctypes.byref(h)) == B.T7_EINVAL, (sys_, nx, ny)
         assert not h.value
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """include/teno7.h compiles as strict C99 (-Wall -Wextra -pedantic, no
+    warnings), and a C program linked against libteno7 calls t7_create with an
+    empty grid and gets T7_EINVAL back (no device work on that path)."""
+    import shutil
+    import subprocess
+    from paper_1808_00037_gb300 import build as cuda_build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_path = cuda_build.build()
+    src = tmp_path / "use.c"
+    src.write_text('#include "teno7.h"\n'
+                   "int main(void) {\n"
+                   "    t7_grid g = {0};\n"
+                   "    t7_ctx *c = 0;\n"
+                   "    g.sys = T7_EULER1D; g.prec = T7_F32; g.nx = 0; g.ny = 1; g.dx = 1.0;\n"
+                   "    return t7_create(&g, 0, &c) == T7_EINVAL && c == 0 ? 0 : 1;\n"
+                   "}\n")
+    exe = tmp_path / "use"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", str(ROOT / "include"),
+                        str(src), "-L", str(lib_path.parent), "-lteno7", f"-Wl,-rpath,{lib_path.parent}",
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
