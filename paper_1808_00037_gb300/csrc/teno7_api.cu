@@ -14,6 +14,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "teno7.h"
 #include "teno7_internal.h"
 #include "teno7_adjoint_params.h"
@@ -55,6 +57,15 @@ struct t7_ctx {
 };
 
 namespace {
+
+// NVTX range around an entry point (or a phase of one), for profiler
+// timelines; costs a pointer test when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 t7_status fail(t7_ctx *c, t7_status st, const char *fmt, ...) {
     if (c) {
@@ -200,6 +211,7 @@ cudaError_t alpha_init(t7_ctx *c, const void *U) {
 // copies.
 constexpr int OUT_PARTS = 8;
 cudaError_t last_stage_to_host(t7_ctx *c, t7::Stage1D p, void *host_out) {
+    TraceRange trace("last stage in parts, copied out");
     cudaError_t e = cudaSuccess;
     if (!c->cstream) {
         if ((e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -403,6 +415,7 @@ t7_status t7_sync(t7_ctx *c) {
 
 t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double eps, void *fhat, uint8_t *d3,
                                uint8_t *D5) {
+    TraceRange trace("t7_teno7_reconstruct");
     if (!c) return T7_EINVAL;
     if (!v || !fhat || n < 1 || (sign != 1 && sign != -1) || !(eps > 0.0))
         return fail(c, T7_EINVAL, "t7_teno7_reconstruct: bad argument");
@@ -425,6 +438,7 @@ t7_status t7_teno7_reconstruct(t7_ctx *c, const void *v, int n, int sign, double
 }
 
 t7_status t7_euler_rhs(t7_ctx *c, const void *U, void *dUdt, uint8_t *masks) {
+    TraceRange trace("t7_euler_rhs");
     t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !dUdt) return fail(c, T7_EINVAL, "t7_euler_rhs: null array");
@@ -449,6 +463,7 @@ t7_status t7_euler_rhs(t7_ctx *c, const void *U, void *dUdt, uint8_t *masks) {
 }
 
 t7_status t7_cfl_dt(t7_ctx *c, const void *U, double cfl, double *dt_out) {
+    TraceRange trace("t7_cfl_dt");
     t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !dt_out || !(cfl > 0.0)) return fail(c, T7_EINVAL, "t7_cfl_dt: bad argument");
@@ -468,6 +483,7 @@ t7_status t7_cfl_dt(t7_ctx *c, const void *U, double cfl, double *dt_out) {
 }
 
 t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
+    TraceRange trace("t7_rk3_step");
     t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step: bad argument");
@@ -570,6 +586,7 @@ static t7_status run_core(t7_ctx *c, void *U, double cfl, double t_end, int max_
 }
 
 t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out) {
+    TraceRange trace("t7_run");
     t7_status st = check_sys(c);
     if (st) return st;
     if (!U || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0)) return fail(c, T7_EINVAL, "t7_run: bad argument");
@@ -578,12 +595,17 @@ t7_status t7_run(t7_ctx *c, void *U, double cfl, double t_end, int max_steps, in
 
 t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out) {
+    TraceRange trace("t7_run_host");
     t7_status st = check_sys(c);
     if (st) return st;
     if (!U_host || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0))
         return fail(c, T7_EINVAL, "t7_run_host: bad argument");
     size_t bytes = c->ncell * c->m * c->esize;
-    cudaError_t e = cudaMemcpyAsync(c->Uhost, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e;
+    {
+        TraceRange phase("t7_run_host: copy in");
+        e = cudaMemcpyAsync(c->Uhost, U_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "H2D copy");
     // With a known number of steps (t_end = inf) in 1D, the last step's last
     // stage is launched in parts and each finished part is copied back while
@@ -708,6 +730,7 @@ static cudaError_t forward_masks(t7_ctx *c, const void *U, int slot, uint8_t *ma
 }
 
 t7_status t7_euler_rhs_adjoint(t7_ctx *c, const void *U, const void *v, void *out) {
+    TraceRange trace("t7_euler_rhs_adjoint");
     t7_status st = adj_check(c);
     if (st) return st;
     if (!U || !v || !out) return fail(c, T7_EINVAL, "t7_euler_rhs_adjoint: null array");
@@ -723,6 +746,7 @@ t7_status t7_euler_rhs_adjoint(t7_ctx *c, const void *U, const void *v, void *ou
 }
 
 t7_status t7_rk3_step_adjoint(t7_ctx *c, const void *U, double dt, void *lambda) {
+    TraceRange trace("t7_rk3_step_adjoint");
     t7_status st = adj_check(c);
     if (st) return st;
     if (!U || !lambda || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step_adjoint: bad argument");
@@ -771,6 +795,7 @@ t7_status t7_tape_bytes(t7_ctx *c, size_t *bytes) {
 }
 
 t7_status t7_rk3_step_record(t7_ctx *c, const void *U_in, void *U_out, double dt, void *tape) {
+    TraceRange trace("t7_rk3_step_record");
     t7_status st = adj_check(c);
     if (st) return st;
     if (!U_in || !U_out || !tape || !(dt > 0.0)) return fail(c, T7_EINVAL, "t7_rk3_step_record: bad argument");
@@ -811,6 +836,7 @@ t7_status t7_rk3_step_record(t7_ctx *c, const void *U_in, void *U_out, double dt
 }
 
 t7_status t7_rk3_step_adjoint_recorded(t7_ctx *c, const void *U_in, const void *tape, double dt, void *lambda) {
+    TraceRange trace("t7_rk3_step_adjoint_recorded");
     t7_status st = adj_check(c);
     if (st) return st;
     if (!U_in || !tape || !lambda || !(dt > 0.0))
@@ -975,6 +1001,7 @@ static t7_status batch_check(t7_ctx *c, void *U, const int64_t *offsets, const d
 
 t7_status t7_batch_run(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes, double t_end,
                        double cfl, int max_steps, int group_warps, int *steps_out, double *t_out) {
+    TraceRange trace("t7_batch_run");
     t7_status st = batch_check(c, U, offsets, dx, ntubes);
     if (st) return st;
     if (!(cfl > 0.0) || !(t_end >= 0.0) || max_steps < 0) return fail(c, T7_EINVAL, "t7_batch_run: bad argument");
@@ -996,6 +1023,7 @@ t7_status t7_batch_run(t7_ctx *c, void *U, const int64_t *offsets, const double 
 
 t7_status t7_batch_autotune(t7_ctx *c, const void *U, const int64_t *offsets, const double *dx, int ntubes,
                             double cfl, int trial_steps, int *group_out, float *ms_out) {
+    TraceRange trace("t7_batch_autotune");
     t7_status st = batch_check(c, (void *)U, offsets, dx, ntubes);
     if (st) return st;
     if (!(cfl > 0.0) || trial_steps < 1) return fail(c, T7_EINVAL, "t7_batch_autotune: bad argument");
