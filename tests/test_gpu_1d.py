@@ -425,3 +425,36 @@ def test_streams_switching_and_error_text():
         assert ei.value.status == B.T7_EINVAL and "bad argument" in str(ei.value)
         c.close()
         c.close()
+
+
+def test_advection_full_size_sampled():
+    """The advection workload the bench times (sin(pi x) on [-1, 1], N = 2^24,
+    periodic).  With alpha = |a| fixed, the RHS at a cell depends on the 4
+    cells each side and one fixed-dt RK3 step on 12, so the oracle on 33-cell
+    windows (wrapped at the periodic ends) gives those cells exactly: at 64
+    sampled cells, both ends included, the FP64 RHS and RK3 step are
+    bit-identical to it, and the FP32 RHS is within the FP32 rounding bound of
+    the face fluxes, 64 * 2^-24 * max|F| / dx."""
+    n = 1 << 24
+    U, dx, _ = I.advection_sine(n)
+    dt = 0.2 * dx
+    rng = np.random.default_rng(5)
+    cells = [0, 1, 2, n - 3, n - 2, n - 1] + [int(i) for i in rng.integers(0, n, 58)]
+    c = ctx(oracle.SYS_ADVECTION, n, dx)
+    Ug = dev(U)
+    r64 = host(c.euler_rhs(Ug)[0])
+    c.rk3_step(Ug, dt)
+    s64 = host(Ug)
+    c32 = ctx(oracle.SYS_ADVECTION, n, dx, prec=B.T7_F32)
+    r32 = host(c32.euler_rhs(dev(U, torch.float32))[0])
+    bound = 64 * 2.0**-24 * np.abs(U).max() / dx
+    H = 16
+    for i in cells:
+        win = np.take(U, np.arange(i - H, i + H + 1), axis=1, mode="wrap")
+        ro, _, _ = oracle.rhs_1d(oracle.SYS_ADVECTION, win, dx, bc=(1, 1))
+        so, steps, _, st = oracle.run_1d(oracle.SYS_ADVECTION, win, dx, t_end=1.0, dt_fixed=dt, max_steps=1,
+                                         bc=(1, 1))
+        assert st == 0 and steps == 1
+        assert r64[0, i] == ro[0, H], i
+        assert s64[0, i] == so[0, H], i
+        assert abs(float(r32[0, i]) - ro[0, H]) <= bound, i
