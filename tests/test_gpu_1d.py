@@ -261,6 +261,43 @@ def test_full_size_rhs_sampled_f64():
         assert np.array_equal(mg[:, :, i].cpu().numpy(), mo[:, :, k]), i
 
 
+@pytest.mark.parametrize("prec,dtype", [(B.T7_F32, torch.float32), (B.T7_MIXED, torch.float64)], ids=["f32", "mixed"])
+def test_full_size_rhs_sampled_f32_and_mixed(prec, dtype):
+    """FP32 and mixed forms at the benchmark size, on the windows of the FP64
+    test: the Delta codes of the sampled cells' two faces agree with the
+    oracle's on >= 99% of the entries, and where they all agree the RHS is
+    within the FP32 rounding bound 64 * 2^-24 * max|F| / dx (alpha differs at
+    FP32 rounding level, so the split fluxes do)."""
+    U, dx = I.shu_osher(1600, tiles=NBIG // 1600)
+    n = U.shape[1]
+    alpha = oracle.alpha_1d(oracle.SYS_EULER1D, U)
+    c = ctx(oracle.SYS_EULER1D, n, dx, bc=(1, 1), prec=prec)
+    rg, mg = c.euler_rhs(dev(U, dtype), want_masks=True)
+    c.sync()
+    rho, u, pr = I.cons_to_prim_1d(U)
+    fmax = np.max(np.abs(np.stack([U[1], U[1] * u + pr, u * (U[2] + pr)])))
+    bound = 64 * 2.0**-24 * fmax / dx
+    rng = np.random.default_rng(9)
+    idx = np.concatenate([[0, 1, 2, 3, 252, 253, n - 1, n - 2, n - 5], rng.integers(0, n, 200)])
+    W = 12
+    same = total = checked = 0
+    for i in idx:
+        lo, hi = max(0, i - W), min(n, i + W + 1)
+        ro, _, mo = oracle.rhs_1d(oracle.SYS_EULER1D, U[:, lo:hi], dx, bc=(1, 1), alpha=alpha, want_masks=True)
+        k = i - lo
+        if (lo > 0 and k < 6) or (hi < n and (hi - lo) - k < 7):
+            continue
+        mgi = mg[:, :, i:i + 2].cpu().numpy()
+        moi = mo[:, :, k:k + 2]
+        same += int((mgi == moi).sum())
+        total += mgi.size
+        if np.array_equal(mgi, moi):
+            checked += 1
+            assert np.max(np.abs(host(rg[:, i:i + 1])[:, 0] - ro[:, k])) <= bound, i
+    assert same >= 0.99 * total, (same, total)
+    assert checked >= 150
+
+
 @pytest.mark.parametrize("prec,dtype", [(B.T7_F64, torch.float64), (B.T7_F32, torch.float32)])
 def test_full_size_periodic_conservation(prec, dtype):
     """At the benchmark size with periodic ends, three SSP-RK3 steps conserve
