@@ -107,15 +107,16 @@ def test_2d_mixed_runs_against_oracle():
     assert np.abs(Ug.cpu().numpy()[0] - Uo[0]).sum() / np.abs(Uo[0]).sum() < 1e-3
 
 
-def test_2d_f32_full_size_sampled():
-    """2048^2 quadrants (the benchmark size): the FP32 RHS on sampled cells is
-    within the FP32 bound of the oracle on 25 x 25 windows wherever the
-    sampled cell's eight Delta codes of each face agree."""
+@pytest.mark.parametrize("prec,dtype", [(B.T7_F32, torch.float32), (B.T7_MIXED, torch.float64)], ids=["f32", "mixed"])
+def test_2d_f32_full_size_sampled(prec, dtype):
+    """2048^2 quadrants (the benchmark size): the FP32 and mixed RHS on sampled
+    cells are within the FP32 bound of the oracle on 25 x 25 windows wherever
+    the sampled cell's eight Delta codes of each face agree."""
     n = 2048
     U, dx, dy, _ = I.quadrants_2d(4, n, n)
     ax, ay = oracle.alpha_2d(U)
-    c = ctx(n, n, dx, dy, B.T7_F32, ZG)
-    rg, (mxg, myg) = c.euler_rhs(torch.tensor(U, dtype=torch.float32, device="cuda"), want_masks=True)
+    c = ctx(n, n, dx, dy, prec, ZG)
+    rg, (mxg, myg) = c.euler_rhs(torch.tensor(U, dtype=dtype, device="cuda"), want_masks=True)
     c.sync()
     rg = rg.double().cpu().numpy()
     rng = np.random.default_rng(2)
