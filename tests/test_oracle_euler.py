@@ -265,3 +265,20 @@ def test_2d_order_on_the_isentropic_vortex(orc):
         errs.append(np.abs(r - exact)[:, core].max())
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(orders > 6.6) and orders[-1] > 6.85 and np.all(orders < 7.3), orders
+
+
+def test_1d_euler_order_on_an_entropy_wave(orc):
+    """rho = 1 + 0.2 sin(2 pi x), u = p = 1 on a periodic [0, 1): an exact
+    solution that translates with speed 1, so L(U) = -(rho', rho', rho'/2)
+    exactly.  Every stencil of every field is kept and the maximum error falls
+    at order ~7 (N = 20, 40, 80; at N = 160 it nears FP64 round-off)."""
+    errs = []
+    for n in (20, 40, 80):
+        x = (np.arange(n) + 0.5) / n
+        U = I.prim_to_cons_1d(1 + 0.2 * np.sin(2 * np.pi * x), np.ones(n), np.ones(n))
+        dr = 0.4 * np.pi * np.cos(2 * np.pi * x)
+        r, _, m = orc.rhs_1d(orc.SYS_EULER1D, U, 1.0 / n, want_masks=True)
+        assert np.all(m == 31)
+        errs.append(np.abs(r + np.stack([dr, dr, 0.5 * dr])).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 6.9) and np.all(orders < 7.1), orders
