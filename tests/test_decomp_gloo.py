@@ -4,12 +4,10 @@ ranks, each rank computing its padded slab's RHS with the oracle.  The
 gathered result must be bit-identical to the unsplit oracle run, which pins
 the halo width, the boundary handling at the domain ends and the
 synchronisation of alpha and dt."""
-import os
 import socket
 
 import numpy as np
 import pytest
-import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

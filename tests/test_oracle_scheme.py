@@ -3,7 +3,6 @@
 data, the measured order of accuracy, the exact shift of linear advection,
 conservation, mirror symmetry of the '-' split, and non-oscillatory selection
 at a jump."""
-from fractions import Fraction as Fr
 
 import numpy as np
 import pytest

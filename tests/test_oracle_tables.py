@@ -17,7 +17,6 @@ from fractions import Fraction as Fr
 from pathlib import Path
 
 import numpy as np
-import pytest
 
 GOLD = Path(__file__).parent / "golden"
 

@@ -7,7 +7,6 @@ from fractions import Fraction as Fr
 from pathlib import Path
 
 import numpy as np
-import pytest
 
 import oracle
 from oracle import riemann

@@ -7,7 +7,6 @@ reject sizes beyond its fixed scratch with a clear error.  Kept in a file
 that pytest collects last."""
 import ctypes
 
-import numpy as np
 import pytest
 
 from paper_1808_00037_gb300 import binding as B
