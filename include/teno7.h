@@ -133,10 +133,22 @@ t7_status t7_teno7_reconstruct(t7_ctx *ctx, const void *v_padded, int n, int sig
  *             i+1/2, i = -1 .. nx-1.  Async. */
 t7_status t7_euler_rhs(t7_ctx *ctx, const void *U, void *dUdt, uint8_t *masks);
 
-/* dt = CFL dx / alpha(U) (1D).  Synchronises; *dt_out is a host double. */
+/* Time step from the CFL condition of the global Lax-Friedrichs scheme (Sec.
+ * "One dimensional Euler equations": one alpha = max_i (|u_i| + c_i) over the
+ * whole domain, the same alpha that splits the flux): dt = CFL dx / alpha(U)
+ * in 1D, CFL / (alpha_x/dx + alpha_y/dy) in 2D.  U: device, the context's
+ * layout.  Synchronises; *dt_out is a host double.  Non-physical or
+ * non-finite cells return their status and leave *dt_out unset. */
 t7_status t7_cfl_dt(t7_ctx *ctx, const void *U, double cfl, double *dt_out);
 
-/* One SSP-RK3 step (Shu-Osher form) of size dt, in place on device U.  Async. */
+/* One step of the third-order SSP Runge-Kutta method (Sec. 2.1, Gottlieb-Shu;
+ * the paper omits the formula, so the Shu-Osher form is used):
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ *   U  = 1/3 U + 2/3 (U2 + dt L(U2)),
+ * each L the right-hand side of t7_euler_rhs with alpha recomputed from that
+ * stage's state.  In place on device U (the context's layout), fixed dt > 0.
+ * Async; non-physical or non-finite states met are latched and returned by
+ * the next synchronising call. */
 t7_status t7_rk3_step(t7_ctx *ctx, void *U, double dt);
 
 /* March device U in place until t_end (last step clipped to land on it) or
@@ -186,7 +198,8 @@ t7_status t7_rk3_step_adjoint_recorded(t7_ctx *ctx, const void *U_in, const void
  * length, each advanced by its own SSP-RK3 loop with its own CFL step
  * dt = CFL dx_t / alpha_t(U^n) to t_end (or max_steps), all in ONE persistent
  * launch: groups of `group_warps` warps take tubes from a device work queue,
- * costliest (longest) first, so no host round trip happens per step.  The
+ * costliest first (cells x estimated steps), so no host round trip happens
+ * per step.  The
  * scheme inside each tube is exactly t7_run's (Eq. app, the TENO7-ext
  * reconstruction, Remark 3, SSP-RK3).
  *   ctx          created with sys = T7_EULER1D, nx = total cells, bc[0..1]
@@ -197,7 +210,8 @@ t7_status t7_rk3_step_adjoint_recorded(t7_ctx *ctx, const void *U_in, const void
  *   dx           host, per-tube cell width (epsilon = dx^3 per tube)
  *   group_warps  1, 2, 4 or 8: that many warps per tube, for every tube;
  *                -1, -2, -4 or -8: the same group size, but the costliest
- *                tubes -- those whose estimated cost (cells^2) is above half
+ *                tubes -- those whose estimated cost (cells x estimated
+ *                steps, the steps from the tube's initial wave speed) is above half
  *                of one group's share of the whole batch -- run first on
  *                whole 8-warp CTAs, so that no single tube sets the run time
  *                (with -8 there is nothing to split off);

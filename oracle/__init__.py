@@ -11,7 +11,11 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                   golden copies of the printed tables, and the
                                   "no reconstruction crosses a discontinuity"
                                   rule checked exhaustively over all 32 vectors.
-  or_face_bits                 -- hand-computed windows (constant, step).
+  or_face_bits                 -- hand-computed windows (constant, step), and two
+                                  windows whose smallest chi lies just above and
+                                  just below C_T, evaluated in exact rationals
+                                  (they fail for q = 2, 4, 8, C = 0, a missing
+                                  normalisation, a wrong tau or a reversed window).
   teno7_reconstruct / rhs_1d   -- linear 7th-order upwind recovery on smooth
                                   data, measured order >= 6.5, conservation,
                                   mirror symmetry, uniform-flow invariance.

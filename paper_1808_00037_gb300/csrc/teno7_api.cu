@@ -37,7 +37,7 @@ struct t7_ctx {
     int *b_order, *b_steps, *b_queue;
     int b_cap;
     int b_group;           // warps per tube chosen by t7_batch_autotune (0: not tuned)
-    std::vector<double> b_cost;  // estimated cost (cells^2) of the tubes in processing order
+    std::vector<double> b_cost;  // estimated cost (cells x estimated steps) of the tubes in processing order
     void *adj[3];          // adjoint work vectors (allocated on first use)
     uint8_t *adj_masks[3]; // FP32: forward masks of the three stage states
     t7::DevCtl *ctl_host;  // pinned mirror for status reads

@@ -9,27 +9,27 @@
 //                 rescaled form (g_k / g_max)^6 because gamma_k = (1 + r)^6
 //                 overflows FP32 near strong jumps.
 //
-// Tile design (1D).  One CTA of NT = 256 threads owns the faces j+1/2,
-// j = s-2 .. s+253, one face per thread, and updates the TILE = 253 cells
-// s .. s+252.  Per-cell data for cells s-5 .. s+257 (the face stencils plus
-// halo) are staged once in shared memory: conserved variables, the global
-// Lax-Friedrichs split fluxes G+- = (F +- alpha U)/2, and for the Euler system
-// u, H and sqrt(rho) for the Roe average.  Each thread then
-//   1. builds its face's Roe frame (L, R) and projects the 8 cells it needs
-//      into characteristic fields, keeping q+ (7 cells) and q- (7 cells) per
-//      field in registers;
+// Tile design (1D).  The work unit is a warp tile: one warp owns the 32
+// faces j+1/2, j = c0-2 .. c0+29, one face per lane, and updates the WT = 29
+// cells c0 .. c0+28.  The 39 cells c0-5 .. c0+33 that those faces' stencils
+// reach are staged in warp-private shared memory (conserved variables, the
+// global Lax-Friedrichs split fluxes G+- = (F +- alpha U)/2 and, for the Euler
+// system, u, H and sqrt(rho) for the Roe average), so no CTA-wide barrier is
+// needed inside the loop; warps stride over tiles.  Each lane then
+//   1. builds its face's Roe frame (L, R) and projects the cells it needs into
+//      characteristic fields (q+ on cells j-3 .. j+3, q- on j-2 .. j+4);
 //   2. computes the three cutoff bits of both splits of every field (Eqs.
-//      smooth_expl, tau5, TENO1, norm, seclect) and publishes them as one
-//      word in shared memory -- the "store the smoothness of the whole field
-//      first" step of the paper, done per tile;
-//   3. after a barrier, reads the neighbouring faces' words, forms Delta_i
-//      (Eq. vec) for each split and field, looks the polynomial up (Table co3,
-//      a 32 x 4-bit table held in two 64-bit immediates) and evaluates it
-//      (Table co2, 7 taps, coefficients in shared memory);
-//   4. back-projects with R and publishes the face flux; after a barrier the
-//      cell threads take the flux difference (Eq. app), apply the SSP-RK3
-//      stage, write the new state and reduce max(|u| + c) of it for the next
-//      stage's alpha (one atomicMax per CTA).
+//      smooth_expl, tau5, TENO1, norm, seclect) -- the paper's "measure the
+//      smoothness of every face first" pass, kept per warp tile;
+//   3. takes the neighbouring faces' bits by __shfl (faces i-1/2 and i+3/2 are
+//      the adjacent lanes), forms Delta_i (Eq. vec) for each split and field,
+//      selects the polynomial (Table co3) and evaluates it (Table co2, 7 taps);
+//   4. back-projects with R; the face flux of lane l-1 arrives by __shfl, and
+//      lanes 2..30 take the flux difference (Eq. app), apply the SSP-RK3 stage,
+//      write the new state and fold max(|u| + c) of it into the next stage's
+//      alpha (a warp/CTA reduction, one atomicMax per CTA).
+// The FP32 kernel (stage1d_f32_kernel below) keeps this structure with the two
+// splits paired in float2 registers.
 #pragma once
 #include <math.h>
 #include <stdint.h>

@@ -9,6 +9,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "teno7.h"
 #include "teno7_internal.h"
 
@@ -18,10 +20,16 @@ static __device__ __align__(256) unsigned char t7_static_scratch[T7_STATIC_SCRAT
 namespace {
 
 constexpr int kMaxDevices = 64;
-// Device address of t7_static_scratch per device ordinal, filled on the first
-// call made on that device.  (The name t7_static_scratch in host code is only
-// a host-side stand-in, never a device address.)
-void *g_scratch[kMaxDevices];
+// Device address of t7_static_scratch per device ordinal, looked up once per
+// device (std::call_once, so host threads making their first calls at the
+// same time do not race on the slot).  The name t7_static_scratch in host
+// code is only a host-side stand-in, never a device address.
+struct ScratchSlot {
+    std::once_flag once;
+    void *ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+ScratchSlot g_scratch[kMaxDevices];
 
 constexpr size_t kCtlBytes = (sizeof(t7::DevCtl) + 255) / 256 * 256;
 
@@ -60,14 +68,14 @@ extern "C" t7_status t7_rk3_step_static(const t7_grid *g, void *U, double dt, vo
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return report(errbuf, errlen, T7_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return report(errbuf, errlen, T7_EINVAL, "device ordinal %d too large", dev);
-    if (!g_scratch[dev]) {  // set-up, once per device, with that device current
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, t7_static_scratch);
-        if (e != cudaSuccess || !ptr)
-            return report(errbuf, errlen, T7_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_scratch[dev] = ptr;
-    }
-    unsigned char *base = static_cast<unsigned char *>(g_scratch[dev]);
+    ScratchSlot &slot = g_scratch[dev];
+    std::call_once(slot.once, [&slot] {  // set-up, once per device, with that device current
+        slot.err = cudaGetSymbolAddress(&slot.ptr, t7_static_scratch);
+        if (slot.err == cudaSuccess && !slot.ptr) slot.err = cudaErrorInvalidSymbol;
+    });
+    if (slot.err != cudaSuccess)
+        return report(errbuf, errlen, T7_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(slot.err));
+    unsigned char *base = static_cast<unsigned char *>(slot.ptr);
     t7::DevCtl *ctl = reinterpret_cast<t7::DevCtl *>(base);
     void *U1 = base + kCtlBytes;
     void *U2 = base + kCtlBytes + buf;

@@ -183,3 +183,53 @@ def test_cutoff_threshold_direction(orc):
     below, _ = orc.face_bits(w, eps, CT=chi[k] * (1 + 1e-9))
     above, _ = orc.face_bits(w, eps, CT=chi[k] * (1 - 1e-9))
     assert (below >> k) & 1 == 0 and (above >> k) & 1 == 1
+
+
+# Marginal cutoff windows, evaluated by hand in exact arithmetic.  The window
+# w = (f_{i-2}, .., f_{i+2}) = (0, 0, 1, 2, 0) gives, by Eq. smooth_expl,
+#   beta_0 = 1/4 (0 - 0 + 3)^2 + 13/12 (0 - 0 + 1)^2   = 9/4 + 13/12   = 10/3
+#   beta_1 = 1/4 (0 - 2)^2     + 13/12 (0 - 2 + 2)^2   = 1 + 0         = 1
+#   beta_2 = 1/4 (3 - 8 + 0)^2 + 13/12 (1 - 4 + 0)^2   = 25/4 + 39/4   = 16
+# and tau_5 = |beta_0 - beta_2| = 38/3 (Eq. tau5).  With C = 1, q = 6
+# (Eq. TENO1), gamma_k = g_k^6 where g_k = 1 + tau_5 / (beta_k + eps):
+#   eps = 1/6:  g = (1 + 76/21, 1 + 76/7, 1 + 76/97) = (97/21, 83/7, 173/97)
+#               chi_2 = g_2^6 / sum g^6 = 1.1541e-5, between C_T and 2 C_T
+#   eps = 1/8:  g = (1 + 304/83, 1 + 304/27, 1 + 304/387) = (387/83, 331/27, 691/387)
+#               chi_2 = 9.517e-6, just below C_T
+# (Eq. norm), so by Eq. seclect with C_T = 1e-5 the first keeps all three
+# stencils (bits 111) and the second cuts stencil 2 (bits 011).  chi_0 and
+# chi_1 are 3.5e-3 / 3.0e-3 and 0.9965 / 0.9970, far from the threshold.
+# Each of these mistakes changes the bits of one of the two windows:
+# q = 2, 4 or 8; C = 0; no normalisation (delta from gamma itself); tau from
+# |beta_0 - beta_1| or |beta_1 - beta_2|; the window read in reverse order.
+MARGINAL_W = [0.0, 0.0, 1.0, 2.0, 0.0]
+MARGINAL_BETA = (Fr(10, 3), Fr(1), Fr(16))
+MARGINAL_CASES = [
+    # eps, (g_0, g_1, g_2), chi_2 bounds, bits
+    (Fr(1, 6), (Fr(97, 21), Fr(83, 7), Fr(173, 97)), (Fr(115, 10**7), Fr(116, 10**7)), 0b111),
+    (Fr(1, 8), (Fr(387, 83), Fr(331, 27), Fr(691, 387)), (Fr(95, 10**7), Fr(96, 10**7)), 0b011),
+]
+
+
+def test_cutoff_marginal_windows_exact(orc):
+    """Eqs. smooth_expl, tau5, TENO1 (C = 1, q = 6), norm and seclect pinned
+    by two windows whose smallest chi lies within a factor 2 of C_T = 1e-5,
+    worked out by hand above; the rationals there are re-checked here with
+    exact arithmetic before the oracle's bits and betas are compared."""
+    tau = abs(MARGINAL_BETA[0] - MARGINAL_BETA[2])
+    assert tau == Fr(38, 3)
+    for eps, g_hand, (lo, hi), bits_hand in MARGINAL_CASES:
+        g = tuple(1 + tau / (b + eps) for b in MARGINAL_BETA)
+        assert g == g_hand
+        gam = [x ** 6 for x in g]
+        chi = [x / sum(gam) for x in gam]
+        assert lo < chi[2] < hi
+        assert bits_hand == sum((0 if chi[k] < Fr(1, 10**5) else 1) << k for k in range(3))
+        bits, beta = orc.face_bits(MARGINAL_W, float(eps), CT=1e-5)
+        assert bits == bits_hand, (float(eps), bits)
+        # beta_1 and beta_2 are exact in FP64; beta_0 = 9/4 + fl(13/12) is 10/3 to rounding
+        assert abs(beta[0] - float(MARGINAL_BETA[0])) <= 2 * np.spacing(10.0 / 3.0)
+        assert beta[1] == 1.0 and beta[2] == 16.0
+    # the mirrored window moves the marginal stencil from 2 to 0
+    bits, _ = orc.face_bits(MARGINAL_W[::-1], 1.0 / 8.0, CT=1e-5)
+    assert bits == 0b110
