@@ -236,6 +236,39 @@ t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const doubl
 t7_status t7_batch_autotune(t7_ctx *ctx, const void *U, const int64_t *offsets, const double *dx, int ntubes,
                             double cfl, int trial_steps, int *group_out, float *ms_out);
 
+/* Slabs of a decomposed 1D domain (one per rank, or per stream).  The scheme
+ * is the conservative form Eq. app, whose stencils reach 4 cells per side
+ * (the RHS at cell i depends on cells i-4 .. i+4: faces i-1/2 and i+1/2, their
+ * 7-point polynomials and their neighbour faces' cutoff bits, Eq. vec), with
+ * one global Lax-Friedrichs alpha over the whole domain (Sec. "One
+ * dimensional Euler equations").  So a slab of nx cells takes every array
+ * PADDED: [m][nx + 8], row stride nx + 8, cell 0 at offset 4; the 4 cells
+ * before and after are halos the caller fills (from the neighbouring slabs,
+ * or from the domain's boundary condition at its real ends) before a call
+ * reads them.  alpha values are device doubles, so that a collective
+ * (all-reduce max over the slabs) can feed them without a host round trip.
+ * The context is created for the slab (nx = its cell count); its bc[] is
+ * not used by these calls.  Async.
+ * t7_slab_alpha: max_i (|u_i| + c_i) over the slab's own cells into the
+ *   device double *alpha_out (reads only the interior of U).
+ * t7_slab_rhs: L(U) = -(F_{i+1/2} - F_{i-1/2})/dx (Eq. app) of the slab's
+ *   cells with the given global alpha (device double) into dUdt ([m][nx],
+ *   unpadded); masks as t7_euler_rhs's (device or NULL).
+ * t7_slab_stage: stage k (0, 1, 2) of the SSP-RK3 step (Sec. 2.1) of fixed
+ *   dt, Shu-Osher form as t7_rk3_step:
+ *     k = 0: out = Us + dt L(Us);  k = 1: out = 3/4 U0 + 1/4 (Us + dt L(Us));
+ *     k = 2: out = 1/3 U0 + 2/3 (Us + dt L(Us)),
+ *   with L from the global alpha of Us (device double *alpha).  Us, U0, out
+ *   padded; only out's interior is written, and out may not alias Us (U0
+ *   may alias out: the usual k = 2 call updates U^n in place).  alpha_out
+ *   (device double or NULL) receives max(|u| + c) over the output's cells,
+ *   the slab's part of the next stage's alpha.
+ * Non-physical or non-finite states are latched as for t7_rk3_step. */
+t7_status t7_slab_alpha(t7_ctx *ctx, const void *U, double *alpha_out);
+t7_status t7_slab_rhs(t7_ctx *ctx, const void *U, const double *alpha, void *dUdt, uint8_t *masks);
+t7_status t7_slab_stage(t7_ctx *ctx, int k, const void *Us, const void *U0, void *out, const double *alpha, double dt,
+                        double *alpha_out);
+
 /* The paper has no counterpart to this call: it serves callers that cannot
  * allocate device memory -- plug-ins whose host application owns every device
  * allocation, real-time loops that forbid allocation after start-up, and

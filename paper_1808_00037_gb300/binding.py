@@ -21,6 +21,7 @@ T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
 T7_F64, T7_F32, T7_MIXED = 0, 1, 2
 T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
 T7_TENO7EXT, T7_TENO5 = 0, 1
+T7_PROBE_F32, T7_PROBE_F32X2, T7_PROBE_F64 = 0, 1, 2
 
 _STATUS = {0: "T7_OK", -1: "T7_EINVAL", -2: "T7_ECUDA", -3: "T7_ENONPHYSICAL", -4: "T7_ENONFINITE",
            -5: "T7_ETIMEOUT", -6: "T7_ENOMEM"}
@@ -73,6 +74,10 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_rk3_step_record": ([vp, vp, vp, d, vp], i),
         "t7_rk3_step_adjoint_recorded": ([vp, vp, vp, d, vp], i),
         "t7_batch_autotune": ([vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), vp], i),
+        "t7_probe_fma": ([i, i, i, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)], i),
+        "t7_slab_alpha": ([vp, vp, vp], i),
+        "t7_slab_rhs": ([vp, vp, vp, vp, u8p], i),
+        "t7_slab_stage": ([vp, i, vp, vp, vp, vp, d, vp], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -178,6 +183,45 @@ class Context:
         self._check(self.lib.t7_cfl_dt(self.h, _ptr(self._dev(U)), cfl, ctypes.byref(dt)), "t7_cfl_dt")
         return dt.value
 
+    # -- slabs of a decomposed 1D domain: padded arrays [m, nx + 8], device alphas
+    def _padded(self, t):
+        t = self._dev(t)
+        if t.shape[-1] != self.nx + 8 or t.numel() != self.m * (self.nx + 8):
+            raise ValueError(f"expected a padded slab array [{self.m}, {self.nx + 8}]")
+        return t
+
+    def _alpha(self, a):
+        torch = self._torch
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.numel() >= 1):
+            raise ValueError("alpha values are CUDA float64 tensors")
+        return a
+
+    def slab_alpha(self, U, alpha_out):
+        """max(|u| + c) of the slab's cells (the interior of padded U) into the
+        device double tensor alpha_out (one element)."""
+        self._check(self.lib.t7_slab_alpha(self.h, _ptr(self._padded(U)), _ptr(self._alpha(alpha_out))),
+                    "t7_slab_alpha")
+        return alpha_out
+
+    def slab_rhs(self, U, alpha, out=None, want_masks: bool = False):
+        """L(U) of the slab's cells (padded U, halos filled) with the global
+        alpha (device double tensor); returns dU/dt [m, nx] (and the masks)."""
+        torch = self._torch
+        U = self._padded(U)
+        out = torch.empty((self.m, self.nx), dtype=U.dtype, device=U.device) if out is None else self._dev(out)
+        masks = torch.empty((2, self.m, self.nx + 1), dtype=torch.uint8, device=U.device) if want_masks else None
+        self._check(self.lib.t7_slab_rhs(self.h, _ptr(U), _ptr(self._alpha(alpha)), _ptr(out), _ptr(masks)),
+                    "t7_slab_rhs")
+        return (out, masks) if want_masks else out
+
+    def slab_stage(self, k: int, Us, U0, out, alpha, dt: float, alpha_out=None):
+        """SSP-RK3 stage k of fixed dt on padded slab arrays (see t7_slab_stage)."""
+        U0 = None if U0 is None else self._padded(U0)
+        alpha_out = None if alpha_out is None else self._alpha(alpha_out)
+        self._check(self.lib.t7_slab_stage(self.h, k, _ptr(self._padded(Us)), _ptr(U0), _ptr(self._padded(out)),
+                                           _ptr(self._alpha(alpha)), dt, _ptr(alpha_out)), "t7_slab_stage")
+        return out
+
     def rk3_step(self, U, dt: float):
         self._check(self.lib.t7_rk3_step(self.h, _ptr(self._dev(U)), dt), "t7_rk3_step")
         return U
@@ -276,3 +320,15 @@ class Context:
 
     def sync(self):
         self._check(self.lib.t7_sync(self.h), "t7_sync")
+
+
+def probe_fma(kind: int, iters: int = 4096, repeats: int = 3, stream=None) -> tuple[float, float]:
+    """Measured FMA rate of the device (t7_probe_fma): (TFLOP/s, ms per launch)."""
+    import torch
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    tf, ms = ctypes.c_double(), ctypes.c_float()
+    st = lib.t7_probe_fma(kind, iters, repeats, ctypes.c_void_p(s.cuda_stream), ctypes.byref(tf), ctypes.byref(ms))
+    if st != T7_OK:
+        raise T7Error(st, "t7_probe_fma failed")
+    return tf.value, ms.value

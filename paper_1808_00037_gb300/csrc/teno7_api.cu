@@ -493,6 +493,88 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
     return T7_OK;
 }
 
+// ---------------------------------------------------------------- slabs ----
+// One rank's (or one stream's) part of a 1D domain split into slabs: arrays
+// padded by HALO_CELLS cells per side, halos filled by the caller, the global
+// alpha passed in as a device value (see include/teno7.h).
+static t7_status slab_check(t7_ctx *c, const char *what) {
+    if (!c) return T7_EINVAL;
+    if (!is_1d(c->g.sys)) return fail(c, T7_EINVAL, "%s: a 1D system only", what);
+    return T7_OK;
+}
+
+static t7::Stage1D slab_params(t7_ctx *c, const void *Us, const void *U0, void *out, const double *alpha_in) {
+    t7::Stage1D p = stage_params(c, Us, U0, out);
+    p.halo = 1;
+    p.alpha_in = alpha_in;
+    return p;
+}
+
+// alpha of the slab's cells (the padded array's interior) into *alpha_out
+static cudaError_t slab_alpha_launch(t7_ctx *c, const void *U, double *alpha_out) {
+    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[0][0], 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    t7::Alpha1D a;
+    memset(&a, 0, sizeof(a));
+    a.U = static_cast<const char *>(U) + t7::HALO_CELLS * c->esize;
+    a.n = c->g.nx;
+    a.stride = c->g.nx + 2 * t7::HALO_CELLS;
+    a.sys = c->g.sys;
+    a.gamma = c->g.gamma;
+    a.a = c->g.adv_speed;
+    a.ctl = c->ctl;
+    a.slot = 0;
+    a.alpha_rec = alpha_out;
+    return c->g.prec != T7_F32 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
+}
+
+extern "C" t7_status t7_slab_alpha(t7_ctx *c, const void *U, double *alpha_out) {
+    TraceRange trace("t7_slab_alpha");
+    t7_status st = slab_check(c, "t7_slab_alpha");
+    if (st) return st;
+    if (!U || !alpha_out) return fail(c, T7_EINVAL, "t7_slab_alpha: null pointer");
+    cudaError_t e = slab_alpha_launch(c, U, alpha_out);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slab alpha launch");
+    return T7_OK;
+}
+
+extern "C" t7_status t7_slab_rhs(t7_ctx *c, const void *U, const double *alpha, void *dUdt, uint8_t *masks) {
+    TraceRange trace("t7_slab_rhs");
+    t7_status st = slab_check(c, "t7_slab_rhs");
+    if (st) return st;
+    if (!U || !alpha || !dUdt) return fail(c, T7_EINVAL, "t7_slab_rhs: null pointer");
+    t7::Stage1D p = slab_params(c, U, nullptr, dUdt, alpha);
+    p.rhs_mode = 1;
+    p.masks = masks;
+    cudaError_t e = stage(c, p);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slab rhs launch");
+    return T7_OK;
+}
+
+extern "C" t7_status t7_slab_stage(t7_ctx *c, int k, const void *Us, const void *U0, void *out, const double *alpha,
+                                   double dt, double *alpha_out) {
+    TraceRange trace("t7_slab_stage");
+    t7_status st = slab_check(c, "t7_slab_stage");
+    if (st) return st;
+    if (k < 0 || k > 2 || !Us || !out || !alpha || !(dt > 0.0) || (k > 0 && !U0))
+        return fail(c, T7_EINVAL, "t7_slab_stage: bad argument");
+    if (Us == out) return fail(c, T7_EINVAL, "t7_slab_stage: the stage input may not alias the output");
+    // the slot this launch reduces the output's alpha into starts at zero
+    const int so = (k + 1) % 3;
+    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[so][0], 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slab stage slot");
+    t7::Stage1D p = slab_params(c, Us, k == 0 ? nullptr : U0, out, alpha);
+    p.rhs_mode = 0;
+    p.stage = k;
+    p.dt_fixed = dt;
+    p.f_dt_fixed = (float)dt;
+    p.slot_in = k;
+    p.alpha_rec = alpha_out;
+    e = stage(c, p);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slab stage launch");
+    return T7_OK;
+}
+
 // Steps per t7_run chunk, and the size up to which a chunk runs as one CUDA
 // graph (below it a stage launch lasts a few microseconds and launch overhead
 // dominates; above it the 3 launches per step cost nothing measurable).

@@ -51,11 +51,22 @@ struct Stage1D {
     double *alpha_rec;  // nullable: receives alpha of the output state (RK mode)
     int tile_lo, tile_hi;  // warp tiles [tile_lo, tile_hi) of the domain (29 cells each; tile_hi <= 0: all)
     int partial;           // RK mode: one part of a stage split over several launches, not its last
+    // Slab of a decomposed domain: Us, U0 and out are padded by HALO_CELLS
+    // cells per side (row stride n + 2 HALO_CELLS, cell 0 at offset
+    // HALO_CELLS); the stencils read the padding, which the caller has
+    // filled, instead of applying the boundary condition
+    int halo;
+    const double *alpha_in;  // nullable: alpha of Us from this device value instead of the control block
 };
+
+// Ghost cells per side of a slab (the stencil reach of the scheme, Eq. app:
+// the RHS at cell i depends on cells i-4 .. i+4).
+constexpr int HALO_CELLS = 4;
 
 struct Alpha1D {
     const void *U;
     int n, sys;
+    int stride;  // between conserved variables (0: n)
     double gamma, a;
     DevCtl *ctl;
     int slot;

@@ -1,24 +1,30 @@
-"""Slab decompositions of the 1D and 2D schemes over ranks (torch.distributed),
-tube sharding for ragged batches, and FP64 domain sums.
+"""Slab decompositions of the 1D and 2D schemes, tube sharding for ragged
+batches, and FP64 domain sums.
 
-Rank r owns the contiguous cells [lo_r, hi_r) of a 1D domain.  Every RHS
-evaluation needs, per side, a halo of HALO = 4 cells and the global
-Lax-Friedrichs alpha: the RHS at cell i reads faces i-1/2 and i+1/2, whose
-polynomials reach cells i-4 .. i+4 and whose neighbour-face cutoff bits are
-computed from windows inside the same range.  So one SSP-RK3 stage is
+A domain of N cells (2D: N rows, split along y so rows stay contiguous) is cut
+into contiguous slabs, one per rank -- or, on one GPU, one per CUDA stream.
+Every RHS evaluation of a slab needs, per side, a halo of HALO = 4 cells
+(rows) and the global Lax-Friedrichs alpha: the RHS at cell i reads faces
+i-1/2 and i+1/2, whose polynomials reach cells i-4 .. i+4 and whose
+neighbour-face cutoff bits are computed from windows inside the same range
+(Eq. app, Eq. vec).  So one SSP-RK3 stage is
 
-    exchange 4-cell halos  ->  all-reduce(max) of the local alphas
-    ->  RHS of the padded slab (inner cells only)  ->  RK combination,
+    fill the 4-cell halos  ->  stage kernel on the padded slab
+    ->  all-reduce(max) of the slabs' alphas of the stage output,
 
-and each step starts with an all-reduce(max) for the CFL step.  The domain's
-own boundaries (periodic or zero-gradient) become halos from the periodic
-neighbour or copies of the edge cell.  These are the only exchanges: the path
-has no other collective.
+and the step's CFL step comes from the all-reduced alpha of U^n.  The
+domain's own boundaries (periodic or zero-gradient) become halos from the
+periodic neighbour or copies of the edge cell.  These are the only
+exchanges: the path has no other collective.
 
-The per-rank RHS is a callable ``rhs(U_padded, alpha) -> L(U) on the padded
-slab`` so the same exchange logic drives any implementation; the CPU tests
-run it with the oracle on gloo ranks and require bit-identical results to
-the unsplit run.
+Each slab keeps its three RK states (U^n and the two stage states) as arrays
+padded by HALO cells (rows) on each side of axis 1, so the stage kernel reads
+its halos in place.  A slab's ``backend`` does the arithmetic:
+``alpha(P, out)`` (local max wave speed into a one-element float64 tensor)
+and ``stage(k, Us, U0, out, alpha, dt, alpha_out)`` (one Shu-Osher stage).
+``CudaSlab1D`` wraps the library's t7_slab_* entry points, so the RK stages,
+the wave-speed reductions and the alpha values never leave the GPU; only dt
+(one double per step) is read on the host.
 """
 from __future__ import annotations
 
@@ -34,57 +40,217 @@ def partition(n: int, world: int, rank: int) -> tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
-def exchange_halos(U, periodic: bool):
-    """U: [m, n_local] numpy (1D), or [4, ny_local, nx] (2D, split along y).
-    Returns the array padded by HALO cells (rows) on each side of axis 1, the
-    halos coming from the neighbouring ranks (or from the domain boundary
-    condition at the ends: periodic wrap, or copies of the edge cell/row)."""
+def padded(U_local):
+    """U_local [m, n] (or [4, ny, nx]) as a tensor padded by HALO cells (rows)
+    on each side of axis 1, halos zero."""
     import torch
-    import torch.distributed as dist
 
-    world, rank = dist.get_world_size(), dist.get_rank()
-    n = U.shape[1]
-    if n < HALO:
-        raise ValueError("each rank needs at least 4 cells (rows)")
-    left_n = (rank - 1) % world if (periodic or rank > 0) else None
-    right_n = (rank + 1) % world if (periodic or rank < world - 1) else None
-    send_l = torch.from_numpy(np.ascontiguousarray(U[:, :HALO]))
-    send_r = torch.from_numpy(np.ascontiguousarray(U[:, -HALO:]))
-    recv_l = torch.empty(send_l.shape, dtype=torch.float64)
-    recv_r = torch.empty(send_r.shape, dtype=torch.float64)
-    reqs = []
-    if world > 1:
-        # tags by direction: with two ranks (periodic) both neighbours are the
-        # same rank, and the two messages must not be confused
-        LEFTWARD, RIGHTWARD = 1, 2
-        if left_n is not None:
-            reqs.append(dist.isend(send_l, left_n, tag=LEFTWARD))
-            reqs.append(dist.irecv(recv_l, left_n, tag=RIGHTWARD))
-        if right_n is not None:
-            reqs.append(dist.isend(send_r, right_n, tag=RIGHTWARD))
-            reqs.append(dist.irecv(recv_r, right_n, tag=LEFTWARD))
-        for r in reqs:
-            r.wait()
-    else:
-        if periodic:
-            recv_l, recv_r = send_r.clone(), send_l.clone()
-    shape = list(U.shape)
-    shape[1] = n + 2 * HALO
-    P = np.empty(shape)
-    P[:, HALO:HALO + n] = U
-    P[:, :HALO] = recv_l.numpy() if left_n is not None else U[:, :1]
-    P[:, HALO + n:] = recv_r.numpy() if right_n is not None else U[:, -1:]
+    t = U_local if isinstance(U_local, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(U_local))
+    shape = list(t.shape)
+    shape[1] += 2 * HALO
+    P = torch.zeros(shape, dtype=t.dtype, device=t.device)
+    P[:, HALO:-HALO] = t
     return P
 
 
-def allreduce_max(x):
-    """Max over ranks of a float, or element-wise of a tuple of floats."""
-    import torch
-    import torch.distributed as dist
+def interior(P):
+    return P[:, HALO:-HALO]
 
-    t = torch.tensor(np.atleast_1d(np.asarray(x, np.float64)))
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t[0]) if np.ndim(x) == 0 else tuple(float(v) for v in t)
+
+class CudaSlab1D:
+    """A slab backend on the CUDA library: one context per slab (nx = the
+    slab's cells), t7_slab_alpha / t7_slab_stage on padded tensors."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.stream = ctx.stream
+
+    def alpha(self, P, out):
+        self.ctx.slab_alpha(P, out)
+
+    def stage(self, k, Us, U0, out, alpha, dt, alpha_out):
+        self.ctx.slab_stage(k, Us, U0, out, alpha, dt, alpha_out)
+
+
+class Slab:
+    """One slab: its backend, its three padded RK states and its local alphas."""
+
+    def __init__(self, backend, U_local, nalpha: int = 1):
+        import torch
+
+        self.backend = backend
+        self.stream = getattr(backend, "stream", None)
+        self.P = [padded(U_local)]
+        self.P += [torch.zeros_like(self.P[0]) for _ in range(2)]
+        self.a = [torch.zeros(nalpha, dtype=torch.float64, device=self.P[0].device) for _ in range(3)]
+
+    def state(self):
+        return interior(self.P[0])
+
+
+class LocalSlabs:
+    """Every slab of the domain in this process, in domain order (one GPU,
+    one CUDA stream per slab, or CPU tensors): halos are device-local copies
+    and the all-reduce is a max over the slabs' values.  Work on the slabs'
+    streams is ordered through the current stream at each all-reduce."""
+
+    def __init__(self, slabs, periodic: bool):
+        self.slabs = slabs
+        self.periodic = periodic
+
+    def _streams(self):
+        return [s.stream for s in self.slabs if s.stream is not None]
+
+    def fill_halos(self, k: int):
+        import torch
+
+        n = len(self.slabs)
+        for i, s in enumerate(self.slabs):
+            P = s.P[k]
+            left = self.slabs[i - 1].P[k] if (i > 0 or self.periodic) else None
+            right = self.slabs[(i + 1) % n].P[k] if (i < n - 1 or self.periodic) else None
+            ctx = torch.cuda.stream(s.stream) if s.stream is not None else _null()
+            with ctx:
+                if s.stream is not None:
+                    for j in (i - 1, (i + 1) % n):
+                        if self.slabs[j].stream is not None and j != i:
+                            s.stream.wait_stream(self.slabs[j].stream)
+                P[:, :HALO].copy_(left[:, -2 * HALO:-HALO] if left is not None else
+                                  P[:, HALO:HALO + 1].expand_as(P[:, :HALO]))
+                P[:, -HALO:].copy_(right[:, HALO:2 * HALO] if right is not None else
+                                   P[:, -HALO - 1:-HALO].expand_as(P[:, -HALO:]))
+
+    def allreduce_max(self, k: int, out):
+        """out <- max over the slabs of their alpha slot k; every slab's stream
+        then waits for it."""
+        import torch
+
+        streams = self._streams()
+        cur = torch.cuda.current_stream() if streams else None
+        for st in streams:
+            cur.wait_stream(st)
+        torch.amax(torch.stack([s.a[k] for s in self.slabs]), dim=0, out=out)
+        for st in streams:
+            st.wait_stream(cur)
+        return out
+
+
+class RankSlabs:
+    """One slab per rank over torch.distributed (NCCL for CUDA tensors, gloo
+    for CPU ones): halos travel by point-to-point messages in two phases
+    (rightward, then leftward, so that with two periodic ranks the two
+    messages between the same pair never cross), the alphas by all-reduce(max)."""
+
+    def __init__(self, slab, periodic: bool):
+        import torch.distributed as dist
+
+        self.slabs = [slab]
+        self.periodic = periodic
+        self.world, self.rank = dist.get_world_size(), dist.get_rank()
+
+    def fill_halos(self, k: int):
+        import torch
+        import torch.distributed as dist
+
+        P = self.slabs[0].P[k]
+        world, rank = self.world, self.rank
+        if P.shape[1] < 3 * HALO:
+            raise ValueError("each rank needs at least 4 cells (rows)")
+        left = (rank - 1) % world if (self.periodic or rank > 0) else None
+        right = (rank + 1) % world if (self.periodic or rank < world - 1) else None
+        if world == 1:
+            if self.periodic:
+                P[:, :HALO].copy_(P[:, -2 * HALO:-HALO])
+                P[:, -HALO:].copy_(P[:, HALO:2 * HALO])
+        else:
+            RIGHTWARD, LEFTWARD = 1, 2
+            for direction in (RIGHTWARD, LEFTWARD):
+                src = right if direction == LEFTWARD else left    # who sends to me in this phase
+                dst = right if direction == RIGHTWARD else left   # whom I send to
+                ops = []
+                if dst is not None:
+                    edge = P[:, -2 * HALO:-HALO] if direction == RIGHTWARD else P[:, HALO:2 * HALO]
+                    ops.append(dist.P2POp(dist.isend, edge.contiguous(), dst, tag=direction))
+                recv = None
+                if src is not None:
+                    recv = torch.empty_like(P[:, :HALO]).contiguous()
+                    ops.append(dist.P2POp(dist.irecv, recv, src, tag=direction))
+                if ops:
+                    for r in dist.batch_isend_irecv(ops):
+                        r.wait()
+                if recv is not None:
+                    (P[:, :HALO] if direction == RIGHTWARD else P[:, -HALO:]).copy_(recv)
+        if left is None:
+            P[:, :HALO].copy_(P[:, HALO:HALO + 1].expand_as(P[:, :HALO]))
+        if right is None:
+            P[:, -HALO:].copy_(P[:, -HALO - 1:-HALO].expand_as(P[:, -HALO:]))
+
+    def allreduce_max(self, k: int, out):
+        import torch.distributed as dist
+
+        out.copy_(self.slabs[0].a[k])
+        dist.all_reduce(out, op=dist.ReduceOp.MAX)
+        return out
+
+
+class _null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def cfl_dt_1d(dx: float, cfl: float):
+    """dt of the 1D CFL condition, in the expression order of the unsplit run."""
+    return lambda a: (cfl * dx) / float(a[0])
+
+
+def cfl_dt_2d(dx: float, dy: float, cfl: float):
+    """dt of the 2D CFL condition cfl / (ax/dx + ay/dy)."""
+    return lambda a: cfl / (float(a[0]) / dx + float(a[1]) / dy)
+
+
+def rk3_run_slabs(comm, dt_of_alpha, *, t_end: float, max_steps: int):
+    """March every slab of `comm` with the SSP-RK3 scheme (Shu-Osher form):
+
+        U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U = 1/3 U + 2/3 (U2 + dt L(U2)),
+
+    each stage one backend call per slab after its halos are filled, each L
+    with the all-reduced alpha of its input.  dt = dt_of_alpha(alpha(U^n)),
+    the last step clipped to land on t_end.  Returns (steps, t); every slab
+    takes the same steps and dt."""
+    import torch
+
+    slabs = comm.slabs
+    dev = slabs[0].P[0].device
+    g = [torch.zeros_like(slabs[0].a[0]) for _ in range(3)]  # all-reduced alphas
+    for s in slabs:
+        with (torch.cuda.stream(s.stream) if s.stream is not None else _null()):
+            s.backend.alpha(s.P[0], s.a[0])
+    t, steps = 0.0, 0
+    while steps < max_steps and t < t_end:
+        comm.allreduce_max(0, g[0])
+        dt = dt_of_alpha(g[0].cpu() if dev.type == "cuda" else g[0])
+        if t + dt > t_end:
+            dt = t_end - t
+        for k in range(3):
+            comm.fill_halos(k)
+            for s in slabs:
+                Us, U0 = s.P[k], s.P[0]
+                out = s.P[k + 1] if k < 2 else s.P[0]
+                with (torch.cuda.stream(s.stream) if s.stream is not None else _null()):
+                    s.backend.stage(k, Us, None if k == 0 else U0, out, g[k], dt, s.a[(k + 1) % 3])
+            if k < 2:
+                comm.allreduce_max(k + 1, g[k + 1])
+        t = t + dt
+        steps += 1
+    if any(s.stream is not None for s in slabs):
+        cur = torch.cuda.current_stream()
+        for s in slabs:
+            if s.stream is not None:
+                cur.wait_stream(s.stream)
+    return steps, t
 
 
 def global_sums(U_local):
@@ -114,57 +280,3 @@ def shard_tubes(costs, world: int):
         loads[r] += costs[t]
     return out
 
-
-def rk3_run(U_local, rhs, alpha_local, *, dx: float, cfl: float, t_end: float, max_steps: int, periodic: bool):
-    """March the local slab with the SSP-RK3 scheme, exchanging halos and the
-    global alpha at every stage.  rhs(P, alpha) -> L on the padded slab P;
-    alpha_local(U) -> max characteristic speed of the rank's cells.  Returns
-    (U_local, steps, t); every rank takes the same steps and dt."""
-    def L(U, alpha):
-        return rhs(exchange_halos(U, periodic), alpha)[:, HALO:-HALO]
-
-    U = np.array(U_local, dtype=np.float64)
-    t, steps = 0.0, 0
-    while steps < max_steps and t < t_end:
-        a0 = allreduce_max(alpha_local(U))
-        dt = (cfl * dx) / a0
-        if t + dt > t_end:
-            dt = t_end - t
-        U0 = U.copy()
-        U1 = U0 + dt * L(U0, a0)
-        a1 = allreduce_max(alpha_local(U1))
-        U2 = 0.75 * U0 + 0.25 * (U1 + dt * L(U1, a1))
-        a2 = allreduce_max(alpha_local(U2))
-        U = (1.0 / 3.0) * U0 + (2.0 / 3.0) * (U2 + dt * L(U2, a2))
-        t = t + dt
-        steps += 1
-    return U, steps, t
-
-
-def rk3_run_2d(U_local, rhs, alpha_local, *, dx: float, dy: float, cfl: float, t_end: float, max_steps: int,
-               periodic_y: bool):
-    """2D slab decomposition along y (rows stay contiguous): U_local
-    [4, ny_local, nx].  rhs(P, (ax, ay)) -> L on the padded slab P (4 halo rows
-    per side; x boundaries inside the rank); alpha_local(U) -> (ax, ay) of the
-    rank's cells.  Per stage: halo-row exchange and all-reduce(max) of both
-    alphas; per step the CFL step cfl / (ax/dx + ay/dy).  Returns
-    (U_local, steps, t)."""
-    def L(U, a):
-        return rhs(exchange_halos(U, periodic_y), a)[:, HALO:-HALO]
-
-    U = np.array(U_local, dtype=np.float64)
-    t, steps = 0.0, 0
-    while steps < max_steps and t < t_end:
-        a0 = allreduce_max(alpha_local(U))
-        dt = cfl / (a0[0] / dx + a0[1] / dy)
-        if t + dt > t_end:
-            dt = t_end - t
-        U0 = U.copy()
-        U1 = U0 + dt * L(U0, a0)
-        a1 = allreduce_max(alpha_local(U1))
-        U2 = 0.75 * U0 + 0.25 * (U1 + dt * L(U1, a1))
-        a2 = allreduce_max(alpha_local(U2))
-        U = (1.0 / 3.0) * U0 + (2.0 / 3.0) * (U2 + dt * L(U2, a2))
-        t = t + dt
-        steps += 1
-    return U, steps, t

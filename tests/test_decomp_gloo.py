@@ -1,9 +1,11 @@
-"""Multi-rank path on CPU: the slab decomposition (4-cell halo exchange and
-all-reduce(max) of alpha per RK stage, all-reduce of the CFL step) with gloo
-ranks, each rank computing its padded slab's RHS with the oracle.  The
-gathered result must be bit-identical to the unsplit oracle run, which pins
-the halo width, the boundary handling at the domain ends and the
-synchronisation of alpha and dt."""
+"""Multi-rank path on CPU: the slab decomposition of paper_1808_00037_gb300.decomp
+(4-cell halo exchange and all-reduce(max) of alpha per RK stage, the CFL step
+from the all-reduced alpha) on gloo ranks -- and, in one process, over
+several slabs -- each slab's stages computed by the oracle backend of
+tests/slab_backends.py.  The gathered result must be bit-identical to the
+unsplit oracle run, which pins the halo width, the boundary handling at the
+domain ends and the synchronisation of alpha and dt.  The GPU counterpart
+(the CUDA slab stages) is tests/test_gpu_slabs.py."""
 import socket
 
 import numpy as np
@@ -14,6 +16,7 @@ import torch.multiprocessing as mp
 import oracle
 from paper_1808_00037_gb300 import decomp
 from paper_1808_00037_gb300 import inputs as I
+from slab_backends import OracleSlab1D, OracleSlab2D
 
 
 def _free_port():
@@ -41,17 +44,11 @@ def _worker(rank, world, port, name):
         U, dx, periodic, t_end, max_steps = _case(name)
         bc = (0, 0) if periodic else (1, 1)
         lo, hi = decomp.partition(U.shape[1], world, rank)
-
-        def rhs(P, alpha):
-            return oracle.rhs_1d(oracle.SYS_EULER1D, P, dx, bc=(1, 1), alpha=alpha)[0]
-
-        def alpha_local(X):
-            return oracle.alpha_1d(oracle.SYS_EULER1D, X)
-
-        Ul, steps, t = decomp.rk3_run(U[:, lo:hi], rhs, alpha_local, dx=dx, cfl=0.5, t_end=t_end,
-                                      max_steps=max_steps, periodic=periodic)
+        slab = decomp.Slab(OracleSlab1D(oracle.SYS_EULER1D, dx), U[:, lo:hi])
+        steps, t = decomp.rk3_run_slabs(decomp.RankSlabs(slab, periodic), decomp.cfl_dt_1d(dx, 0.5),
+                                        t_end=t_end, max_steps=max_steps)
         parts = [None] * world
-        dist.all_gather_object(parts, (lo, hi, Ul, steps, t))
+        dist.all_gather_object(parts, (lo, hi, slab.state().numpy().copy(), steps, t))
         if rank == 0:
             Uo, so, to, st = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=t_end, cfl=0.5, bc=bc,
                                            max_steps=max_steps)
@@ -66,6 +63,24 @@ def _worker(rank, world, port, name):
 @pytest.mark.parametrize("name", ["sod", "shu-osher", "smooth-periodic"])
 def test_slab_decomposition_bit_identical(world, name):
     mp.spawn(_worker, args=(world, _free_port(), name), nprocs=world, join=True)
+
+
+@pytest.mark.parametrize("nslabs", [1, 2, 3])
+@pytest.mark.parametrize("name", ["sod", "smooth-periodic"])
+def test_local_slabs_bit_identical(nslabs, name):
+    """All slabs in one process (the one-GPU layout, here on CPU tensors): the
+    same orchestration with device-local halo copies and a max over the slabs
+    as the all-reduce; bit-identical to the unsplit oracle run."""
+    U, dx, periodic, t_end, max_steps = _case(name)
+    bc = (0, 0) if periodic else (1, 1)
+    slabs = [decomp.Slab(OracleSlab1D(oracle.SYS_EULER1D, dx), U[:, lo:hi])
+             for lo, hi in (decomp.partition(U.shape[1], nslabs, r) for r in range(nslabs))]
+    steps, t = decomp.rk3_run_slabs(decomp.LocalSlabs(slabs, periodic), decomp.cfl_dt_1d(dx, 0.5),
+                                    t_end=min(t_end, 0.02), max_steps=min(max_steps, 12))
+    Uo, so, to, _ = oracle.run_1d(oracle.SYS_EULER1D, U, dx, t_end=min(t_end, 0.02), cfl=0.5, bc=bc,
+                                  max_steps=min(max_steps, 12))
+    assert (steps, t) == (so, to)
+    assert np.array_equal(np.concatenate([s.state().numpy() for s in slabs], axis=1), Uo)
 
 
 def test_partition_covers_domain():
@@ -94,12 +109,10 @@ def _worker2d(rank, world, port, name):
         U, dx, dy, periodic, nsteps = _case2d(name)
         bcx = (0, 0) if periodic else (1, 1)
         lo, hi = decomp.partition(U.shape[1], world, rank)
-
-        def rhs(P, alpha):
-            return oracle.rhs_2d(P, dx, dy, bc=(bcx[0], bcx[1], 1, 1), alpha=alpha)[0]
-
-        Ul, steps, t = decomp.rk3_run_2d(U[:, lo:hi], rhs, oracle.alpha_2d, dx=dx, dy=dy, cfl=0.4,
-                                         t_end=np.inf, max_steps=nsteps, periodic_y=periodic)
+        slab = decomp.Slab(OracleSlab2D(dx, dy, bcx), U[:, lo:hi], nalpha=2)
+        steps, t = decomp.rk3_run_slabs(decomp.RankSlabs(slab, periodic), decomp.cfl_dt_2d(dx, dy, 0.4),
+                                        t_end=np.inf, max_steps=nsteps)
+        Ul = slab.state().numpy().copy()
         sums = decomp.global_sums(Ul)
         parts = [None] * world
         dist.all_gather_object(parts, (lo, Ul, steps, t))
