@@ -39,16 +39,24 @@ TILES = 10486
 N1 = 1600
 CFL = 0.5
 GAMMA = 1.4
-# ALU peaks from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
-# lanes x 2 flop per FMA x 2.07 GHz; FP64 is GB300's nominal 1.25 TFLOP/s.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# Nominal ALU peaks, for context only: 152 SMs x 128 FP32 lanes x 2 flop per
+# FMA x 2.07 GHz, and GB300's nominal FP64 rate.  The roofline divides by the
+# rates the library's FMA probe measures on the device (t7_probe_fma).
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_NOMINAL_TFLOPS = 1.25
 # Algorithmic floating-point operations per cell per stage launch of the fused
 # 1D-Euler stage kernel (FMA = 2, add/mul/divide/rcp/sqrt/compare = 1), counted
-# from the kernel's arithmetic without the warp-tile redundancy:
+# from the kernel's arithmetic without the warp-tile redundancy and with the
+# cutoff evaluated in full:
 #   FP32: 31 per-cell staging + 751 per face + 26 update = 808
 #   FP64: 30 per-cell staging + 718 per face + 28 update = 776 (no FMA)
 FLOPS_PER_CELL_STAGE = {"f32": 808.0, "f64": 776.0}
+# Executed floating-point operations per cell per stage launch, from ncu's
+# per-opcode thread counters of one launch on the same workload (FMA = 2,
+# packed f32x2 FMA = 4, packed add/mul = 2, scalar add/mul = 1; the keep-all
+# shortcut skips most of the cutoff, so this is below the algorithmic count);
+# None when not captured for the current kernel.
+EXEC_FLOPS_PER_CELL_STAGE = {"f32": None, "f64": None}
 # DRAM bytes per stage launch per cell measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, averaged over the three stage launches of one RK3
 # step at N = 16,777,600) for the current kernels; None when not captured.
@@ -445,6 +453,138 @@ def bench_advection(args, torch, B, dist, world):
     return out
 
 
+def alu_peaks(B):
+    """FP32 and FP64 FMA rates measured on this device by the library's probe
+    (t7_probe_fma: every SM full of independent FMA chains); the FP32
+    denominator is the faster of the scalar and the packed f32x2 form."""
+    f32, _ = B.probe_fma(B.T7_PROBE_F32, iters=2048, repeats=5)
+    f32x2, _ = B.probe_fma(B.T7_PROBE_F32X2, iters=2048, repeats=5)
+    f64, _ = B.probe_fma(B.T7_PROBE_F64, iters=256, repeats=5)
+    return {"f32": max(f32, f32x2), "f64": f64, "f32_scalar": f32, "f32x2": f32x2,
+            "kind": "measured: t7_probe_fma FMA-chain probe (f32: max of scalar and f32x2)"}
+
+
+def _rel_l1(a, b):
+    return float((a.double() - b.double()).abs().sum() / b.double().abs().sum())
+
+
+def _flips(ma, mb):
+    if isinstance(ma, tuple):
+        d = sum(int((x != y).sum()) for x, y in zip(ma, mb))
+        return d / sum(x.numel() for x in ma)
+    return float((ma != mb).double().mean())
+
+
+def _trajectory(torch, B, make, U0, cfl, t_end, nchk, lo_prec):
+    """The same problem run in FP64 and in lo_prec (FP32 or mixed) side by
+    side to t_end in nchk equal chunks.  At each chunk end: the fraction of
+    Delta masks that differ with each precision evaluating its own state
+    (trajectory), and with the low precision evaluating the FP64 state (same
+    state); at the end the relative L1 error of every variable against FP64."""
+    c64, clo = make(B.T7_F64), make(lo_prec)
+    lo_dtype = torch.float32 if lo_prec == B.T7_F32 else torch.float64
+    U64 = torch.tensor(U0, dtype=torch.float64, device="cuda")
+    Ulo = torch.tensor(U0, dtype=lo_dtype, device="cuda")
+    traj, same = [], []
+    for k in range(nchk):
+        c64.run(U64, cfl, t_end=t_end / nchk)
+        clo.run(Ulo, cfl, t_end=t_end / nchk)
+        m64 = c64.euler_rhs(U64, want_masks=True)[1]
+        traj.append(_flips(m64, clo.euler_rhs(Ulo, want_masks=True)[1]))
+        same.append(_flips(m64, clo.euler_rhs(U64.to(lo_dtype), want_masks=True)[1]))
+    out = {"rel_l1_vs_f64": _rel_l1(Ulo, U64), "mask_flip_trajectory": traj, "mask_flip_same_state": same,
+           "checkpoints": nchk}
+    c64.close()
+    clo.close()
+    return out
+
+
+def bench_accuracy(args, torch, B):
+    """Accuracy of the reduced-precision forms against the FP64 path on the
+    configurations' smooth and shock cases: relative L1 error (the smooth
+    gate is 1e-5) and mask-flip fractions along the trajectory."""
+    out = {}
+    Us, dxs, _ = I.random_euler_smooth(9, N1)
+    Ua, dxa = I.shu_osher(N1)
+
+    def mk1(U, dx, bc):
+        return lambda prec: B.Context(B.T7_EULER1D, U.shape[1], dx, prec=prec, bc=bc, gamma=GAMMA)
+    for form, prec in (("f32", B.T7_F32), ("mixed", B.T7_MIXED)):
+        out[f"euler1d_{form}"] = {
+            "smooth": {"case": f"random smooth periodic Euler, N={N1}, t=0.25",
+                       **_trajectory(torch, B, mk1(Us, dxs, (0, 0, 0, 0)), Us, CFL, 0.25, 5, prec)},
+            "shock": {"case": f"Shu-Osher N={N1}, t=1.8",
+                      **_trajectory(torch, B, mk1(Ua, dxa, (1, 1, 0, 0)), Ua, CFL, 1.8, 6, prec)}}
+    n2 = 256
+    U2s, dx2s, dy2s = I.random_smooth_2d(4, n2, n2)
+    U2q, dx2q, dy2q, _ = I.quadrants_2d(2024, n2, n2)
+
+    def mk2(dx, dy, bc):
+        return lambda prec: B.Context(B.T7_EULER2D, n2, dx, ny=n2, dy=dy, prec=prec, bc=bc, gamma=GAMMA)
+    for form, prec in (("f32", B.T7_F32), ("mixed", B.T7_MIXED)):
+        out[f"euler2d_{form}"] = {
+            "smooth": {"case": f"random smooth periodic 2D Euler, {n2}^2, t=0.05",
+                       **_trajectory(torch, B, mk2(dx2s, dy2s, (0, 0, 0, 0)), U2s, 0.4, 0.05, 4, prec)},
+            "shock": {"case": f"four-quadrant Riemann data, {n2}^2, t=0.1",
+                      **_trajectory(torch, B, mk2(dx2q, dy2q, (1, 1, 1, 1)), U2q, 0.4, 0.1, 4, prec)}}
+    # ragged batch: the first 32 tubes of the batch recipe to t = 0.1 in FP32 and FP64
+    Ub, off, dxb, _ = I.riemann_tube_batch(7, 32, 256, 8192)
+    res = {}
+    for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
+        c = B.Context(B.T7_EULER1D, Ub.shape[1], 1.0, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
+        Ug = torch.tensor(Ub, dtype=dtype, device="cuda")
+        c.batch_run(Ug, off, dxb, 0.1, 0.5)
+        res[name] = Ug
+        c.close()
+    flips = []
+    for t in range(0, 32, 4):
+        a, b = off[t], off[t + 1]
+        cs = [B.Context(B.T7_EULER1D, b - a, dxb[t], prec=p, bc=(1, 1, 0, 0), gamma=GAMMA)
+              for p in (B.T7_F64, B.T7_F32)]
+        m64 = cs[0].euler_rhs(res["f64"][:, a:b].contiguous(), want_masks=True)[1]
+        m32 = cs[1].euler_rhs(res["f32"][:, a:b].contiguous(), want_masks=True)[1]
+        flips.append(_flips(m64, m32))
+        for c in cs:
+            c.close()
+    out["batch_f32"] = {"case": "first 32 tubes of the 4096-tube recipe (seed 7), t=0.1",
+                        "rel_l1_vs_f64": _rel_l1(res["f32"], res["f64"]),
+                        "mask_flip_end_state": float(np.mean(flips)), "tubes_for_masks": 8}
+    gate = 1e-5
+    out["smooth_gate"] = {"limit": gate, "pass": all(
+        out[k]["smooth"]["rel_l1_vs_f64"] <= gate for k in out if "smooth" in out[k])}
+    return out
+
+
+def bench_strong(args, torch, B, U0, dx, dist, world, rank):
+    """Strong scaling: the one tiled Shu-Osher domain split into `world` slabs,
+    one per rank, each advanced by the CUDA slab stages with 4-cell halos
+    exchanged by NCCL point-to-point messages and the alpha of every stage
+    all-reduced (max) on the device (paper_1808_00037_gb300.decomp).  FP32,
+    CFL steps as in the primary line."""
+    from paper_1808_00037_gb300 import decomp
+    lo, hi = decomp.partition(U0.shape[1], world, rank)
+    ctx = B.Context(B.T7_EULER1D, hi - lo, dx, prec=B.T7_F32, gamma=GAMMA)
+    slab = decomp.Slab(decomp.CudaSlab1D(ctx), torch.tensor(U0[:, lo:hi], dtype=torch.float32, device="cuda"))
+    comm = decomp.RankSlabs(slab, periodic=False)
+    dt_of = decomp.cfl_dt_1d(dx, CFL)
+    decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, _ = decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    t = torch.tensor([el], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el = float(t.item())
+    ctx.close()
+    return {"value": U0.shape[1] * steps / el / 1e9, "unit": "Gcell-steps/s", "ms_per_step": el / steps * 1e3,
+            "steps": steps, "scaling": "strong", "cells_total": int(U0.shape[1]),
+            "timing": "host wall clock between barriers and device synchronisations (max over ranks)",
+            "parallelism": f"slab decomposition over {world} ranks, NCCL halos + all-reduce(max) of alpha"}
+
+
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
     stream = ctx.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -489,12 +629,23 @@ def main():
     ap.add_argument("--no-teno5", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-advection", action="store_true")
+    ap.add_argument("--no-strong", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
     ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint", "advection"], default=None,
                     help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: re-run this command under torchrun
+        import socket
+        sock = socket.socket()
+        sock.bind(("127.0.0.1", 0))
+        port = sock.getsockname()[1]
+        sock.close()
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", str(args.gpus),
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        return subprocess.call(cmd)
     world, rank, local = dist_setup(args.gpus)
 
     if args.impl == "reference":
@@ -526,6 +677,7 @@ def main():
     U0, dx = I.shu_osher(N1, tiles=args.tiles)
     n = U0.shape[1]
     hbm_peak, peak_kind = peaks()
+    alu = alu_peaks(B)
     res = {}
     for name, prec, dtype in (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64)):
         if args.only and name != args.only:
@@ -546,16 +698,21 @@ def main():
         achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
         flops = FLOPS_PER_CELL_STAGE[name] * n
         tflops = flops / (stage_ms * 1e-3) / 1e12
-        peak_alu = FP32_PEAK_TFLOPS if name == "f32" else FP64_PEAK_TFLOPS
+        peak_alu = alu[name]
         tr = TRAFFIC_PER_CELL_LAUNCH[name]
+        ex = EXEC_FLOPS_PER_CELL_STAGE[name]
+        ex_tflops = None if ex is None else ex * n / (stage_ms * 1e-3) / 1e12
         res[name] = {
             "value": n * steps * world / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps, "steps": steps,
             "clocks": clocks, "gpu_launches": launches + 2, "stage_launch_ms": stage_ms,
             "roofline": {"bound": "alu", "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
                          "frac": tflops / peak_alu, "traffic": None if tr is None else tr * n,
                          "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[name],
-                         "peak_kind": "derived from unit counts and max SM clock" if name == "f32"
-                         else "nominal GB300 FP64 rate"},
+                         "flops_kind": "algorithmic (cutoff counted in full)",
+                         "executed": {"flops_per_cell_stage": ex, "achieved": ex_tflops,
+                                      "frac": None if ex is None else ex_tflops / peak_alu},
+                         "peak_kind": alu["kind"],
+                         "nominal_peak": FP32_NOMINAL_TFLOPS if name == "f32" else FP64_NOMINAL_TFLOPS},
             "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                     "peak_kind": peak_kind, "bytes_per_cell_step": 8 * 3 * s,
                     "traffic": None if tr is None else tr * n},
@@ -594,28 +751,10 @@ def main():
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
     resa = None if (args.no_adjoint or rank != 0) else bench_adjoint(args, torch, B)
     # accuracy at the quoted configuration: 1600 cells to t = 1.8, FP32 vs FP64
-    acc = {}
-    Ua, dxa = I.shu_osher(N1)
-    outs = {}
-    for name, prec, dtype in (() if args.no_accuracy else
-                              (("f32", B.T7_F32, torch.float32), ("f64", B.T7_F64, torch.float64),
-                               ("mixed", B.T7_MIXED, torch.float64))):
-        c = B.Context(B.T7_EULER1D, N1, dxa, prec=prec, bc=(1, 1, 0, 0), gamma=GAMMA)
-        Ug = torch.tensor(Ua, dtype=dtype, device="cuda")
-        c.run(Ug, CFL, t_end=1.8)
-        outs[name] = (c, Ug)
-    if outs:
-        f32 = outs["f32"][1].double().cpu().numpy()
-        f64 = outs["f64"][1].double().cpu().numpy()
-        acc["f32_vs_f64_rel_l1_rho"] = float(np.abs(f32[0] - f64[0]).sum() / np.abs(f64[0]).sum())
-        mix = outs["mixed"][1].cpu().numpy()
-        acc["mixed_vs_f64_rel_l1_rho"] = float(np.abs(mix[0] - f64[0]).sum() / np.abs(f64[0]).sum())
-        # stencil-selection flips: both precisions evaluate L(U) on the same FP64 end state
-        _, m64 = outs["f64"][0].euler_rhs(outs["f64"][1], want_masks=True)
-        _, m32 = outs["f32"][0].euler_rhs(outs["f64"][1].float(), want_masks=True)
-        torch.cuda.synchronize()
-        acc["mask_flip_fraction"] = float((m64 != m32).double().mean().item())
-        acc["case"] = "Shu-Osher N=1600, CFL 0.5, t=1.8"
+    # accuracy of the FP32 and mixed forms against FP64 (smooth and shock
+    # cases of every form), on rank 0
+    acc = None if (args.no_accuracy or rank != 0) else bench_accuracy(args, torch, B)
+    strong = None if (world == 1 or args.no_strong) else bench_strong(args, torch, B, U0, dx, dist, world, rank)
 
     if rank != 0:
         return 0
@@ -635,7 +774,8 @@ def main():
         "hbm_roofline": main_res["hbm"],
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
-        "f64": res["f64"], "mixed": resm, "teno5": res5, "advection": resv, "accuracy": acc, "euler2d": res2d, "batch": resb, "adjoint": resa,
+        "f64": res["f64"], "mixed": resm, "teno5": res5, "advection": resv, "accuracy": acc, "euler2d": res2d,
+        "batch": resb, "adjoint": resa, "strong": strong, "alu_peaks": alu,
         "cpu_baseline": cpu,
     }
     # compact FP64 figures at the end of the line, where a reader of its tail finds them

@@ -24,6 +24,7 @@ UNITS = {
     "teno7_f64.cu": ["-fmad=false"],
     "teno7_f32.cu": [],
     "teno7_static.cu": [],
+    "teno7_probe.cu": [],
 }
 
 
@@ -38,7 +39,7 @@ def _sources_newer_than(target: Path) -> bool:
     if not target.exists():
         return True
     t = target.stat().st_mtime
-    deps = list(CSRC.glob("*")) + [ROOT / "include" / "teno7.h", Path(__file__)]
+    deps = list(CSRC.glob("*")) + list((ROOT / "include").glob("*.h")) + [Path(__file__)]
     return any(p.stat().st_mtime > t for p in deps if p.is_file())
 
 

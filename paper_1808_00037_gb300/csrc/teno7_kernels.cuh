@@ -390,7 +390,8 @@ struct TileArgs {
     T *out;          // RK: stage output; RHS: dU/dt
     uint8_t *masks;  // RHS only, nullable: [2][m][n+1]
     int n;           // cells
-    size_t cs;       // stride between conserved variables
+    size_t cs;       // stride between conserved variables (Us, U0)
+    size_t cso;      // stride between conserved variables of out
     int bc_lo, bc_hi;
     double dx;
     float f_dx;
@@ -398,8 +399,17 @@ struct TileArgs {
     double dtD;      // FP64 step (mixed precision: FP64 state, FP32 reconstruction)
     int rhs_mode, stage;
     int ebase;       // added to cell/face indices in error reports
+    int halo;        // the arrays hold HALO_CELLS filled ghost cells per side (slab mode)
     DevCtl *ctl;
 };
+
+// Index of a staged cell l outside 0 .. n-1: the boundary condition, or in
+// slab mode the caller-filled padding (cells beyond it are never used by an
+// updated cell and are read clamped into it).
+__device__ __forceinline__ int ghost_or_halo(int l, int n, int bc_lo, int bc_hi, int halo) {
+    if (halo) return l < -HALO_CELLS ? -HALO_CELLS : (l > n + HALO_CELLS - 1 ? n + HALO_CELLS - 1 : l);
+    return ghost_map(l, n, bc_lo, bc_hi);
+}
 
 template <typename T, int SYS, int SCH = SCH_TENO7EXT>
 __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)[WC], T (*sgm)[WC], T (*spr)[WC],
@@ -423,7 +433,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
         // ---- stage cells c0-5 .. c0+33 -----------------------------------
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
-            if (gi < 0 || gi >= n) gi = ghost_map(gi, n, A.bc_lo, A.bc_hi);
+            if (gi < 0 || gi >= n) gi = ghost_or_halo(gi, n, A.bc_lo, A.bc_hi, A.halo);
             T U[M], F[M];
 #pragma unroll
             for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * cs + gi];
@@ -633,7 +643,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
             }
             if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * cs + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + i] = r[k];
             } else {
                 T o[M];
 #pragma unroll
@@ -653,7 +663,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                             o[k] = fmaf(2.0f / 3.0f, (us + dtT * r[k]) - u0, u0);
                         }
                     }
-                    out[(size_t)k * cs + i] = o[k];
+                    out[(size_t)k * A.cso + i] = o[k];
                 }
                 int wflag = 0;
                 wsmax = fmax(wsmax, wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag));
@@ -692,18 +702,22 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
 
     TileArgs<T> A;
     if constexpr (sizeof(T) == 8) {
-        A.alpha = __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
+        A.alpha = p.alpha_in ? *p.alpha_in : __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
         A.dtT = fixed ? p.dt_fixed : ctl->dt;
     } else {
-        A.alpha = ctl->alpha_f[p.slot_in][0];
+        A.alpha = p.alpha_in ? (float)*p.alpha_in : ctl->alpha_f[p.slot_in][0];
         A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
     }
-    A.Us = static_cast<const T *>(p.Us);
-    A.U0 = static_cast<const T *>(p.U0);
-    A.out = static_cast<T *>(p.out);
+    // slab mode: cell 0 follows the padding (the RHS output dU/dt is unpadded)
+    const int off = p.halo ? HALO_CELLS : 0, offo = p.rhs_mode ? 0 : off;
+    A.Us = static_cast<const T *>(p.Us) + off;
+    A.U0 = p.U0 ? static_cast<const T *>(p.U0) + off : nullptr;
+    A.out = static_cast<T *>(p.out) + offo;
     A.masks = p.masks;
     A.n = p.n;
-    A.cs = (size_t)p.n;
+    A.cs = (size_t)p.n + 2 * off;
+    A.cso = (size_t)p.n + 2 * offo;
+    A.halo = p.halo;
     A.bc_lo = p.bc_lo;
     A.bc_hi = p.bc_hi;
     A.dx = p.dx;
@@ -776,6 +790,19 @@ constexpr float RO_FLOOR4 = RO_FLOOR12 / 3.f;           // the same floor for 4 
 // leaves gamma unchanged; chi_k is evaluated as x_k^6 / sum x^6 with
 // x = g / g_max in (0, 1] so that nothing overflows.  Returns the codes
 // d0<<2 | d1<<1 | d2 of both splits.
+// tau of both windows (Eq. tau5 on the 4-beta scale below), with the same
+// operations as in cutoff2, for the keep-all test of all fields at once
+__device__ __forceinline__ float2 tau_pair(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4) {
+    const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
+    const float2 s0b = __fadd2_rn(__ffma2_rn(f2(-2.f), w1, w0), w2);
+    const float2 s2a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w3, w4));
+    const float2 s2b = __fadd2_rn(__ffma2_rn(f2(-2.f), w3, w2), w4);
+    const float2 b0 = __ffma2_rn(s0b, __fmul2_rn(f2(13.f / 3.f), s0b), __fmul2_rn(s0a, s0a));
+    const float2 b2 = __ffma2_rn(s2b, __fmul2_rn(f2(13.f / 3.f), s2b), __fmul2_rn(s2a, s2a));
+    const float2 td = __ffma2_rn(f2(-1.f), b2, b0);
+    return make_float2(fabsf(td.x), fabsf(td.y));
+}
+
 __device__ __forceinline__ void cutoff2(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps4, float CT,
                                         float kt, unsigned &cp, unsigned &cm) {
     const float2 s0a = __ffma2_rn(f2(3.f), w2, __ffma2_rn(f2(-4.f), w1, w0));
@@ -963,8 +990,8 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     auto load_tile = [&](int tile) {
         const int c0 = tile * WT;
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
-        if (ga < 0 || ga >= n) ga = ghost_map(ga, n, A.bc_lo, A.bc_hi);
-        if (gb < 0 || gb >= n) gb = ghost_map(gb, n, A.bc_lo, A.bc_hi);
+        if (ga < 0 || ga >= n) ga = ghost_or_halo(ga, n, A.bc_lo, A.bc_hi, A.halo);
+        if (gb < 0 || gb >= n) gb = ghost_or_halo(gb, n, A.bc_lo, A.bc_hi, A.halo);
 #pragma unroll
         for (int k = 0; k < M; k++) {
             ua[k] = Us[(size_t)k * cs + ga];
@@ -1197,7 +1224,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                     else
                         o[k] = fma(2.0 / 3.0, v, (1.0 / 3.0) * (double)u0r[k]);
                 }
-                out[(size_t)k * cs + i] = (S)o[k];
+                out[(size_t)k * A.cso + i] = (S)o[k];
                 of[k] = to_f32(o[k]);
             }
             if (!A.rhs_mode) {
@@ -1211,7 +1238,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
             for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
             if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * cs + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + i] = r[k];
             } else {
                 float o[M];
 #pragma unroll
@@ -1226,7 +1253,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                         // grow the solution by 6e-8 every step
                         o[k] = fmaf(2.0f / 3.0f, v - (float)u0r[k], (float)u0r[k]);
                     }
-                    out[(size_t)k * cs + i] = (S)o[k];
+                    out[(size_t)k * A.cso + i] = (S)o[k];
                 }
                 int wflag = 0;
                 wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(o, gm1, gamma, a, &wflag));
@@ -1259,15 +1286,20 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     else
         fill_delta_table(s_cf);
     TileArgs<float> A;
-    A.alpha = ctl->alpha_f[p.slot_in][0];
+    A.alpha = p.alpha_in ? (float)*p.alpha_in : ctl->alpha_f[p.slot_in][0];
     A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
     A.dtD = fixed ? p.dt_fixed : ctl->dt;
-    A.Us = static_cast<const float *>(p.Us);
-    A.U0 = static_cast<const float *>(p.U0);
-    A.out = static_cast<float *>(p.out);
+    // (the pointers stay untyped here: the state type S may be double)
+    // slab mode: cell 0 follows the padding (the RHS output dU/dt is unpadded)
+    const int off = p.halo ? HALO_CELLS : 0, offo = p.rhs_mode ? 0 : off;
+    A.Us = reinterpret_cast<const float *>(static_cast<const S *>(p.Us) + off);
+    A.U0 = p.U0 ? reinterpret_cast<const float *>(static_cast<const S *>(p.U0) + off) : nullptr;
+    A.out = reinterpret_cast<float *>(static_cast<S *>(p.out) + offo);
     A.masks = p.masks;
     A.n = p.n;
-    A.cs = (size_t)p.n;
+    A.cs = (size_t)p.n + 2 * off;
+    A.cso = (size_t)p.n + 2 * offo;
+    A.halo = p.halo;
     A.bc_lo = p.bc_lo;
     A.bc_hi = p.bc_hi;
     A.dx = p.dx;
@@ -1302,6 +1334,433 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
     }
 }
 
+// ==========================================================================
+// FP32 stage kernel with paired FACES (grid-wide launches over the whole
+// domain, FP32 state).  Lane l of a warp owns the two faces jA = c0-2+l and
+// jB = c0+30+l of a WT2 = 61-cell warp tile (cells c0 .. c0+60), and every
+// float2 holds (face A, face B).  The two splits run one after the other,
+// each through the same projection, smoothness measure, neighbour exchange
+// and polynomial as the paired-split kernel above, so every face sees the
+// same per-element operations; the Roe frame, the back projection and the
+// RK update of the two faces and cells run as packed f32x2 arithmetic, and a
+// tile stages 71 cells for 61 updated (39 for 29 in the paired-split tiles).
+// Neighbour faces: jA - 1 and jA + 1 are the A faces of lanes l-1 and l+1,
+// except that face c0+30 (right of lane 31's A) is lane 0's B; jB - 1 and
+// jB + 1 are the B faces of lanes l-1 and l+1, except that face c0+29 (left of
+// lane 0's B) is lane 31's A.  Faces c0-2 (lane 0, A) and c0+61 (lane 31, B)
+// lack a neighbour code and only serve their neighbours.
+// Scalar advection with a = alpha > 0 (the host's dispatch guarantees it)
+// reconstructs the '+' split only: the '-' split flux (a - alpha) u / 2 is
+// identically zero, its windows are all zero, every stencil of them is kept
+// and its polynomial is exactly zero.
+// ==========================================================================
+constexpr int WT2 = 61;  // cells updated per face-paired warp tile
+constexpr int WS2 = 71;  // cells staged per face-paired warp tile (c0-5 .. c0+65)
+constexpr int WC2 = 72;  // padded row length
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int SYS, int SCH>
+__device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float (*sU)[WC2], float (*sgp)[WC2],
+                                                float (*sgm)[WC2], float (*spr)[WC2], const float (*s_cf)[8],
+                                                int tile0, int tstride) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr bool PLUS_ONLY = SYS == SYS_ADV;
+    constexpr int SH = 5 * M;                          // B slots sit SH bits above the A slots
+    constexpr unsigned MASK_A = (1u << SH) - 1u;       // the A slots of a code word
+    constexpr unsigned ALL_A = M == 3 ? 0x7FFFu : 31u; // every A slot all ones
+    const int lane = threadIdx.x & 31;
+    const float alpha = A.alpha, dtT = A.dtT, gamma = A.gamma, gm1 = A.gm1, a = A.a;
+    const float eps4 = SCH == SCH_TENO5 ? fmaxf(4.f * A.eps, 1.17549435e-38f) : 4.f * A.eps, CT = A.CT;
+    const float kt = keep_all_factor(CT);
+    const float idx = 1.f / A.f_dx;
+    const float *Us = A.Us;
+    const float *U0 = A.U0;
+    float *out = A.out;
+    const int n = A.n;
+    const size_t cs = A.cs;
+    const int ntiles = (n + WT2 - 1) / WT2;
+    DevCtl *ctl = A.ctl;
+    float wsmax = 0.f;
+    // raw state of the staged cells (rounds r = 0, 1, 2: cells c0-5+32r+lane),
+    // loaded one tile ahead
+    float ur[3][M];
+    auto load_tile = [&](int tile) {
+        const int c0 = tile * WT2;
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            int g = c0 - 5 + 32 * r + lane;
+            if (g < 0 || g >= n) g = ghost_map(g, n, A.bc_lo, A.bc_hi);
+#pragma unroll
+            for (int k = 0; k < M; k++) ur[r][k] = (r < 2 || lane < WS2 - 64) ? Us[(size_t)k * cs + g] : 0.f;
+        }
+    };
+    int tile = tile0;
+    if (tile < ntiles) load_tile(tile);
+
+    for (; tile < ntiles; tile += tstride) {
+        const int c0 = tile * WT2;
+        const int jA = c0 - 2 + lane, jB = c0 + 30 + lane;  // faces, and the cells they update
+        const bool updA = lane >= 2 && jA < n, updB = lane <= 30 && jB < n;
+        float2 u0r[M];
+        if (!A.rhs_mode && A.stage > 0) {
+            const int iA = jA < n ? jA : n - 1, iB = jB < n ? jB : n - 1;
+#pragma unroll
+            for (int k = 0; k < M; k++)
+                u0r[k] = make_float2(U0[(size_t)k * cs + (iA < 0 ? 0 : iA)], U0[(size_t)k * cs + iB]);
+        }
+        float Ucur[3][M];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int k = 0; k < M; k++) Ucur[r][k] = ur[r][k];
+        if (tile + tstride < ntiles) load_tile(tile + tstride);
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const int c = lane + 32 * r;
+            if (c >= WS2) break;
+            float U[M], F[M];
+#pragma unroll
+            for (int k = 0; k < M; k++) U[k] = Ucur[r][k];
+            if (SYS == SYS_ADV) {
+                F[0] = a * U[0];
+            } else if (SYS == SYS_BURGERS) {
+                F[0] = 0.5f * U[0] * U[0];
+            } else {
+                const float ri = rcp_approx(U[0]);
+                const float u = U[1] * ri;
+                const float pr = gm1 * (U[2] - 0.5f * U[1] * u);
+                F[0] = U[1];
+                F[1] = U[1] * u + pr;
+                F[2] = u * (U[2] + pr);
+                spr[0][c] = u;
+                spr[NP > 1 ? 1 : 0][c] = (U[2] + pr) * ri;
+                spr[NP > 2 ? 2 : 0][c] = U[0] * rsqrtf(U[0]);
+            }
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                sU[k][c] = U[k];
+                if (SYS == SYS_ADV) {
+                    sgp[k][c] = (0.5f * (a + alpha)) * U[k];
+                } else {
+                    sgp[k][c] = 0.5f * fmaf(alpha, U[k], F[k]);
+                    sgm[k][c] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- Roe frames of faces A and B (packed) --------------------------
+        float2 L2[M][M];
+        float2 ut = f2(0.f), cc = f2(0.f), Ht = f2(0.f);
+        int flagA = 0, flagB = 0;
+        if (SYS == SYS_EULER1D) {
+            const float2 ul = make_float2(spr[0][lane + 3], spr[0][lane + 35]);
+            const float2 ur_ = make_float2(spr[0][lane + 4], spr[0][lane + 36]);
+            const float2 Hl = make_float2(spr[NP > 1 ? 1 : 0][lane + 3], spr[NP > 1 ? 1 : 0][lane + 35]);
+            const float2 Hr = make_float2(spr[NP > 1 ? 1 : 0][lane + 4], spr[NP > 1 ? 1 : 0][lane + 36]);
+            const float2 sl = make_float2(spr[NP > 2 ? 2 : 0][lane + 3], spr[NP > 2 ? 2 : 0][lane + 35]);
+            const float2 sr = make_float2(spr[NP > 2 ? 2 : 0][lane + 4], spr[NP > 2 ? 2 : 0][lane + 36]);
+            const float2 ssum = __fadd2_rn(sl, sr);
+            const float2 w = make_float2(rcp_approx(ssum.x), rcp_approx(ssum.y));
+            ut = __fmul2_rn(__ffma2_rn(sl, ul, __fmul2_rn(sr, ur_)), w);
+            Ht = __fmul2_rn(__ffma2_rn(sl, Hl, __fmul2_rn(sr, Hr)), w);
+            const float2 hu = __fmul2_rn(f2(0.5f), ut);              // u/2
+            const float2 c2 = __fmul2_rn(f2(gm1), __ffma2_rn(f2neg(hu), ut, Ht));
+            const float2 rc = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));  // 1/c
+            cc = __fmul2_rn(c2, rc);
+            const float2 b1 = __fmul2_rn(f2(gm1), __fmul2_rn(rc, rc));
+            const float2 b2 = __fmul2_rn(__fmul2_rn(hu, ut), b1);
+            const float2 uc = __fmul2_rn(ut, rc);
+            const float2 hb1 = __fmul2_rn(f2(0.5f), b1);
+            L2[0][0] = __fmul2_rn(f2(0.5f), __fadd2_rn(b2, uc));
+            L2[0][1 % M] = __fmul2_rn(f2(-0.5f), __ffma2_rn(b1, ut, rc));
+            L2[0][2 % M] = hb1;
+            L2[1 % M][0] = __fadd2_rn(f2(1.f), f2neg(b2));
+            L2[1 % M][1 % M] = __fmul2_rn(b1, ut);
+            L2[1 % M][2 % M] = f2neg(b1);
+            L2[2 % M][0] = __fmul2_rn(f2(0.5f), __fadd2_rn(b2, f2neg(uc)));
+            L2[2 % M][1 % M] = __fmul2_rn(f2(-0.5f), __ffma2_rn(b1, ut, f2neg(rc)));
+            L2[2 % M][2 % M] = hb1;
+            if (!(c2.x > 0.f)) flagA |= isfinite(c2.x) ? ERR_NONPHYSICAL : ERR_NONFINITE;
+            if (!(c2.y > 0.f)) flagB |= isfinite(c2.y) ? ERR_NONPHYSICAL : ERR_NONFINITE;
+        }
+
+        // ---- the two splits: projection, cutoff, neighbour codes, polynomial
+        float2 f[M];
+        unsigned Dsave[2] = {0u, 0u};
+#pragma unroll
+        for (int s = 0; s < (PLUS_ONLY ? 1 : 2); s++) {
+            float (*sg)[WC2] = s == 0 ? sgp : sgm;
+            float2 P[M][7];
+#pragma unroll
+            for (int t = 0; t < 7; t++) {
+                if (SCH == SCH_TENO5 && (t == 0 || t == 6)) {
+#pragma unroll
+                    for (int k = 0; k < M; k++) P[k][t] = f2(0.f);
+                    continue;
+                }
+                // '+': cells j-3+t; '-': cells j+4-t (mirror image about j+1/2)
+                const int o = s == 0 ? lane + t : lane + 7 - t;
+                float2 g[M];
+#pragma unroll
+                for (int c = 0; c < M; c++) g[c] = make_float2(sg[c][o], sg[c][o + 32]);
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    if (M == 1) {
+                        P[k][t] = g[0];
+                    } else {
+                        float2 q = __fmul2_rn(L2[k][0], g[0]);
+#pragma unroll
+                        for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
+                        P[k][t] = q;
+                    }
+                }
+            }
+            // Every stencil of every window kept (tau < kt eps, see
+            // keep_all_factor) is tested for all fields at once, without
+            // branches in between, so that the fields' measures overlap; the
+            // per-window test below gives the same bits whenever this holds.
+            bool keep_all = true;
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const float2 tau = tau_pair(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5]);
+                keep_all = keep_all && tau.x < kt * eps4 && tau.y < kt * eps4;
+            }
+            unsigned word = 0;
+            if (keep_all) {
+#pragma unroll
+                for (int k = 0; k < M; k++) word |= (7u << (5 * k + 1)) | (7u << (SH + 5 * k + 1));
+            } else {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    unsigned cA, cB;
+                    cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps4, CT, kt, cA, cB);
+                    word |= (cA << (5 * k + 1)) | (cB << (SH + 5 * k + 1));
+                }
+            }
+            unsigned D;
+            if constexpr (SCH == SCH_TENO5) {
+                D = word;
+            } else {
+                const unsigned wl = __shfl_sync(0xffffffffu, word, (lane + 31) & 31);
+                const unsigned wr = __shfl_sync(0xffffffffu, word, (lane + 1) & 31);
+                // codes of each face's left and right neighbour faces, in its own slots
+                const unsigned LW = lane == 0 ? (wl & MASK_A) | (wl << SH) : wl;
+                const unsigned RW = lane == 31 ? (wr >> SH) | (wr & ~MASK_A) : wr;
+                D = s == 0 ? (((LW << 1) & SLOT_HI) | (word & SLOT_MID) | ((RW >> 1) & SLOT_LO))
+                           : (((RW << 1) & SLOT_HI) | (word & SLOT_MID) | ((LW >> 1) & SLOT_LO));
+            }
+            Dsave[s] = D;
+            constexpr unsigned ALL = SCH == SCH_TENO5 ? ((M == 3) ? SLOT_MID : (14u | (14u << 5)))
+                                                      : (ALL_A | (ALL_A << SH));
+            float2 fs[M];
+            if (SCH == SCH_TENO5 && (D & ALL) == ALL) {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    float2 v = __fmul2_rn(f2(1.f / 30.f), P[k][1]);
+                    v = __ffma2_rn(f2(-13.f / 60.f), P[k][2], v);
+                    v = __ffma2_rn(f2(47.f / 60.f), P[k][3], v);
+                    v = __ffma2_rn(f2(9.f / 20.f), P[k][4], v);
+                    v = __ffma2_rn(f2(-1.f / 20.f), P[k][5], v);
+                    fs[k] = v;
+                }
+            } else if (SCH == SCH_TENO5) {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    const float *cA = s_cf[(D >> (5 * k)) & 31u];
+                    const float *cB = s_cf[(D >> (SH + 5 * k)) & 31u];
+                    float2 v = __fmul2_rn(make_float2(cA[1], cB[1]), P[k][1]);
+#pragma unroll
+                    for (int t = 2; t < 6; t++) v = __ffma2_rn(make_float2(cA[t], cB[t]), P[k][t], v);
+                    fs[k] = v;
+                }
+            } else if ((D & ALL) == ALL) {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    float2 v = __fmul2_rn(f2(-1.f / 140.f), P[k][0]);
+                    v = __ffma2_rn(f2(5.f / 84.f), P[k][1], v);
+                    v = __ffma2_rn(f2(-101.f / 420.f), P[k][2], v);
+                    v = __ffma2_rn(f2(319.f / 420.f), P[k][3], v);
+                    v = __ffma2_rn(f2(107.f / 210.f), P[k][4], v);
+                    v = __ffma2_rn(f2(-19.f / 210.f), P[k][5], v);
+                    v = __ffma2_rn(f2(1.f / 105.f), P[k][6], v);
+                    fs[k] = v;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    const float *cA = s_cf[(D >> (5 * k)) & 31u];
+                    const float *cB = s_cf[(D >> (SH + 5 * k)) & 31u];
+                    float2 v = __fmul2_rn(make_float2(cA[0], cB[0]), P[k][0]);
+#pragma unroll
+                    for (int t = 1; t < 7; t++) v = __ffma2_rn(make_float2(cA[t], cB[t]), P[k][t], v);
+                    fs[k] = v;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < M; k++) f[k] = s == 0 ? fs[k] : __fadd2_rn(f[k], fs[k]);
+        }
+        if (A.masks) {
+            // '+' in index 0, '-' in index 1 (advection: every '-' code is all ones)
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int j = h == 0 ? jA : jB;
+                    const bool ok = (h == 0 ? lane >= 1 : lane <= 30) && j >= -1 && j <= n - 1;
+                    if (!ok) continue;
+                    const int sh = h == 0 ? 5 * k : SH + 5 * k;
+                    const unsigned sp = (Dsave[0] >> sh) & 31u;
+                    const unsigned sm = PLUS_ONLY ? (SCH == SCH_TENO5 ? 14u : 31u) : (Dsave[1] >> sh) & 31u;
+                    A.masks[(size_t)(0 * M + k) * (n + 1) + (j + 1)] =
+                        (uint8_t)(SCH == SCH_TENO5 ? slot_code(sp) : sp);
+                    A.masks[(size_t)(1 * M + k) * (n + 1) + (j + 1)] =
+                        (uint8_t)(SCH == SCH_TENO5 ? slot_code(sm) : sm);
+                }
+            }
+        }
+        float2 fh[M];
+        if (SYS == SYS_EULER1D) {
+            // R columns: eigenvectors of u-c, u, u+c at the Roe state
+            fh[0] = __fadd2_rn(__fadd2_rn(f[0], f[1 % M]), f[2 % M]);
+            // (a f0 + b f1 + c f2 is evaluated as fma(c, f2, fma(a, f0, b f1)))
+            const float2 umc = __fadd2_rn(ut, f2neg(cc)), upc = __fadd2_rn(ut, cc);
+            fh[1 % M] = __ffma2_rn(upc, f[2 % M], __ffma2_rn(umc, f[0], __fmul2_rn(ut, f[1 % M])));
+            const float2 R20 = __ffma2_rn(f2neg(ut), cc, Ht), R22 = __ffma2_rn(ut, cc, Ht);
+            const float2 R21 = __fmul2_rn(__fmul2_rn(f2(0.5f), ut), ut);
+            fh[2 % M] = __ffma2_rn(R22, f[2 % M], __ffma2_rn(R20, f[0], __fmul2_rn(R21, f[1 % M])));
+        } else {
+            fh[0] = f[0];
+        }
+        if (flagA && lane >= 1 && jA >= -2 && jA <= n) latch_error(ctl, flagA, A.ebase + jA);
+        if (flagB && lane <= 30 && jB <= n) latch_error(ctl, flagB, A.ebase + jB);
+
+        // ---- flux difference and RK stage of cells jA and jB -------------
+        float2 fprev[M];
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            const float xr = __shfl_sync(0xffffffffu, fh[k].x, (lane + 31) & 31);
+            const float yr = __shfl_sync(0xffffffffu, fh[k].y, (lane + 31) & 31);
+            fprev[k] = make_float2(xr, lane == 0 ? xr : yr);
+        }
+        if (updA || updB) {
+            float2 r[M];
+#pragma unroll
+            for (int k = 0; k < M; k++) r[k] = __fmul2_rn(__fadd2_rn(fprev[k], f2neg(fh[k])), f2(idx));
+            if (A.rhs_mode) {
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    if (updA) out[(size_t)k * cs + jA] = r[k].x;
+                    if (updB) out[(size_t)k * cs + jB] = r[k].y;
+                }
+            } else {
+                float2 o[M];
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    const float2 v = __ffma2_rn(f2(dtT), r[k], make_float2(sU[k][lane + 3], sU[k][lane + 35]));
+                    if (A.stage == 0) {
+                        o[k] = v;
+                    } else if (A.stage == 1) {
+                        o[k] = __ffma2_rn(f2(0.75f), u0r[k], __fmul2_rn(f2(0.25f), v));
+                    } else {
+                        // u0 + 2/3 (v - u0): float(1/3) + float(2/3) != 1 would
+                        // grow the solution by 6e-8 every step
+                        o[k] = __ffma2_rn(f2(2.0f / 3.0f), __fadd2_rn(v, f2neg(u0r[k])), u0r[k]);
+                    }
+                    if (updA) out[(size_t)k * cs + jA] = o[k].x;
+                    if (updB) out[(size_t)k * cs + jB] = o[k].y;
+                }
+                float oa[M], ob[M];
+#pragma unroll
+                for (int k = 0; k < M; k++) {
+                    oa[k] = o[k].x;
+                    ob[k] = o[k].y;
+                }
+                int wfA = 0, wfB = 0;
+                const float wa = wavespeed1d_fast<SYS>(oa, gm1, gamma, a, &wfA);
+                const float wb = wavespeed1d_fast<SYS>(ob, gm1, gamma, a, &wfB);
+                if (updA) {
+                    wsmax = fmaxf(wsmax, wa);
+                    if (wfA) latch_error(ctl, wfA, A.ebase + jA);
+                }
+                if (updB) {
+                    wsmax = fmaxf(wsmax, wb);
+                    if (wfB) latch_error(ctl, wfB, A.ebase + jB);
+                }
+            }
+        }
+        __syncwarp();  // the next tile overwrites this warp's staging rows
+    }
+    return wsmax;
+}
+
+template <int SYS, int SCH>
+__global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(const Stage1D p) {
+    constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
+    constexpr int MG = (SYS == SYS_ADV) ? 1 : M;  // '-' staging rows (unused for advection)
+    __shared__ float s_U[WPB][M][WC2];
+    __shared__ float s_gp[WPB][M][WC2];
+    __shared__ float s_gm[WPB][MG][WC2];
+    __shared__ float s_pr[WPB][NP][WC2];
+    __shared__ __align__(16) float s_cf[32][8];
+    __shared__ float s_red[WPB];
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;  // uniform: the run has ended
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (SCH == SCH_TENO5)
+        fill_delta_table5(s_cf);
+    else
+        fill_delta_table(s_cf);
+    TileArgs<float> A;
+    A.alpha = ctl->alpha_f[p.slot_in][0];
+    A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
+    A.dtD = fixed ? p.dt_fixed : ctl->dt;
+    A.Us = static_cast<const float *>(p.Us);
+    A.U0 = static_cast<const float *>(p.U0);
+    A.out = static_cast<float *>(p.out);
+    A.masks = p.masks;
+    A.n = p.n;
+    A.cs = (size_t)p.n;
+    A.cso = A.cs;
+    A.bc_lo = p.bc_lo;
+    A.bc_hi = p.bc_hi;
+    A.dx = p.dx;
+    A.f_dx = p.f_dx;
+    A.gamma = p.f_gamma;
+    A.gm1 = p.f_gm1;
+    A.a = p.f_a;
+    A.eps = p.f_eps;
+    A.CT = p.f_CT;
+    A.rhs_mode = p.rhs_mode;
+    A.stage = p.stage;
+    A.ebase = 0;
+    A.halo = 0;
+    A.ctl = ctl;
+    __syncthreads();
+    float wsmax = tiles1d_f32_fp<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
+                                           blockIdx.x * nw + warp, gridDim.x * nw);
+    (void)lane;
+    if (!p.rhs_mode) {
+        wsmax = warp_max(wsmax);
+        if ((threadIdx.x & 31) == 0) s_red[warp] = wsmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = s_red[0];
+#pragma unroll
+            for (int w = 1; w < nw; w++) v = fmaxf(v, s_red[w]);
+            const int so = (p.stage + 1) % 3;
+            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
+                          p.alpha_rec);
+        }
+    }
+}
+
 // alpha of a 1D state into ctl->amax[slot][0]; grid-stride, one atomic per CTA;
 // the last CTA converts it and plans the first RK step (see finish_launch).
 template <typename T, int SYS>
@@ -1312,10 +1771,11 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     T m = T(0);
     int flag = 0, first = 0x7fffffff;
+    const size_t cs = p.stride > 0 ? (size_t)p.stride : (size_t)p.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
         T Uc[M];
 #pragma unroll
-        for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * p.n + i];
+        for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * cs + i];
         int f = 0;
         const T w = wavespeed1d<T, SYS>(Uc, gm1, gamma, a, &f);
         if (f) {
@@ -1436,6 +1896,36 @@ cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
+    // FP32 state of a scalar law over the whole domain: face-paired tiles
+    // (advection when a > 0, where alpha = a makes the '-' split vanish).
+    // Their results equal the paired-split kernel's bit for bit.  (Euler
+    // stays on the paired-split kernel: its face-paired form rounds the Roe
+    // frame differently, and one colliding-flow tube of the FP32 robustness
+    // family went non-physical with it.)
+    if (sizeof(S) == 4 && p.tile_lo == 0 && p.tile_hi <= 0 && !p.partial && !p.halo &&
+        ((p.sys == SYS_ADV && p.a > 0.0) || p.sys == SYS_BURGERS)) {
+        const int nt2 = (p.n + WT2 - 1) / WT2;
+        const int nw2 = warps_per_cta(nt2, false);
+        const int res2 = num_sms() * T7_F32_MINB * 4 * (WPB / nw2);
+        int grid2 = (nt2 + nw2 - 1) / nw2;
+        if (grid2 > res2) grid2 = res2;
+        switch (p.sys) {
+            case SYS_ADV:
+                if (t5) stage1d_f32fp_kernel<SYS_ADV, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
+                else stage1d_f32fp_kernel<SYS_ADV, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                break;
+            case SYS_BURGERS:
+                if (t5) stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
+                else stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                break;
+            case SYS_EULER1D:
+                if (t5) stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
+                else stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (p.sys) {
         case SYS_ADV:
             if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
@@ -1590,6 +2080,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
         A.masks = nullptr;
         A.n = n;
         A.cs = cs;
+        A.cso = cs;
         A.bc_lo = p.bc_lo;
         A.bc_hi = p.bc_hi;
         A.dx = dx;
@@ -1601,6 +2092,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) batch1d_ke
         A.CT = T(p.CT);
         A.rhs_mode = 0;
         A.ebase = (int)off;
+        A.halo = 0;
         A.ctl = p.ctl;
         A.U0 = U + off;
         T *ins[3] = {U + off, W1 + off, W2 + off};

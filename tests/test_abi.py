@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads without a GPU, and exports every
-entry point include/teno7.h declares (no compute call is made here)."""
+entry point the headers under include/ declare (no compute call is made here)."""
 import ctypes
 import re
 from pathlib import Path
@@ -10,8 +10,11 @@ ROOT = Path(__file__).resolve().parents[1]
 
 
 def declared():
-    text = (ROOT / "include" / "teno7.h").read_text()
-    return sorted(set(re.findall(r"^\s*(?:t7_status|const char \*)\s*(t7_\w+)\s*\(", text, re.M)))
+    names = set()
+    for h in sorted((ROOT / "include").glob("*.h")):
+        text = h.read_text()
+        names |= set(re.findall(r"^\s*(?:t7_status|const char \*)\s*(t7_\w+)\s*\(", text, re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_hot_path_calls():
@@ -104,7 +107,7 @@ def test_header_is_plain_c_and_links_from_c(tmp_path):
         pytest.skip("no C compiler")
     lib_path = cuda_build.build()
     src = tmp_path / "use.c"
-    src.write_text('#include "teno7.h"\n'
+    src.write_text('#include "teno7.h"\n#include "teno7_probe.h"\n'
                    "int main(void) {\n"
                    "    t7_grid g = {0};\n"
                    "    t7_ctx *c = 0;\n"
