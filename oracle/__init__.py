@@ -24,6 +24,12 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                   Sod and Lax tubes; exact shift for advection.
   rhs_2d / run_2d              -- reduces to the 1D scheme on y-independent
                                   data; x/y transpose symmetry.
+  rhs_1d_tl / rk3_step_1d_tl   -- tangent linear with frozen selection and alpha:
+  / run_1d_tl                     value parts bit-identical to the primal,
+                                  derivative against fourth-order central
+                                  differences of the primal (frozen alpha and
+                                  masks), Euler's theorem J U = L(U) for the
+                                  degree-1 homogeneous frozen scheme.
 """
 from __future__ import annotations
 
@@ -81,6 +87,9 @@ def lib() -> ctypes.CDLL:
         _lib.or_select5.argtypes = [i]
         _lib.or_coeffs5.argtypes = [p]
         _lib.or_frame_2d.argtypes = [p, p, d, i, p, p]
+        _lib.or_rhs_1d_tl.argtypes = [i, p, p, i, d, d, d, i, i, d, p, p, p]
+        _lib.or_rk3_step_1d_tl.argtypes = [i, p, p, i, d, d, d, d, d, i, i, d]
+        _lib.or_run_1d_tl.argtypes = [i, p, p, i, d, d, d, d, d, i, i, d, i]
     return _lib
 
 
@@ -201,6 +210,47 @@ def cfl_dt_1d(sys, U, dx, cfl, *, gamma=1.4, a=1.0):
     st = lib().or_cfl_dt_1d(sys, _ptr(U), U.shape[1], dx, gamma, a, cfl, _ptr(dt))
     _check(st, "cfl_dt_1d", True)
     return float(dt[0])
+
+
+# ------------------------------------------------------ tangent linear ----
+def rhs_1d_tl(sys, U, dU, dx, alpha, masks, *, gamma=1.4, a=1.0, bc=(BC_PERIODIC, BC_PERIODIC)):
+    """(L(U), (dL/dU) dU) with alpha and the selection `masks` ([2, m, n+1]
+    Delta codes, as rhs_1d returns them for U) frozen.  TENO7-ext only."""
+    U = _f64(U)
+    m = nvars(sys)
+    U = U.reshape(m, -1)
+    dU = _f64(dU).reshape(m, -1)
+    n = U.shape[1]
+    masks = np.ascontiguousarray(masks, dtype=np.uint8)
+    if masks.shape != (2, m, n + 1):
+        raise ValueError("masks must be [2, m, n + 1]")
+    L, dL = np.zeros_like(U), np.zeros_like(U)
+    st = lib().or_rhs_1d_tl(sys, _ptr(U), _ptr(dU), n, dx, gamma, a, bc[0], bc[1], alpha, _ptr(masks), _ptr(L),
+                            _ptr(dL))
+    _check(st, "rhs_1d_tl", True)
+    return L, dL
+
+
+def rk3_step_1d_tl(sys, U, dU, dx, dt, *, gamma=1.4, a=1.0, CT=1e-5, eps=-1.0, bc=(BC_PERIODIC, BC_PERIODIC)):
+    """One SSP-RK3 step of fixed dt and its tangent along dU (each stage's
+    alpha and selection frozen at the primal stage state).  Returns (U', dU')."""
+    m = nvars(sys)
+    U = _f64(U).copy().reshape(m, -1)
+    dU = _f64(dU).copy().reshape(m, -1)
+    st = lib().or_rk3_step_1d_tl(sys, _ptr(U), _ptr(dU), U.shape[1], dx, gamma, a, CT, eps, bc[0], bc[1], dt)
+    _check(st, "rk3_step_1d_tl", True)
+    return U, dU
+
+
+def run_1d_tl(sys, U, dU, dx, dt, nsteps, *, gamma=1.4, a=1.0, CT=1e-5, eps=-1.0, bc=(BC_PERIODIC, BC_PERIODIC)):
+    """nsteps tangent-linear RK3 steps of fixed dt.  Returns (U_final, dU_final)."""
+    m = nvars(sys)
+    U = _f64(U).copy().reshape(m, -1)
+    dU = _f64(dU).copy().reshape(m, -1)
+    st = lib().or_run_1d_tl(sys, _ptr(U), _ptr(dU), U.shape[1], dx, gamma, a, CT, eps, bc[0], bc[1], dt,
+                            int(nsteps))
+    _check(st, "run_1d_tl", True)
+    return U, dU
 
 
 def alpha_1d(sys, U, *, gamma=1.4, a=1.0):

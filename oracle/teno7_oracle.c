@@ -841,3 +841,243 @@ int or_alpha_2d(const double *U, int nx, int ny, double gamma, double *alpha_out
     if (bad & 1) return OR_ENONPHYSICAL;
     return OR_OK;
 }
+
+/* ======================================================================== */
+/* Tangent-linear (forward-mode) 1D right-hand side and SSP-RK3 step.        */
+/*                                                                          */
+/* The discrete adjoint of the scheme differentiates it with the stencil    */
+/* selection (every Delta of both splits and all fields) and the global      */
+/* Lax-Friedrichs alpha held at their values for the state: with those       */
+/* frozen, L is a smooth function of U (Eq. app through the Roe frame of     */
+/* Remark 3, the split fluxes and the fixed Table co2 polynomials).  This    */
+/* section evaluates the directional derivative dL = (dL/dU) dU exactly, by  */
+/* carrying every quantity as a dual number (value, derivative) through the  */
+/* same operations, in the same order, as the primal code above; the value   */
+/* parts therefore equal the primal results.  It is the reference the        */
+/* hand-written GPU adjoint is checked against by the dot-product identity   */
+/* <v, J u> = <J^T v, u>.  TENO7-ext, 1D systems.                            */
+/* ======================================================================== */
+typedef struct {
+    double v, d;
+} dual;
+
+static dual dcst(double v) { return (dual){v, 0.0}; }
+static dual dadd(dual a, dual b) { return (dual){a.v + b.v, a.d + b.d}; }
+static dual dsub(dual a, dual b) { return (dual){a.v - b.v, a.d - b.d}; }
+static dual dmul(dual a, dual b) { return (dual){a.v * b.v, a.d * b.v + a.v * b.d}; }
+static dual dscale(double c, dual a) { return (dual){c * a.v, c * a.d}; }
+static dual ddiv(dual a, dual b) {
+    double q = a.v / b.v;
+    return (dual){q, (a.d - q * b.d) / b.v};
+}
+static dual dsqrt(dual a) {
+    double s = sqrt(a.v);
+    return (dual){s, a.d / (2.0 * s)};
+}
+
+static void flux_tl(const sysdef *S, const dual *U, dual *F) {
+    if (S->sys == SYS_ADVECTION) {
+        F[0] = dscale(S->a, U[0]);
+    } else if (S->sys == SYS_BURGERS) {
+        F[0] = dmul(dscale(0.5, U[0]), U[0]);
+    } else {
+        dual u = ddiv(U[1], U[0]);
+        dual p = dscale(S->gamma - 1.0, dsub(U[2], dmul(dscale(0.5, U[1]), u)));
+        F[0] = U[1];
+        F[1] = dadd(dmul(U[1], u), p);
+        F[2] = dmul(u, dadd(U[2], p));
+    }
+}
+
+/* Roe frame of the 1D Euler system (as frame() above) in dual numbers. */
+static void frame_tl(const sysdef *S, const dual *UL, const dual *UR, dual L[3][3], dual R[3][3]) {
+    if (S->m == 1) {
+        L[0][0] = dcst(1.0);
+        R[0][0] = dcst(1.0);
+        return;
+    }
+    double gm = S->gamma - 1.0;
+    dual rl = UL[0], rr = UR[0];
+    dual ul = ddiv(UL[1], rl), ur = ddiv(UR[1], rr);
+    dual pl = dscale(gm, dsub(UL[2], dmul(dscale(0.5, UL[1]), ul)));
+    dual pr = dscale(gm, dsub(UR[2], dmul(dscale(0.5, UR[1]), ur)));
+    dual Hl = ddiv(dadd(UL[2], pl), rl), Hr = ddiv(dadd(UR[2], pr), rr);
+    dual sl = dsqrt(rl), sr = dsqrt(rr);
+    dual ut = ddiv(dadd(dmul(sl, ul), dmul(sr, ur)), dadd(sl, sr));
+    dual Ht = ddiv(dadd(dmul(sl, Hl), dmul(sr, Hr)), dadd(sl, sr));
+    dual c2 = dscale(gm, dsub(Ht, dmul(dscale(0.5, ut), ut)));
+    dual c = dsqrt(c2);
+    dual b1 = ddiv(dcst(gm), c2);
+    dual b2 = dmul(dmul(dscale(0.5, ut), ut), b1);
+    dual uc = ddiv(ut, c), rc = ddiv(dcst(1.0), c);
+    R[0][0] = dcst(1.0);
+    R[0][1] = dcst(1.0);
+    R[0][2] = dcst(1.0);
+    R[1][0] = dsub(ut, c);
+    R[1][1] = ut;
+    R[1][2] = dadd(ut, c);
+    R[2][0] = dsub(Ht, dmul(ut, c));
+    R[2][1] = dmul(dscale(0.5, ut), ut);
+    R[2][2] = dadd(Ht, dmul(ut, c));
+    L[0][0] = dscale(0.5, dadd(b2, uc));
+    L[0][1] = dscale(-0.5, dadd(dmul(b1, ut), rc));
+    L[0][2] = dscale(0.5, b1);
+    L[1][0] = dsub(dcst(1.0), b2);
+    L[1][1] = dmul(b1, ut);
+    L[1][2] = dscale(-1.0, b1);
+    L[2][0] = dscale(0.5, dsub(b2, uc));
+    L[2][1] = dscale(-0.5, dsub(dmul(b1, ut), rc));
+    L[2][2] = dscale(0.5, b1);
+}
+
+static dual poly_tl(int m, const dual *v) {
+    dual s = dcst(0.0);
+    for (int t = 0; t < 7; t++) s = dadd(s, dscale(COEF[m][t], v[t]));
+    return s;
+}
+
+/* One x sweep (as sweep() above) with the selection taken from masks
+ * ([2][m][n+1] Delta codes of faces -1 .. n-1) instead of the cutoff. */
+static void sweep_tl(const sysdef *S, dual **P, int n, double alpha, const uint8_t *masks, dual **Fh) {
+    int m = S->m, np = n + 2 * NG;
+    dual *Gp = (dual *)malloc(sizeof(dual) * m * np);
+    dual *Gm = (dual *)malloc(sizeof(dual) * m * np);
+    for (int l = 0; l < np; l++) {
+        dual U[3], F[3];
+        for (int c = 0; c < m; c++) U[c] = P[c][l];
+        flux_tl(S, U, F);
+        for (int c = 0; c < m; c++) {
+            Gp[c * np + l] = dscale(0.5, dadd(F[c], dscale(alpha, U[c])));
+            Gm[c * np + l] = dscale(0.5, dsub(F[c], dscale(alpha, U[c])));
+        }
+    }
+    for (int i = -1; i <= n - 1; i++) {
+        dual L[3][3], R[3][3], UL[3], UR[3], f[3];
+        for (int c = 0; c < m; c++) {
+            UL[c] = P[c][i + NG];
+            UR[c] = P[c][i + 1 + NG];
+        }
+        frame_tl(S, UL, UR, L, R);
+        for (int k = 0; k < m; k++) {
+            int mp = or_select(masks[(0 * m + k) * (n + 1) + i + 1]);
+            int mm = or_select(masks[(1 * m + k) * (n + 1) + i + 1]);
+            if (mp < 0) mp = 11;
+            if (mm < 0) mm = 11;
+            dual vp[7], vm[7];
+            for (int t = 0; t < 7; t++) {
+                int lp = i - 3 + t + NG, lm = i + 4 - t + NG;
+                dual sp = dmul(L[k][0], Gp[lp]), sm = dmul(L[k][0], Gm[lm]);
+                for (int c = 1; c < m; c++) {
+                    sp = dadd(sp, dmul(L[k][c], Gp[c * np + lp]));
+                    sm = dadd(sm, dmul(L[k][c], Gm[c * np + lm]));
+                }
+                vp[t] = sp;
+                vm[t] = sm;
+            }
+            f[k] = dadd(poly_tl(mp, vp), poly_tl(mm, vm));
+        }
+        for (int c = 0; c < m; c++) {
+            dual s = dmul(R[c][0], f[0]);
+            for (int k = 1; k < m; k++) s = dadd(s, dmul(R[c][k], f[k]));
+            Fh[c][i + 1] = s;
+        }
+    }
+    free(Gp);
+    free(Gm);
+}
+
+/* L(U) and dL = (dL/dU) dU with alpha and the selection (masks, as returned
+ * by or_rhs_1d for U) frozen.  U, dU, L, dL: [m][n]. */
+int or_rhs_1d_tl(int sys, const double *U, const double *dU, int n, double dx, double gamma, double a, int bc_lo,
+                 int bc_hi, double alpha, const uint8_t *masks, double *L, double *dL) {
+    if (n < 1 || !check_sys(sys, bc_lo, bc_hi) || !(dx > 0.0) || !masks || g_scheme != SCHEME_TENO7EXT)
+        return OR_EINVAL;
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int m = S.m, np = n + 2 * NG;
+    dual *P[3], *Fh[3];
+    for (int c = 0; c < m; c++) {
+        P[c] = (dual *)malloc(sizeof(dual) * np);
+        Fh[c] = (dual *)malloc(sizeof(dual) * (n + 1));
+        for (int l = -NG; l < n + NG; l++) {
+            int q = c * n + ghost_index(l, n, bc_lo, bc_hi);
+            P[c][l + NG] = (dual){U[q], dU[q]};
+        }
+    }
+    sweep_tl(&S, P, n, alpha, masks, Fh);
+    for (int c = 0; c < m; c++)
+        for (int i = 0; i < n; i++) {
+            dual r = ddiv(dsub(Fh[c][i], Fh[c][i + 1]), dcst(dx));
+            L[c * n + i] = r.v;
+            dL[c * n + i] = r.d;
+        }
+    for (int c = 0; c < m; c++) {
+        free(P[c]);
+        free(Fh[c]);
+    }
+    return OR_OK;
+}
+
+/* One SSP-RK3 step of fixed dt (as or_rk3_step_1d) with its tangent: U and
+ * dU advance in place; each stage's alpha and selection are those of the
+ * primal stage state (computed by or_rhs_1d) and are not differentiated. */
+int or_rk3_step_1d_tl(int sys, double *U, double *dU, int n, double dx, double gamma, double a, double CT,
+                      double eps, int bc_lo, int bc_hi, double dt) {
+    if (n < 1 || !check_sys(sys, bc_lo, bc_hi) || g_scheme != SCHEME_TENO7EXT) return OR_EINVAL;
+    int m = nvars_of(sys), N = m * n, status = OR_OK;
+    double *X[2], *dX[2], *r = (double *)malloc(sizeof(double) * N), *dr = (double *)malloc(sizeof(double) * N);
+    uint8_t *masks = (uint8_t *)malloc(2 * m * (n + 1));
+    for (int k = 0; k < 2; k++) {
+        X[k] = (double *)malloc(sizeof(double) * N);
+        dX[k] = (double *)malloc(sizeof(double) * N);
+    }
+    const double *stage_in[3] = {U, X[0], X[1]}, *dstage_in[3] = {dU, dX[0], dX[1]};
+    for (int s = 0; s < 3; s++) {
+        double alpha = 0.0;
+        int st = or_rhs_1d(sys, stage_in[s], n, dx, gamma, a, CT, eps, bc_lo, bc_hi, -1.0, r, masks, &alpha);
+        if (st) status = st;
+        or_rhs_1d_tl(sys, stage_in[s], dstage_in[s], n, dx, gamma, a, bc_lo, bc_hi, alpha, masks, r, dr);
+        for (int q = 0; q < N; q++) {
+            /* the Shu-Osher stages, in the primal's expression order */
+            dual u = {stage_in[s][q], dstage_in[s][q]}, u0 = {U[q], dU[q]}, rr = {r[q], dr[q]}, o;
+            if (s == 0)
+                o = dadd(u, dscale(dt, rr));
+            else if (s == 1)
+                o = dadd(dscale(0.75, u0), dscale(0.25, dadd(u, dscale(dt, rr))));
+            else
+                o = dadd(dscale(1.0 / 3.0, u0), dscale(2.0 / 3.0, dadd(u, dscale(dt, rr))));
+            if (s < 2) {
+                X[s][q] = o.v;
+                dX[s][q] = o.d;
+            } else {
+                r[q] = o.v; /* U is still read by later q as u0: keep the result aside */
+                dr[q] = o.d;
+            }
+        }
+        if (s == 2) {
+            memcpy(U, r, sizeof(double) * N);
+            memcpy(dU, dr, sizeof(double) * N);
+        }
+    }
+    for (int k = 0; k < 2; k++) {
+        free(X[k]);
+        free(dX[k]);
+    }
+    free(r);
+    free(dr);
+    free(masks);
+    return status;
+}
+
+/* nsteps tangent-linear RK3 steps of fixed dt (U, dU in place). */
+int or_run_1d_tl(int sys, double *U, double *dU, int n, double dx, double gamma, double a, double CT, double eps,
+                 int bc_lo, int bc_hi, double dt, int nsteps) {
+    int status = OR_OK;
+    for (int s = 0; s < nsteps; s++) {
+        int st = or_rk3_step_1d_tl(sys, U, dU, n, dx, gamma, a, CT, eps, bc_lo, bc_hi, dt);
+        if (st) {
+            status = st;
+            break;
+        }
+    }
+    return status;
+}

@@ -8,7 +8,11 @@ and the checkpointed autograd Function) against finite differences:
 * dot-product test of one RK3 step's adjoint against GPU forward differences;
 * gradients of J = sum rho^2 dx for the sine-mode problem against central
   differences of the oracle (reduced size) and of the GPU forward (full size:
-  N = 4096, 2000 steps, checkpoints every 100 steps).
+  N = 4096, 2000 steps, checkpoints every 100 steps);
+* dot-product tests of the RHS adjoint, the RK3-step adjoint and the reduced
+  sine-mode gradient against the oracle's tangent-linear mode (the exact
+  directional derivative with the same frozen selection and alpha) in FP64
+  to 1e-10.
 """
 import numpy as np
 import pytest
@@ -151,3 +155,67 @@ def test_recorded_step_and_its_adjoint(prec):
         scale = float(l_old.abs().max())
         tol = 1e-12 if prec == B.T7_F64 else 1e-4
         assert float((l_new - l_old).abs().max()) <= tol * scale
+
+
+# ---- against the oracle's tangent-linear mode (forward-mode derivative with
+# the same frozen selection and alpha), by the dot-product identity
+# <v, J u> = <J^T v, u>, in FP64 to 1e-10
+
+def test_rhs_adjoint_dot_product_against_tangent_linear_oracle():
+    rng = np.random.default_rng(15)
+    for name, (U, dx), bc in states():
+        n = U.shape[1]
+        _, alpha, masks = oracle.rhs_1d(oracle.SYS_EULER1D, U, dx, bc=bc, want_masks=True)
+        v = rng.normal(size=U.shape)
+        u = rng.normal(size=U.shape) * np.abs(U)
+        _, Ju = oracle.rhs_1d_tl(oracle.SYS_EULER1D, U, u, dx, alpha, masks, bc=bc)
+        lhs = np.sum(v * Ju)
+        c = B.Context(B.T7_EULER1D, n, dx, prec=B.T7_F64, bc=(bc[0], bc[1], 0, 0))
+        out = c.euler_rhs_adjoint(torch.tensor(U, device="cuda"), torch.tensor(v, device="cuda"))
+        c.sync()
+        rhs = np.sum(out.cpu().numpy() * u)
+        assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (name, lhs, rhs)
+        c.close()
+
+
+def test_rk3_step_adjoint_dot_product_against_tangent_linear_oracle():
+    """One step's adjoint (stage alphas and selections frozen at the primal
+    stage states) on smooth periodic data and on Shu-Osher."""
+    rng = np.random.default_rng(16)
+    for (U, dx), bc in ((I.random_euler_smooth(4, 512)[:2], (0, 0)), (I.shu_osher(400), (1, 1))):
+        n = U.shape[1]
+        c = B.Context(B.T7_EULER1D, n, dx, prec=B.T7_F64, bc=(bc[0], bc[1], 0, 0))
+        Ud = torch.tensor(U, device="cuda")
+        dt = c.cfl_dt(Ud, 0.5)
+        lam = rng.normal(size=U.shape)
+        w = rng.normal(size=U.shape) * np.abs(U)
+        _, Sw = oracle.rk3_step_1d_tl(oracle.SYS_EULER1D, U, w, dx, dt, bc=bc)
+        lhs = np.sum(lam * Sw)
+        L = torch.tensor(lam, device="cuda")
+        c.rk3_step_adjoint(Ud, dt, L)
+        c.sync()
+        rhs = np.sum(L.cpu().numpy() * w)
+        assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+        c.close()
+
+
+def test_sine_mode_gradient_against_tangent_linear_oracle():
+    """dJ/da . da of the reduced sine-mode problem (N = 256, 200 steps, 8
+    modes, checkpoints every 20): the adjoint gradient against the oracle's
+    tangent-linear run along da, with dJ = 2 sum rho drho dx."""
+    a = I.adjoint_modes(3, K=8)
+    n, nsteps = 256, 200
+    J, g, dt = A.sine_modes_gradient(a, n=n, nsteps=nsteps, every=20)
+    rng = np.random.default_rng(17)
+    for _ in range(3):
+        da = rng.normal(size=a.size) * np.abs(a)
+        U0, dx, x = I.adjoint_ic(a, n)
+        # rho0 = 1 + sum a_k sin(2 pi k x), u0 = p0 = 1: drho0 = sum da_k sin(2 pi k x),
+        # d(rho u)0 = drho0, dE0 = drho0 / 2
+        s = np.sin(2 * np.pi * np.outer(x, np.arange(1, a.size + 1))) @ da
+        dU0 = np.stack([s, s, 0.5 * s])
+        UN, dUN = oracle.run_1d_tl(oracle.SYS_EULER1D, U0, dU0, dx, dt, nsteps, bc=(0, 0))
+        assert float(np.sum(UN[0] ** 2) * dx) == pytest.approx(J, rel=1e-12)
+        lhs = 2.0 * np.sum(UN[0] * dUN[0]) * dx
+        rhs = float(np.dot(g, da))
+        assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
