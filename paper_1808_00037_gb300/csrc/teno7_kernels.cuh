@@ -945,6 +945,58 @@ __device__ __forceinline__ unsigned slot_code(unsigned s) {
     return ((s >> 3) & 1u) | (((s >> 2) & 1u) << 1) | (((s >> 1) & 1u) << 2);
 }
 
+// --------------------------------------------------------------------------
+// FP32 Roe frame and back projection of one 1D Euler face (Remark 3), with
+// every rounding written out: u~ = fma(s_l, u_l, s_r u_r) w, H~ likewise;
+// the shared products b1 u~, u~^2 / 2 and b2 rounded on their own; u~/c~
+// fused into L00 and L20; the back projection a f0 + b f1 + c f2 =
+// fma(c, f2, fma(a, f0, b f1)) with H~ -+ u~ c~ fused.  (This is the order in
+// which the compiler had contracted the same expressions written plainly;
+// spelling it out keeps the FP32 results fixed whatever a compiler's
+// contraction heuristics do.)  The FP32 1D stage kernels compute the frame
+// with these roundings, so their results agree bit for bit.
+// --------------------------------------------------------------------------
+struct RoeF32 {
+    float ut, cc, Ht;
+    float L[3][3];  // rows: left eigenvectors of u-c, u, u+c
+    int flag;       // ERR_NONPHYSICAL / ERR_NONFINITE when c^2 <= 0
+};
+
+__device__ __forceinline__ RoeF32 roe_frame_f32(float ul, float ur, float Hl, float Hr, float sl, float sr,
+                                                float gm1) {
+    RoeF32 F;
+    const float w = rcp_approx(sl + sr);
+    F.ut = __fmul_rn(__fmaf_rn(sl, ul, __fmul_rn(sr, ur)), w);
+    F.Ht = __fmul_rn(__fmaf_rn(sl, Hl, __fmul_rn(sr, Hr)), w);
+    const float q = __fmul_rn(__fmul_rn(0.5f, F.ut), F.ut);  // u~^2 / 2
+    const float c2 = __fmul_rn(gm1, __fadd_rn(F.Ht, -q));
+    const float rc = rsqrtf(c2);  // 1/c
+    F.cc = __fmul_rn(c2, rc);
+    const float b1 = __fmul_rn(gm1, __fmul_rn(rc, rc));
+    const float b2 = __fmul_rn(q, b1);
+    const float b1u = __fmul_rn(b1, F.ut);
+    F.L[0][0] = __fmul_rn(0.5f, __fmaf_rn(F.ut, rc, b2));
+    F.L[0][1] = __fmul_rn(-0.5f, __fadd_rn(b1u, rc));
+    F.L[0][2] = __fmul_rn(0.5f, b1);
+    F.L[1][0] = __fadd_rn(1.f, -b2);
+    F.L[1][1] = b1u;
+    F.L[1][2] = -b1;
+    F.L[2][0] = __fmul_rn(0.5f, __fmaf_rn(-F.ut, rc, b2));
+    F.L[2][1] = __fmul_rn(-0.5f, __fadd_rn(b1u, -rc));
+    F.L[2][2] = F.L[0][2];
+    F.flag = (c2 > 0.f) ? 0 : (isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE);
+    return F;
+}
+
+// R (columns: eigenvectors of u-c, u, u+c) times the characteristic fluxes f
+__device__ __forceinline__ void back_project_f32(const RoeF32 &F, const float f[3], float fh[3]) {
+    const float ut = F.ut, cc = F.cc, Ht = F.Ht;
+    fh[0] = __fadd_rn(__fadd_rn(f[0], f[1]), f[2]);
+    fh[1] = __fmaf_rn(__fadd_rn(ut, cc), f[2], __fmaf_rn(__fadd_rn(ut, -cc), f[0], __fmul_rn(ut, f[1])));
+    fh[2] = __fmaf_rn(__fmaf_rn(ut, cc, Ht), f[2],
+                      __fmaf_rn(__fmaf_rn(-ut, cc, Ht), f[0], __fmul_rn(__fmul_rn(__fmul_rn(0.5f, ut), ut), f[1])));
+}
+
 #ifndef T7_F32_MINB
 #define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
 #endif
@@ -1070,28 +1122,17 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         float ut = 0.f, cc = 0.f, Ht = 0.f;
         int flag = 0;
         if (SYS == SYS_EULER1D) {
-            const float ul = spr[0][lane + 3], ur = spr[0][lane + 4];
-            const float Hl = spr[NP > 1 ? 1 : 0][lane + 3], Hr = spr[NP > 1 ? 1 : 0][lane + 4];
-            const float sl = spr[NP > 2 ? 2 : 0][lane + 3], sr = spr[NP > 2 ? 2 : 0][lane + 4];
-            const float w = rcp_approx(sl + sr);
-            ut = (sl * ul + sr * ur) * w;
-            Ht = (sl * Hl + sr * Hr) * w;
-            const float c2 = gm1 * (Ht - 0.5f * ut * ut);
-            const float rc = rsqrtf(c2);
-            cc = c2 * rc;
-            const float b1 = gm1 * (rc * rc);
-            const float b2 = 0.5f * ut * ut * b1;
-            const float uc = ut * rc;
-            L2[0][0] = f2(0.5f * (b2 + uc));
-            L2[0][1 % M] = f2(-0.5f * (b1 * ut + rc));
-            L2[0][2 % M] = f2(0.5f * b1);
-            L2[1 % M][0] = f2(1.f - b2);
-            L2[1 % M][1 % M] = f2(b1 * ut);
-            L2[1 % M][2 % M] = f2(-b1);
-            L2[2 % M][0] = f2(0.5f * (b2 - uc));
-            L2[2 % M][1 % M] = f2(-0.5f * (b1 * ut - rc));
-            L2[2 % M][2 % M] = f2(0.5f * b1);
-            if (!(c2 > 0.f)) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
+            const RoeF32 F = roe_frame_f32(spr[0][lane + 3], spr[0][lane + 4], spr[NP > 1 ? 1 : 0][lane + 3],
+                                           spr[NP > 1 ? 1 : 0][lane + 4], spr[NP > 2 ? 2 : 0][lane + 3],
+                                           spr[NP > 2 ? 2 : 0][lane + 4], gm1);
+            ut = F.ut;
+            cc = F.cc;
+            Ht = F.Ht;
+#pragma unroll
+            for (int k = 0; k < M; k++)
+#pragma unroll
+                for (int c = 0; c < M; c++) L2[k][c] = f2(F.L[k % 3][c % 3]);
+            flag |= F.flag;
         }
 
         float2 P[M][7];
@@ -1194,9 +1235,14 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         }
         float fh[M];
         if (SYS == SYS_EULER1D) {
-            fh[0] = f[0] + f[1 % M] + f[2 % M];
-            fh[1 % M] = (ut - cc) * f[0] + ut * f[1 % M] + (ut + cc) * f[2 % M];
-            fh[2 % M] = (Ht - ut * cc) * f[0] + 0.5f * ut * ut * f[1 % M] + (Ht + ut * cc) * f[2 % M];
+            RoeF32 F;
+            F.ut = ut;
+            F.cc = cc;
+            F.Ht = Ht;
+            float f3[3] = {f[0], f[1 % M], f[2 % M]}, fh3[3];
+            back_project_f32(F, f3, fh3);
+#pragma unroll
+            for (int k = 0; k < M; k++) fh[k] = fh3[k % 3];
         } else {
             fh[0] = f[0];
         }
@@ -1456,32 +1502,34 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
         float2 ut = f2(0.f), cc = f2(0.f), Ht = f2(0.f);
         int flagA = 0, flagB = 0;
         if (SYS == SYS_EULER1D) {
+            // the roundings of roe_frame_f32, for both faces at once
+            const int P0 = NP > 1 ? 1 : 0, P1 = NP > 2 ? 2 : 0;
             const float2 ul = make_float2(spr[0][lane + 3], spr[0][lane + 35]);
             const float2 ur_ = make_float2(spr[0][lane + 4], spr[0][lane + 36]);
-            const float2 Hl = make_float2(spr[NP > 1 ? 1 : 0][lane + 3], spr[NP > 1 ? 1 : 0][lane + 35]);
-            const float2 Hr = make_float2(spr[NP > 1 ? 1 : 0][lane + 4], spr[NP > 1 ? 1 : 0][lane + 36]);
-            const float2 sl = make_float2(spr[NP > 2 ? 2 : 0][lane + 3], spr[NP > 2 ? 2 : 0][lane + 35]);
-            const float2 sr = make_float2(spr[NP > 2 ? 2 : 0][lane + 4], spr[NP > 2 ? 2 : 0][lane + 36]);
+            const float2 Hl = make_float2(spr[P0][lane + 3], spr[P0][lane + 35]);
+            const float2 Hr = make_float2(spr[P0][lane + 4], spr[P0][lane + 36]);
+            const float2 sl = make_float2(spr[P1][lane + 3], spr[P1][lane + 35]);
+            const float2 sr = make_float2(spr[P1][lane + 4], spr[P1][lane + 36]);
             const float2 ssum = __fadd2_rn(sl, sr);
             const float2 w = make_float2(rcp_approx(ssum.x), rcp_approx(ssum.y));
             ut = __fmul2_rn(__ffma2_rn(sl, ul, __fmul2_rn(sr, ur_)), w);
             Ht = __fmul2_rn(__ffma2_rn(sl, Hl, __fmul2_rn(sr, Hr)), w);
-            const float2 hu = __fmul2_rn(f2(0.5f), ut);              // u/2
-            const float2 c2 = __fmul2_rn(f2(gm1), __ffma2_rn(f2neg(hu), ut, Ht));
+            const float2 q = __fmul2_rn(__fmul2_rn(f2(0.5f), ut), ut);  // u~^2 / 2
+            const float2 c2 = __fmul2_rn(f2(gm1), __fadd2_rn(Ht, f2neg(q)));
             const float2 rc = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));  // 1/c
             cc = __fmul2_rn(c2, rc);
             const float2 b1 = __fmul2_rn(f2(gm1), __fmul2_rn(rc, rc));
-            const float2 b2 = __fmul2_rn(__fmul2_rn(hu, ut), b1);
-            const float2 uc = __fmul2_rn(ut, rc);
+            const float2 b2 = __fmul2_rn(q, b1);
+            const float2 b1u = __fmul2_rn(b1, ut);
             const float2 hb1 = __fmul2_rn(f2(0.5f), b1);
-            L2[0][0] = __fmul2_rn(f2(0.5f), __fadd2_rn(b2, uc));
-            L2[0][1 % M] = __fmul2_rn(f2(-0.5f), __ffma2_rn(b1, ut, rc));
+            L2[0][0] = __fmul2_rn(f2(0.5f), __ffma2_rn(ut, rc, b2));
+            L2[0][1 % M] = __fmul2_rn(f2(-0.5f), __fadd2_rn(b1u, rc));
             L2[0][2 % M] = hb1;
             L2[1 % M][0] = __fadd2_rn(f2(1.f), f2neg(b2));
-            L2[1 % M][1 % M] = __fmul2_rn(b1, ut);
+            L2[1 % M][1 % M] = b1u;
             L2[1 % M][2 % M] = f2neg(b1);
-            L2[2 % M][0] = __fmul2_rn(f2(0.5f), __fadd2_rn(b2, f2neg(uc)));
-            L2[2 % M][1 % M] = __fmul2_rn(f2(-0.5f), __ffma2_rn(b1, ut, f2neg(rc)));
+            L2[2 % M][0] = __fmul2_rn(f2(0.5f), __ffma2_rn(f2neg(ut), rc, b2));
+            L2[2 % M][1 % M] = __fmul2_rn(f2(-0.5f), __fadd2_rn(b1u, f2neg(rc)));
             L2[2 % M][2 % M] = hb1;
             if (!(c2.x > 0.f)) flagA |= isfinite(c2.x) ? ERR_NONPHYSICAL : ERR_NONFINITE;
             if (!(c2.y > 0.f)) flagB |= isfinite(c2.y) ? ERR_NONPHYSICAL : ERR_NONFINITE;
@@ -1623,9 +1671,8 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
         }
         float2 fh[M];
         if (SYS == SYS_EULER1D) {
-            // R columns: eigenvectors of u-c, u, u+c at the Roe state
+            // the roundings of back_project_f32, for both faces at once
             fh[0] = __fadd2_rn(__fadd2_rn(f[0], f[1 % M]), f[2 % M]);
-            // (a f0 + b f1 + c f2 is evaluated as fma(c, f2, fma(a, f0, b f1)))
             const float2 umc = __fadd2_rn(ut, f2neg(cc)), upc = __fadd2_rn(ut, cc);
             fh[1 % M] = __ffma2_rn(upc, f[2 % M], __ffma2_rn(umc, f[0], __fmul2_rn(ut, f[1 % M])));
             const float2 R20 = __ffma2_rn(f2neg(ut), cc, Ht), R22 = __ffma2_rn(ut, cc, Ht);
@@ -1896,14 +1943,14 @@ cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
-    // FP32 state of a scalar law over the whole domain: face-paired tiles
-    // (advection when a > 0, where alpha = a makes the '-' split vanish).
-    // Their results equal the paired-split kernel's bit for bit.  (Euler
-    // stays on the paired-split kernel: its face-paired form rounds the Roe
-    // frame differently, and one colliding-flow tube of the FP32 robustness
-    // family went non-physical with it.)
+    // FP32 state over the whole domain: face-paired tiles (advection when
+    // a > 0, where alpha = a makes the '-' split vanish).  Their results
+    // equal the paired-split kernel's bit for bit (the Roe frame and back
+    // projection share the roundings of roe_frame_f32/back_project_f32), so
+    // parted launches, slabs and batches, which take the paired-split tiles,
+    // agree with them.
     if (sizeof(S) == 4 && p.tile_lo == 0 && p.tile_hi <= 0 && !p.partial && !p.halo &&
-        ((p.sys == SYS_ADV && p.a > 0.0) || p.sys == SYS_BURGERS)) {
+        ((p.sys == SYS_ADV && p.a > 0.0) || p.sys == SYS_BURGERS || p.sys == SYS_EULER1D)) {
         const int nt2 = (p.n + WT2 - 1) / WT2;
         const int nw2 = warps_per_cta(nt2, false);
         const int res2 = num_sms() * T7_F32_MINB * 4 * (WPB / nw2);

@@ -935,6 +935,217 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
     }
 }
 
+// --------------------------------------------------------------------------
+// FP32 y sweep, persistent: each CTA walks blocks b = blockIdx.x, + gridDim.x,
+// ... (32 columns x 29 rows, as ysweep2d_f32_kernel), and the raw state of
+// its next block is copied into shared memory by cp.async while the current
+// block's faces and epilogue compute, so the staging loads are not waited for
+// in the block's critical path.  The per-cell and per-face arithmetic is that
+// of ysweep2d_f32_kernel, so the results are the same bits.
+// Dynamic shared memory: ry [4][29][33]; gp, gm, pr [4][39][33]; raw
+// [4][39][32]; Delta table [32][8]; reductions [2][WPB].
+// --------------------------------------------------------------------------
+static __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+inline constexpr size_t ysweep_f32p_smem_bytes() {
+    return sizeof(float) * (4 * YB_ROWS * YB_LD + 3 * 4 * YB_STAGE * YB_LD + 4 * YB_STAGE * YB_COLS + 32 * 8 +
+                            2 * WPB);
+}
+
+template <typename S>  // float (the FP32 state) only
+__global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2D p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_ry = reinterpret_cast<float *>(smem_raw);  // [4][29][33]
+    float *s_gp = s_ry + 4 * YB_ROWS * YB_LD;            // [4][39][33]
+    float *s_gm = s_gp + 4 * YB_STAGE * YB_LD;
+    float *s_pr = s_gm + 4 * YB_STAGE * YB_LD;
+    float *s_in = s_pr + 4 * YB_STAGE * YB_LD;           // [4][39][32] raw state of the block
+    float(*s_cf)[8] = reinterpret_cast<float(*)[8]>(s_in + 4 * YB_STAGE * YB_COLS);
+    float *s_red = reinterpret_cast<float *>(s_cf + 32);  // [2][WPB]
+    auto at = [](const float *base, int c, int r, int col) -> float {
+        return base[(c * YB_STAGE + r) * YB_LD + col];
+    };
+
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = p.nx, ny = p.ny;
+    const size_t N = (size_t)nx * ny;
+    const int nbx = (nx + YB_COLS - 1) / YB_COLS, nblocks = nbx * ((ny + YB_ROWS - 1) / YB_ROWS);
+    const float alpha = ctl->alpha_f[p.slot_in][1];
+    const float gamma = p.f_gamma, gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_y, CT = p.f_CT;
+    const float kt = keep_all_factor(CT);
+    const float *Us = static_cast<const float *>(p.Us);
+    const float *R = static_cast<const float *>(p.R);
+    const float *U0 = static_cast<const float *>(p.U0);
+    float *out = static_cast<float *>(p.out);
+    const float idy = 1.f / p.f_dy;
+    const float dtF = p.rhs_mode ? 0.f : (fixed ? p.f_dt_fixed : ctl->dt_f);
+    const bool use_u0 = !p.rhs_mode && p.stage > 0;
+    fill_delta_table(s_cf);
+    // running max(|u|+c), max(|v|+c) of the CTA's output cells, as the bit
+    // patterns of non-negative floats (ordered like the values)
+    int *s_amax = reinterpret_cast<int *>(s_red);
+    if (tid < 2) s_amax[tid] = 0;
+
+    // rows r0-5 .. r0+33 of columns x0 .. x0+31 of block b into s_in (one
+    // 4-byte asynchronous copy per value; rows outside the grid by the
+    // boundary map, columns beyond it skipped)
+    auto copy_block = [&](int b) {
+        const int x0 = (b % nbx) * YB_COLS, r0 = (b / nbx) * YB_ROWS;
+        for (int q = tid; q < YB_STAGE * YB_COLS; q += WPB * 32) {
+            const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col;
+            if (x >= nx) continue;
+            int y = r0 - 5 + r;
+            if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[(size_t)k * N + (size_t)y * nx + x]);
+        }
+        cp_async_commit();
+    };
+
+    int b = blockIdx.x;
+    if (b < nblocks) copy_block(b);
+    for (; b < nblocks; b += gridDim.x) {
+        const int x0 = (b % nbx) * YB_COLS, r0 = (b / nbx) * YB_ROWS;
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- split fluxes and primitives of the staged cells
+        for (int q = tid; q < YB_STAGE * YB_COLS; q += WPB * 32) {
+            const int r = q / YB_COLS, col = q % YB_COLS;
+            if (x0 + col >= nx) continue;
+            float uf[4], pr[4], gp[4], gm[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) uf[k] = s_in[(k * YB_STAGE + r) * YB_COLS + col];
+            cell2d_f32<1>(uf, gm1, alpha, pr, gp, gm);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                s_pr[(k * YB_STAGE + r) * YB_LD + col] = pr[k];
+                s_gp[(k * YB_STAGE + r) * YB_LD + col] = gp[k];
+                s_gm[(k * YB_STAGE + r) * YB_LD + col] = gm[k];
+            }
+        }
+        __syncthreads();
+        // the next block's raw state streams in while this one computes
+        if (b + (int)gridDim.x < nblocks) copy_block(b + gridDim.x);
+
+        // ---- faces down the columns: warp w takes columns w, w+8, w+16, w+24
+        for (int col = warp; col < YB_COLS; col += WPB) {
+            const int x = x0 + col;
+            if (x >= nx) break;
+            const int j = r0 - 2 + lane;
+            float fh[4];
+            unsigned cpk, cmk;
+            int flag = 0;
+            face2d_f32<1>(
+                fh, cpk, cmk, flag, [&](int q, int i) { return at(s_pr, q, i, col); },
+                [&](int cc, int i) { return at(s_gp, cc, i, col); },
+                [&](int cc, int i) { return at(s_gm, cc, i, col); }, s_cf, eps4, CT, kt, gm1, lane);
+            const bool face_out = lane >= 1 && lane <= 30;
+            if (p.rhs_mode && p.masks && face_out && j >= -1 && j <= ny - 1) {
+                uint8_t *ym = p.masks + (size_t)8 * ny * (nx + 1);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    ym[((size_t)k * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)((cpk >> (5 * k)) & 31u);
+                    ym[((size_t)(4 + k) * nx + x) * (ny + 1) + (j + 1)] = (uint8_t)((cmk >> (5 * k)) & 31u);
+                }
+            }
+            if (flag && face_out && j >= -2 && j <= ny) latch_error(ctl, flag, flat_cell(j, x, nx, ny));
+            float fprev[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
+            if (lane >= 2 && lane <= 30) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) s_ry[(k * YB_ROWS + (lane - 2)) * YB_LD + col] = (fprev[k] - fh[k]) * idy;
+            }
+        }
+        __syncthreads();
+
+        // ---- L = Lx + Ly, RK stage, wavespeeds (row-major, coalesced)
+        float mx = 0.f, my = 0.f;
+        constexpr int EB = 2;  // (4 spills in the persistent loop)
+        for (int q0 = tid; q0 < YB_ROWS * YB_COLS; q0 += EB * WPB * 32) {
+            float Rv[EB][4], Uv[EB][4], U0v[EB][4];
+#pragma unroll
+            for (int e = 0; e < EB; e++) {
+                const int q = q0 + e * WPB * 32;
+                const int r = q / YB_COLS, x = x0 + q % YB_COLS, y = r0 + r;
+                if (q < YB_ROWS * YB_COLS && x < nx && y < ny) {
+                    const size_t gi = (size_t)y * nx + x;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        Rv[e][k] = R[(size_t)k * N + gi];
+                        Uv[e][k] = p.rhs_mode ? 0.f : Us[(size_t)k * N + gi];
+                        U0v[e][k] = use_u0 ? U0[(size_t)k * N + gi] : 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < EB; e++) {
+                const int q = q0 + e * WPB * 32;
+                const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col, y = r0 + r;
+                if (!(q < YB_ROWS * YB_COLS && x < nx && y < ny)) continue;
+                const size_t gi = (size_t)y * nx + x;
+                float of[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float rr = Rv[e][k] + s_ry[(k * YB_ROWS + r) * YB_LD + col];
+                    if (p.rhs_mode) {
+                        out[(size_t)k * N + gi] = rr;
+                        continue;
+                    }
+                    float o;
+                    const float v = fmaf(dtF, rr, Uv[e][k]);
+                    if (p.stage == 0) {
+                        o = v;
+                    } else if (p.stage == 1) {
+                        o = fmaf(0.75f, U0v[e][k], 0.25f * v);
+                    } else {
+                        const float u0 = U0v[e][k];
+                        o = fmaf(2.0f / 3.0f, v - u0, u0);
+                    }
+                    out[(size_t)k * N + gi] = o;
+                    of[k] = o;
+                }
+                if (!p.rhs_mode) {
+                    int wflag = 0;
+                    float sx, sy;
+                    wavespeed2d<float>(of, gm1, gamma, sx, sy, &wflag);
+                    if (wflag) latch_error(ctl, wflag, (int)gi);
+                    mx = fmaxf(mx, sx);
+                    my = fmaxf(my, sy);
+                }
+            }
+        }
+        if (!p.rhs_mode) {
+            mx = warp_max(mx);
+            my = warp_max(my);
+            if (lane == 0) {
+                atomicMax(&s_amax[0], __float_as_int(mx));
+                atomicMax(&s_amax[1], __float_as_int(my));
+            }
+        }
+        __syncthreads();  // s_ry and the staged arrays are rewritten by the next block
+    }
+    if (!p.rhs_mode) {
+        __syncthreads();
+        if (tid == 0) {
+            const float vx = __int_as_float(s_amax[0]), vy = __int_as_float(s_amax[1]);
+            const int so = (p.stage + 1) % 3;
+            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)vx));
+            atomicMax(&ctl->amax[so][1], (unsigned long long)__double_as_longlong((double)vy));
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true);
+        }
+    }
+}
+
 template <typename S>
 cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
     const int ntx = (p.nx + WT - 1) / WT;
@@ -945,6 +1156,16 @@ cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
     xsweep2d_f32_kernel<S><<<(int)gx, WPB * 32, 0, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(S) == 4) {
+        // FP32 state: persistent CTAs (two per SM) with the next block prefetched
+        const size_t smem = ysweep_f32p_smem_bytes();
+        e = cudaFuncSetAttribute(ysweep2d_f32p_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const long nb = (long)((p.nx + YB_COLS - 1) / YB_COLS) * ((p.ny + YB_ROWS - 1) / YB_ROWS);
+        const long cap = (long)num_sms() * 2;
+        ysweep2d_f32p_kernel<S><<<(int)(nb < cap ? nb : cap), WPB * 32, smem, st>>>(p);
+        return cudaGetLastError();
+    }
     const size_t smem = ysweep_f32_smem_bytes<S>();
     e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
