@@ -56,11 +56,11 @@ FLOPS_PER_CELL_STAGE = {"f32": 808.0, "f64": 776.0}
 # packed f32x2 FMA = 4, packed add/mul = 2, scalar add/mul = 1; the keep-all
 # shortcut skips most of the cutoff, so this is below the algorithmic count);
 # None when not captured for the current kernel.
-EXEC_FLOPS_PER_CELL_STAGE = {"f32": None, "f64": None}
+EXEC_FLOPS_PER_CELL_STAGE = {"f32": 584.4, "f64": 812.0}
 # DRAM bytes per stage launch per cell measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, averaged over the three stage launches of one RK3
 # step at N = 16,777,600) for the current kernels; None when not captured.
-TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.49, "f64": 61.80}
+TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.57, "f64": None}
 
 
 def peaks():
