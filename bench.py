@@ -564,7 +564,7 @@ def bench_strong(args, torch, B, U0, dx, dist, world, rank):
     from paper_1808_00037_gb300 import decomp
     lo, hi = decomp.partition(U0.shape[1], world, rank)
     ctx = B.Context(B.T7_EULER1D, hi - lo, dx, prec=B.T7_F32, gamma=GAMMA)
-    slab = decomp.Slab(decomp.CudaSlab1D(ctx), torch.tensor(U0[:, lo:hi], dtype=torch.float32, device="cuda"))
+    slab = decomp.Slab(decomp.CudaSlab(ctx), torch.tensor(U0[:, lo:hi], dtype=torch.float32, device="cuda"))
     comm = decomp.RankSlabs(slab, periodic=False)
     dt_of = decomp.cfl_dt_1d(dx, CFL)
     decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.warmup)
@@ -583,6 +583,52 @@ def bench_strong(args, torch, B, U0, dx, dist, world, rank):
             "steps": steps, "scaling": "strong", "cells_total": int(U0.shape[1]),
             "timing": "host wall clock between barriers and device synchronisations (max over ranks)",
             "parallelism": f"slab decomposition over {world} ranks, NCCL halos + all-reduce(max) of alpha"}
+
+
+def bench_slabs_local(args, torch, B, U1, dx1, nslabs=2):
+    """The slab decomposition on one GPU: the 16.8M-cell tiled Shu-Osher
+    domain (1D) and the 2048^2 quadrant domain (2D, cut along y) in `nslabs`
+    slabs, each with its own context and CUDA stream, 4-cell (row) halos
+    filled by device-local copies and the alphas of every stage all-reduced
+    (a max over the slabs) on the device (paper_1808_00037_gb300.decomp).
+    FP32.  The rate beside the unsplit kernels' is the cost of the
+    decomposition machinery itself (halo copies, per-stage reductions, one
+    host read of dt per step).  Host wall clock between device
+    synchronisations."""
+    from paper_1808_00037_gb300 import decomp
+    out = {"workload": f"{nslabs} slabs on {nslabs} CUDA streams of one GPU, FP32",
+           "timing": "host wall clock between device synchronisations"}
+    U2, dx2, dy2, _ = I.quadrants_2d(2024, 2048, 2048)
+    cases = (("euler1d", U1, B.T7_EULER1D, decomp.cfl_dt_1d(dx1, CFL), 1),
+             ("euler2d", U2, B.T7_EULER2D, decomp.cfl_dt_2d(dx2, dy2, 0.4), 2))
+    for name, U, sysid, dt_of, nalpha in cases:
+        rows = U.shape[1]
+        slabs = []
+        for r in range(nslabs):
+            lo, hi = decomp.partition(rows, nslabs, r)
+            st = torch.cuda.Stream()
+            if sysid == B.T7_EULER2D:
+                ctx = B.Context(sysid, U.shape[2], dx2, ny=hi - lo, dy=dy2, prec=B.T7_F32, bc=(1, 1, 1, 1),
+                                gamma=GAMMA, stream=st)
+            else:
+                ctx = B.Context(sysid, hi - lo, dx1, prec=B.T7_F32, bc=(1, 1, 0, 0), gamma=GAMMA, stream=st)
+            Ul = torch.tensor(U[:, lo:hi], dtype=torch.float32, device="cuda")
+            slabs.append(decomp.Slab(decomp.CudaSlab(ctx), Ul, nalpha=nalpha))
+        comm = decomp.LocalSlabs(slabs, periodic=False)
+        decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, _ = decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        cells = U[0].size
+        out[name] = {"value": cells * steps / el / 1e9, "unit": "Gcell-steps/s", "ms_per_step": el / steps * 1e3,
+                     "steps": steps, "cells": int(cells)}
+        for sl in slabs:
+            sl.backend.ctx.close()
+        del slabs, comm
+        torch.cuda.empty_cache()
+    return out
 
 
 def time_run(torch, ctx, U, steps, dist, world, sampler_index=None):
@@ -632,7 +678,7 @@ def main():
     ap.add_argument("--no-strong", action="store_true")
     ap.add_argument("--steps-2d", type=int, default=20)
     ap.add_argument("--f64-steps-2d", type=int, default=3)
-    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint", "advection"], default=None,
+    ap.add_argument("--only", choices=["f32", "f64", "2d", "batch", "adjoint", "advection", "slabs"], default=None,
                     help="time one 1D precision, or only the 2D case (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -676,6 +722,10 @@ def main():
         return 0
     U0, dx = I.shu_osher(N1, tiles=args.tiles)
     n = U0.shape[1]
+    if args.only == "slabs":
+        if rank == 0:
+            print(json.dumps({"only": "slabs", **bench_slabs_local(args, torch, B, U0, dx)}), flush=True)
+        return 0
     hbm_peak, peak_kind = peaks()
     alu = alu_peaks(B)
     res = {}
@@ -755,6 +805,11 @@ def main():
     # cases of every form), on rank 0
     acc = None if (args.no_accuracy or rank != 0) else bench_accuracy(args, torch, B)
     strong = None if (world == 1 or args.no_strong) else bench_strong(args, torch, B, U0, dx, dist, world, rank)
+    slabs1 = None if (world > 1 or args.no_strong) else bench_slabs_local(args, torch, B, U0, dx)
+    if slabs1:
+        slabs1["euler1d"]["vs_unsplit"] = slabs1["euler1d"]["value"] / res["f32"]["value"]
+        if res2d:
+            slabs1["euler2d"]["vs_unsplit"] = slabs1["euler2d"]["value"] / res2d["f32"]["value"]
 
     if rank != 0:
         return 0
@@ -775,7 +830,7 @@ def main():
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
         "f64": res["f64"], "mixed": resm, "teno5": res5, "advection": resv, "accuracy": acc, "euler2d": res2d,
-        "batch": resb, "adjoint": resa, "strong": strong, "alu_peaks": alu,
+        "batch": resb, "adjoint": resa, "strong": strong, "slabs_1gpu": slabs1, "alu_peaks": alu,
         "cpu_baseline": cpu,
     }
     # compact FP64 figures at the end of the line, where a reader of its tail finds them

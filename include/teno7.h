@@ -236,7 +236,8 @@ t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const doubl
 t7_status t7_batch_autotune(t7_ctx *ctx, const void *U, const int64_t *offsets, const double *dx, int ntubes,
                             double cfl, int trial_steps, int *group_out, float *ms_out);
 
-/* Slabs of a decomposed 1D domain (one per rank, or per stream).  The scheme
+/* Slabs of a decomposed 1D domain, or of a 2D domain cut along y (one per
+ * rank, or per stream).  The scheme
  * is the conservative form Eq. app, whose stencils reach 4 cells per side
  * (the RHS at cell i depends on cells i-4 .. i+4: faces i-1/2 and i+1/2, their
  * 7-point polynomials and their neighbour faces' cutoff bits, Eq. vec), with
@@ -247,8 +248,16 @@ t7_status t7_batch_autotune(t7_ctx *ctx, const void *U, const int64_t *offsets, 
  * or from the domain's boundary condition at its real ends) before a call
  * reads them.  alpha values are device doubles, so that a collective
  * (all-reduce max over the slabs) can feed them without a host round trip.
- * The context is created for the slab (nx = its cell count); its bc[] is
- * not used by these calls.  Async.
+ * 2D Euler (sys = T7_EULER2D): the slab is ny rows of the domain's nx
+ * columns and every array is [4][ny + 8][nx], row 0 at row offset 4; the 4
+ * rows before and after are the halos (the y stencils reach 4 rows per side
+ * by the same argument, dimension by dimension).  The x direction is whole,
+ * so the context's bc[0..1] apply in x; bc[2..3] are not used.  alpha is two
+ * device doubles (alpha_x = max(|u| + c), alpha_y = max(|v| + c)), and so is
+ * alpha_out; dUdt is [4][ny][nx] and the masks as t7_euler_rhs's for the
+ * slab's grid.
+ * The context is created for the slab (nx = its cell count; 2D: nx columns,
+ * ny = its row count); in 1D its bc[] is not used by these calls.  Async.
  * t7_slab_alpha: max_i (|u_i| + c_i) over the slab's own cells into the
  *   device double *alpha_out (reads only the interior of U).
  * t7_slab_rhs: L(U) = -(F_{i+1/2} - F_{i-1/2})/dx (Eq. app) of the slab's
@@ -283,12 +292,15 @@ t7_status t7_slab_stage(t7_ctx *ctx, int k, const void *Us, const void *U0, void
  * exits.  Sizes whose scratch does not fit (2 x m x nx x element size plus
  * 256 bytes, each buffer rounded up to 256 bytes) are rejected with T7_EINVAL
  * before any GPU work.  The first call on each device looks up that device's
- * address of the array (with the device current), so make that first call
- * before any stream capture.  Every call reuses the array and clears the part
- * that must start at zero; calls that overlap on the GPU (on different
+ * address of the array (with the device current; concurrent first calls from
+ * several host threads are safe).  Every call reuses the array and clears the
+ * part that must start at zero; calls that overlap on the GPU (on different
  * streams, or from several host threads) race on it.  Results equal
- * t7_rk3_step's.  Synchronises the stream and returns any non-physical or
- * non-finite state met.  errbuf (nullable) receives a message. */
+ * t7_rk3_step's.  Every call copies its status word to the host and
+ * synchronises the stream, so it must never be made on a stream that is being
+ * captured into a CUDA graph (the capture would fail).  Returns any
+ * non-physical or non-finite state met.  errbuf (nullable) receives a
+ * message. */
 #define T7_STATIC_SCRATCH_BYTES (16u << 20)
 t7_status t7_rk3_step_static(const t7_grid *grid, void *U, double dt, void *stream, char *errbuf, size_t errlen);
 

@@ -183,17 +183,22 @@ class Context:
         self._check(self.lib.t7_cfl_dt(self.h, _ptr(self._dev(U)), cfl, ctypes.byref(dt)), "t7_cfl_dt")
         return dt.value
 
-    # -- slabs of a decomposed 1D domain: padded arrays [m, nx + 8], device alphas
+    # -- slabs of a decomposed domain: padded arrays [m, nx + 8] (2D [4, ny + 8, nx]), device alphas
     def _padded(self, t):
         t = self._dev(t)
-        if t.shape[-1] != self.nx + 8 or t.numel() != self.m * (self.nx + 8):
+        if self.sys == T7_EULER2D:
+            shape = (4, self.ny + 8, self.nx)
+            if tuple(t.shape) != shape:
+                raise ValueError(f"expected a padded slab array {list(shape)}")
+        elif t.shape[-1] != self.nx + 8 or t.numel() != self.m * (self.nx + 8):
             raise ValueError(f"expected a padded slab array [{self.m}, {self.nx + 8}]")
         return t
 
     def _alpha(self, a):
         torch = self._torch
-        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.numel() >= 1):
-            raise ValueError("alpha values are CUDA float64 tensors")
+        na = 2 if self.sys == T7_EULER2D else 1
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.numel() >= na):
+            raise ValueError(f"alpha values are CUDA float64 tensors of {na} element(s)")
         return a
 
     def slab_alpha(self, U, alpha_out):
@@ -205,14 +210,26 @@ class Context:
 
     def slab_rhs(self, U, alpha, out=None, want_masks: bool = False):
         """L(U) of the slab's cells (padded U, halos filled) with the global
-        alpha (device double tensor); returns dU/dt [m, nx] (and the masks)."""
+        alpha (device double tensor: 2D alpha_x, alpha_y); returns dU/dt
+        [m, nx] (2D [4, ny, nx]) and, if asked, the masks as euler_rhs's."""
         torch = self._torch
         U = self._padded(U)
-        out = torch.empty((self.m, self.nx), dtype=U.dtype, device=U.device) if out is None else self._dev(out)
-        masks = torch.empty((2, self.m, self.nx + 1), dtype=torch.uint8, device=U.device) if want_masks else None
+        two_d = self.sys == T7_EULER2D
+        shape = (4, self.ny, self.nx) if two_d else (self.m, self.nx)
+        out = torch.empty(shape, dtype=U.dtype, device=U.device) if out is None else self._dev(out)
+        masks = None
+        if want_masks:
+            nx, ny = self.nx, self.ny
+            n = 8 * ny * (nx + 1) + 8 * nx * (ny + 1) if two_d else 2 * self.m * (nx + 1)
+            masks = torch.empty(n, dtype=torch.uint8, device=U.device)
         self._check(self.lib.t7_slab_rhs(self.h, _ptr(U), _ptr(self._alpha(alpha)), _ptr(out), _ptr(masks)),
                     "t7_slab_rhs")
-        return (out, masks) if want_masks else out
+        if not want_masks:
+            return out
+        if two_d:
+            k = 8 * self.ny * (self.nx + 1)
+            return out, (masks[:k].view(2, 4, self.ny, self.nx + 1), masks[k:].view(2, 4, self.nx, self.ny + 1))
+        return out, masks.view(2, self.m, self.nx + 1)
 
     def slab_stage(self, k: int, Us, U0, out, alpha, dt: float, alpha_out=None):
         """SSP-RK3 stage k of fixed dt on padded slab arrays (see t7_slab_stage)."""

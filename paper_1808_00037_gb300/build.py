@@ -1,8 +1,9 @@
 """Build libteno7.so (the CUDA kernels + C ABI) in-tree for sm_103a with nvcc.
 
 Each translation unit is compiled in parallel, then linked into one shared
-library next to this file.  teno7_f64.cu is compiled with -fmad=false so that
-the FP64 path evaluates every expression operation by operation.
+library next to this file.  teno7_f64.cu and teno7_slab2d_f64.cu are compiled
+with -fmad=false so that the FP64 path evaluates every expression operation by
+operation.
 """
 from __future__ import annotations
 
@@ -25,6 +26,8 @@ UNITS = {
     "teno7_f32.cu": [],
     "teno7_static.cu": [],
     "teno7_probe.cu": [],
+    "teno7_slab2d_f64.cu": ["-fmad=false"],
+    "teno7_slab2d_f32.cu": [],
 }
 
 

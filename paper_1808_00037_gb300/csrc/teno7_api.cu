@@ -499,8 +499,35 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
 // alpha passed in as a device value (see include/teno7.h).
 static t7_status slab_check(t7_ctx *c, const char *what) {
     if (!c) return T7_EINVAL;
-    if (!is_1d(c->g.sys)) return fail(c, T7_EINVAL, "%s: a 1D system only", what);
+    if (!is_1d(c->g.sys) && c->g.sys != T7_EULER2D) return fail(c, T7_EINVAL, "%s: not a slab system", what);
     return T7_OK;
+}
+
+// 2D slab: offset (bytes) of row 0 of a padded array, and its variable stride
+static size_t slab2d_row0(const t7_ctx *c) { return (size_t)t7::HALO_CELLS * c->g.nx * c->esize; }
+static size_t slab2d_stride(const t7_ctx *c) { return (size_t)c->g.nx * (c->g.ny + 2 * t7::HALO_CELLS); }
+
+static const void *off_c(const void *p, size_t bytes) {
+    return p ? static_cast<const void *>(static_cast<const char *>(p) + bytes) : nullptr;
+}
+
+static cudaError_t stage2d_slab(t7_ctx *c, const t7::Stage2D &p) {
+    if (c->g.prec == T7_MIXED) return t7::launch_stage2d_slab_mixed(p, c->stream);
+    return c->g.prec == T7_F64 ? t7::launch_stage2d_slab_f64(p, c->stream) : t7::launch_stage2d_slab_f32(p, c->stream);
+}
+
+// one RHS (rhs_mode) or RK stage of a 2D slab; out is padded in RK mode
+static t7::Stage2D slab2d_params(t7_ctx *c, const void *Us, const void *U0, void *out, int rhs_mode,
+                                 const double *alpha_in) {
+    const size_t row0 = slab2d_row0(c);
+    void *o = rhs_mode ? out : static_cast<char *>(out) + row0;
+    t7::Stage2D p = stage2d_params(c, off_c(Us, row0), off_c(U0, row0), o, rhs_mode ? out : c->R);
+    p.halo = 1;
+    p.sv = slab2d_stride(c);
+    p.svo = rhs_mode ? (size_t)c->g.nx * c->g.ny : p.sv;
+    p.alpha_in = alpha_in;
+    p.rhs_mode = rhs_mode;
+    return p;
 }
 
 static t7::Stage1D slab_params(t7_ctx *c, const void *Us, const void *U0, void *out, const double *alpha_in) {
@@ -512,8 +539,22 @@ static t7::Stage1D slab_params(t7_ctx *c, const void *Us, const void *U0, void *
 
 // alpha of the slab's cells (the padded array's interior) into *alpha_out
 static cudaError_t slab_alpha_launch(t7_ctx *c, const void *U, double *alpha_out) {
-    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[0][0], 0, sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[0][0], 0, 2 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
+    if (c->g.sys == T7_EULER2D) {
+        t7::Alpha2D a;
+        memset(&a, 0, sizeof(a));
+        a.U = off_c(U, slab2d_row0(c));
+        a.nx = c->g.nx;
+        a.ny = c->g.ny;
+        a.stride = slab2d_stride(c);
+        a.gamma = c->g.gamma;
+        a.ctl = c->ctl;
+        a.slot = 0;
+        a.alpha_rec = alpha_out;
+        return c->g.prec != T7_F32 ? t7::launch_alpha2d_slab_f64(a, c->stream)
+                                   : t7::launch_alpha2d_slab_f32(a, c->stream);
+    }
     t7::Alpha1D a;
     memset(&a, 0, sizeof(a));
     a.U = static_cast<const char *>(U) + t7::HALO_CELLS * c->esize;
@@ -543,6 +584,13 @@ extern "C" t7_status t7_slab_rhs(t7_ctx *c, const void *U, const double *alpha, 
     t7_status st = slab_check(c, "t7_slab_rhs");
     if (st) return st;
     if (!U || !alpha || !dUdt) return fail(c, T7_EINVAL, "t7_slab_rhs: null pointer");
+    if (c->g.sys == T7_EULER2D) {
+        t7::Stage2D p = slab2d_params(c, U, nullptr, dUdt, 1, alpha);
+        p.masks = masks;
+        cudaError_t e = stage2d_slab(c, p);
+        if (e != cudaSuccess) return cuda_fail(c, e, "slab rhs launch");
+        return T7_OK;
+    }
     t7::Stage1D p = slab_params(c, U, nullptr, dUdt, alpha);
     p.rhs_mode = 1;
     p.masks = masks;
@@ -561,8 +609,19 @@ extern "C" t7_status t7_slab_stage(t7_ctx *c, int k, const void *Us, const void 
     if (Us == out) return fail(c, T7_EINVAL, "t7_slab_stage: the stage input may not alias the output");
     // the slot this launch reduces the output's alpha into starts at zero
     const int so = (k + 1) % 3;
-    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[so][0], 0, sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(&c->ctl->amax[so][0], 0, 2 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "slab stage slot");
+    if (c->g.sys == T7_EULER2D) {
+        t7::Stage2D p = slab2d_params(c, Us, k == 0 ? nullptr : U0, out, 0, alpha);
+        p.stage = k;
+        p.dt_fixed = dt;
+        p.f_dt_fixed = (float)dt;
+        p.slot_in = k;
+        p.alpha_rec = alpha_out;
+        e = stage2d_slab(c, p);
+        if (e != cudaSuccess) return cuda_fail(c, e, "slab stage launch");
+        return T7_OK;
+    }
     t7::Stage1D p = slab_params(c, Us, k == 0 ? nullptr : U0, out, alpha);
     p.rhs_mode = 0;
     p.stage = k;

@@ -89,14 +89,26 @@ struct Stage2D {
     DevCtl *ctl;
     int slot_in;
     float f_dx, f_dy, f_eps_x, f_eps_y, f_CT, f_gamma, f_gm1, f_dt_fixed;
+    // Slab of a domain cut along y (the launch_*_slab_* entry points only):
+    // Us, U0 and (RK mode) out hold HALO_CELLS padding rows per side
+    // ([4][ny + 2 HALO_CELLS][nx]) and point at row 0, sv and svo are the
+    // strides between conserved variables of Us / U0 and of out (R is always
+    // [4][ny][nx]); the y stencils read the padding, which the caller has
+    // filled, instead of applying the y boundary condition
+    size_t sv, svo;
+    int halo;
+    const double *alpha_in;  // nullable: [2] alpha_x, alpha_y of Us instead of the control block's
+    double *alpha_rec;       // nullable: receives [2] alpha_x, alpha_y of the output (RK mode)
 };
 
 struct Alpha2D {
     const void *U;
     int nx, ny;
+    size_t stride;  // slab mode: between conserved variables
     double gamma;
     DevCtl *ctl;
     int slot;
+    double *alpha_rec;  // nullable: receives [2] the finished alpha_x, alpha_y
 };
 
 cudaError_t launch_stage2d_f64(const Stage2D &p, cudaStream_t s);
@@ -104,6 +116,12 @@ cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s);
 cudaError_t launch_stage2d_mixed(const Stage2D &p, cudaStream_t s);  // FP64 state, FP32 reconstruction
 cudaError_t launch_alpha2d_f64(const Alpha2D &p, cudaStream_t s);
 cudaError_t launch_alpha2d_f32(const Alpha2D &p, cudaStream_t s);
+// slab mode (halo, alpha_in, alpha_rec, sv / svo / stride honoured)
+cudaError_t launch_stage2d_slab_f64(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_stage2d_slab_f32(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_stage2d_slab_mixed(const Stage2D &p, cudaStream_t s);
+cudaError_t launch_alpha2d_slab_f64(const Alpha2D &p, cudaStream_t s);
+cudaError_t launch_alpha2d_slab_f32(const Alpha2D &p, cudaStream_t s);
 
 // A ragged batch of independent 1D Euler tubes, concatenated variable-major
 // ([3][Ntot]); each tube runs its own SSP-RK3 loop to t_end inside one

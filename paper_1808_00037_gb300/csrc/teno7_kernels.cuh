@@ -38,6 +38,9 @@
 
 namespace t7 {
 
+// CTA tiles of the plain scalar reconstruction kernel (recon_kernel, the face
+// values alone, without the flux difference), which exchanges cutoff words
+// through shared memory; the stage kernels use the warp tiles described above.
 constexpr int NT = 256;         // faces (threads) per tile
 constexpr int TILE = NT - 3;    // cells updated per tile
 constexpr int HALO = 5;         // staged cells start at s - HALO
@@ -346,7 +349,10 @@ __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zer
     const double ay = two_d ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][1], 0ull)) : 0.0;
     ctl->alpha_f[slot_out][0] = (float)a;
     ctl->alpha_f[slot_out][1] = (float)ay;
-    if (alpha_rec) *alpha_rec = a;  // recorded for a later adjoint
+    if (alpha_rec) {  // recorded for a later adjoint, or for a slab's all-reduce
+        alpha_rec[0] = a;
+        if (two_d) alpha_rec[1] = ay;
+    }
     ctl->amax[zero_slot][0] = 0ull;
     ctl->amax[zero_slot][1] = 0ull;
     if (end_of_step) {

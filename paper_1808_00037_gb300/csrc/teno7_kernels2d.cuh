@@ -172,19 +172,32 @@ __device__ __forceinline__ void cell2d(const T U[4], T gm1, T alpha, T prim[4], 
 }
 
 // max(|u|+c) and max(|v|+c) of one cell; flags non-physical / non-finite.
+// In FP32 every rounding is written out (no contraction left to the
+// compiler), so that every instantiation of a kernel gives the same bits.
 template <typename T>
 __device__ __forceinline__ void wavespeed2d(const T U[4], T gm1, T gamma, T &sx, T &sy, int *flag) {
     const T u = U[1] / U[0];
     const T v = U[2] / U[0];
-    const T p = gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
-    const T c = sq_root(gamma * p / U[0]);
+    T p, c;
+    if constexpr (sizeof(T) == 4) {
+        p = __fmul_rn(gm1, __fmaf_rn(-0.5f, __fmaf_rn(U[1], u, __fmul_rn(U[2], v)), U[3]));
+        c = sqrtf(__fdiv_rn(__fmul_rn(gamma, p), U[0]));
+    } else {
+        p = gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+        c = sq_root(gamma * p / U[0]);
+    }
     // a non-finite cell is reported as such; a finite one needs rho > 0, p > 0
     if (!isfinite(U[0]) || !isfinite(U[1]) || !isfinite(U[2]) || !isfinite(U[3]))
         *flag |= ERR_NONFINITE;
     else if (!(U[0] > T(0)) || !(p > T(0)))
         *flag |= ERR_NONPHYSICAL;
-    sx = absval(u) + c;
-    sy = absval(v) + c;
+    if constexpr (sizeof(T) == 4) {
+        sx = __fadd_rn(fabsf(u), c);
+        sy = __fadd_rn(fabsf(v), c);
+    } else {
+        sx = absval(u) + c;
+        sy = absval(v) + c;
+    }
 }
 
 template <typename T>
@@ -196,10 +209,50 @@ __device__ __forceinline__ T alpha_of(const DevCtl *ctl, int slot, int dir) {
     }
 }
 
+// Slab mode of the 2D kernels (template argument HALO; see Stage2D.halo).
+// The instantiations without it are the whole-domain kernels.
+//
+// Source row of staged row y of a y sweep: the grid's own rows as they are;
+// rows outside it by the y boundary condition, or, in a slab, from the
+// padding rows, those beyond the padding clamped into it (they feed only the
+// polynomials of faces 0 and 31 of a tile, whose fluxes no updated cell uses).
+template <bool HALO>
+__device__ __forceinline__ int y_row(int y, const Stage2D &p) {
+    if constexpr (HALO) {
+        if (y >= 0 && y < p.ny) return y;
+        return y < -HALO_CELLS ? -HALO_CELLS : (y >= p.ny + HALO_CELLS ? p.ny + HALO_CELLS - 1 : y);
+    } else {
+        if (y < 0 || y >= p.ny) y = ghost_map(y, p.ny, p.bc[2], p.bc[3]);
+        return y;
+    }
+}
+
+// Offset of value (k, y, x) of a state array with variable stride sv (in a
+// slab y may be negative: the padding rows precede row 0).
+template <bool HALO>
+__device__ __forceinline__ auto st_at(int k, size_t sv, int y, int nx, int x) {
+    if constexpr (HALO) {
+        return (ptrdiff_t)k * (ptrdiff_t)sv + (ptrdiff_t)y * nx + x;
+    } else {
+        return (size_t)k * sv + (size_t)y * nx + x;
+    }
+}
+
+// alpha of the stage input in direction dir: the slab's global value, or the
+// control block's
+template <typename T, bool HALO>
+__device__ __forceinline__ T alpha2d_in(const Stage2D &p, const DevCtl *ctl, int dir) {
+    if constexpr (HALO) {
+        return T(p.alpha_in[dir]);
+    } else {
+        return alpha_of<T>(ctl, p.slot_in, dir);
+    }
+}
+
 // --------------------------------------------------------------------------
 // x sweep: R = Lx(U), warp tiles of 29 cells along rows.
 // --------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool HALO>
 __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) {
     __shared__ T s_gp[WPB][4][WC];
     __shared__ T s_gm[WPB][4][WC];
@@ -210,7 +263,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
     if (!p.rhs_mode && !fixed && !ctl->active) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = lane; q < 91; q += 32) s_coef[warp][q] = coef<T>(q);
-    const T alpha = alpha_of<T>(ctl, p.slot_in, 0);
+    const T alpha = alpha2d_in<T, HALO>(p, ctl, 0);
     const T gm1 = pick<T>(p.gamma - 1.0, p.f_gm1);
     const T eps = pick<T>(p.eps_x, p.f_eps_x), CT = pick<T>(p.CT, p.f_CT);
     const T kt = keep_all_factor(CT);
@@ -218,6 +271,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
     T *R = static_cast<T *>(p.R);
     const int nx = p.nx, ny = p.ny;
     const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N;
     const int ntx = (nx + WT - 1) / WT;
     const long ntiles = (long)ntx * ny;
     T (*sgp)[WC] = s_gp[warp];
@@ -233,7 +287,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
             if (gi < 0 || gi >= nx) gi = ghost_map(gi, nx, p.bc[0], p.bc[1]);
             T U[4], pr[4], gp[4], gm[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) U[k] = row[(size_t)k * N + gi];
+            for (int k = 0; k < 4; k++) U[k] = row[(size_t)k * sv + gi];
             cell2d<T, 0>(U, gm1, alpha, pr, gp, gm);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -293,7 +347,7 @@ constexpr size_t ysweep_smem_bytes() {
     return sizeof(T) * (3 * 4 * YB_STAGE * YB_LD + 4 * YB_ROWS * YB_LD + 92) + 2 * WPB * sizeof(T);
 }
 
-template <typename T>
+template <typename T, bool HALO>
 __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -311,8 +365,9 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
     const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N, svo = HALO ? p.svo : N;
     const int x0 = blockIdx.x * YB_COLS, r0 = blockIdx.y * YB_ROWS;
-    const T alpha = alpha_of<T>(ctl, p.slot_in, 1);
+    const T alpha = alpha2d_in<T, HALO>(p, ctl, 1);
     const T gamma = pick<T>(p.gamma, p.f_gamma), gm1 = pick<T>(p.gamma - 1.0, p.f_gm1);
     const T eps = pick<T>(p.eps_y, p.f_eps_y), CT = pick<T>(p.CT, p.f_CT);
     const T kt = keep_all_factor(CT);
@@ -324,10 +379,10 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
         const int r = idx / YB_COLS, col = idx % YB_COLS, x = x0 + col;
         if (x >= nx) continue;
         int y = r0 - 5 + r;
-        if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
+        y = y_row<HALO>(y, p);
         T U[4], pr[4], gp[4], gm[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) U[k] = Us[(size_t)k * N + (size_t)y * nx + x];
+        for (int k = 0; k < 4; k++) U[k] = Us[st_at<HALO>(k, sv, y, nx, x)];
         cell2d<T, 1>(U, gm1, alpha, pr, gp, gm);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -402,23 +457,23 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
         for (int k = 0; k < 4; k++) {
             const T rr = R[(size_t)k * N + g] + s_ry[(k * YB_ROWS + r) * YB_LD + col];
             if (p.rhs_mode) {
-                out[(size_t)k * N + g] = rr;
+                out[(size_t)k * svo + g] = rr;
                 continue;
             }
-            const T us = Us[(size_t)k * N + g];
+            const T us = Us[(size_t)k * sv + g];
             if (p.stage == 0) {
                 o[k] = us + dtT * rr;
             } else if (p.stage == 1) {
-                o[k] = T(0.75) * U0[(size_t)k * N + g] + T(0.25) * (us + dtT * rr);
+                o[k] = T(0.75) * U0[(size_t)k * sv + g] + T(0.25) * (us + dtT * rr);
             } else {
                 if constexpr (sizeof(T) == 8) {
-                    o[k] = T(1.0 / 3.0) * U0[(size_t)k * N + g] + T(2.0 / 3.0) * (us + dtT * rr);
+                    o[k] = T(1.0 / 3.0) * U0[(size_t)k * sv + g] + T(2.0 / 3.0) * (us + dtT * rr);
                 } else {
-                    const T u0 = U0[(size_t)k * N + g];
+                    const T u0 = U0[(size_t)k * sv + g];
                     o[k] = fmaf(2.0f / 3.0f, (us + dtT * rr) - u0, u0);
                 }
             }
-            out[(size_t)k * N + g] = o[k];
+            out[(size_t)k * svo + g] = o[k];
         }
         if (!p.rhs_mode) {
             int wflag = 0;
@@ -446,24 +501,25 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)vx));
             atomicMax(&ctl->amax[so][1], (unsigned long long)__double_as_longlong((double)vy));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true,
+                          HALO ? p.alpha_rec : nullptr);
         }
     }
 }
 
 // alpha (both directions) of a 2D state into ctl->amax[slot][0..1].
-template <typename T>
+template <typename T, bool HALO>
 __global__ void __launch_bounds__(256) alpha2d_kernel(const Alpha2D p) {
     __shared__ T s_red[2][8];
     const T *U = static_cast<const T *>(p.U);
     const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0);
-    const size_t N = (size_t)p.nx * p.ny;
+    const size_t N = (size_t)p.nx * p.ny, sv = HALO ? p.stride : N;
     T mx = T(0), my = T(0);
     int flag = 0, first = 0x7fffffff;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
         T Uc[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) Uc[k] = U[(size_t)k * N + i];
+        for (int k = 0; k < 4; k++) Uc[k] = U[(size_t)k * sv + i];
         int f = 0;
         T sx, sy;
         wavespeed2d<T>(Uc, gm1, gamma, sx, sy, &f);
@@ -490,7 +546,7 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const Alpha2D p) {
         }
         atomicMax(&p.ctl->amax[p.slot][0], (unsigned long long)__double_as_longlong((double)vx));
         atomicMax(&p.ctl->amax[p.slot][1], (unsigned long long)__double_as_longlong((double)vy));
-        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true, true);
+        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true, true, HALO ? p.alpha_rec : nullptr);
     }
 }
 
@@ -508,31 +564,35 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const Alpha2D p) {
 // ==========================================================================
 
 // Prims (normal velocity, tangential velocity, H, sqrt(rho)) and split fluxes
-// of one cell along DIR, FP32.
+// of one cell along DIR, FP32.  Here and in face2d_f32 every rounding is
+// written out (__fmaf_rn / __fmul_rn / __fadd_rn: nothing is left for the
+// compiler to contract), so the whole-domain and slab instantiations of the
+// sweeps, and any later change around them, give the same bits.
 template <int DIR>
 __device__ __forceinline__ void cell2d_f32(const float U[4], float gm1, float alpha, float pr[4], float gp[4],
                                            float gm[4]) {
     const float ri = rcp_approx(U[0]);
-    const float u = U[1] * ri, v = U[2] * ri;
-    const float p = gm1 * (U[3] - 0.5f * (U[1] * u + U[2] * v));
+    const float u = __fmul_rn(U[1], ri), v = __fmul_rn(U[2], ri);
+    const float p = __fmul_rn(gm1, __fmaf_rn(-0.5f, __fmaf_rn(U[1], u, __fmul_rn(U[2], v)), U[3]));
+    const float ep = __fadd_rn(U[3], p);
     float F[4];
     if (DIR == 0) {
         F[0] = U[1];
-        F[1] = U[1] * u + p;
-        F[2] = U[2] * u;
-        F[3] = u * (U[3] + p);
+        F[1] = __fmaf_rn(U[1], u, p);
+        F[2] = __fmul_rn(U[2], u);
+        F[3] = __fmul_rn(u, ep);
         pr[0] = u;
         pr[1] = v;
     } else {
         F[0] = U[2];
-        F[1] = U[1] * v;
-        F[2] = U[2] * v + p;
-        F[3] = v * (U[3] + p);
+        F[1] = __fmul_rn(U[1], v);
+        F[2] = __fmaf_rn(U[2], v, p);
+        F[3] = __fmul_rn(v, ep);
         pr[0] = v;
         pr[1] = u;
     }
-    pr[2] = (U[3] + p) * ri;
-    pr[3] = U[0] * rsqrtf(U[0]);
+    pr[2] = __fmul_rn(ep, ri);
+    pr[3] = __fmul_rn(U[0], rsqrtf(U[0]));
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         gp[k] = 0.5f * fmaf(alpha, U[k], F[k]);
@@ -550,21 +610,22 @@ __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsig
                                            float gm1, int lane) {
     const float unl = pr(0, lane + 3), unr = pr(0, lane + 4), vtl = pr(1, lane + 3), vtr = pr(1, lane + 4);
     const float Hl = pr(2, lane + 3), Hr = pr(2, lane + 4), sl = pr(3, lane + 3), sr = pr(3, lane + 4);
-    const float w = rcp_approx(sl + sr);
-    const float un = (sl * unl + sr * unr) * w;
-    const float vt = (sl * vtl + sr * vtr) * w;
-    const float Ht = (sl * Hl + sr * Hr) * w;
-    const float q2 = 0.5f * (un * un + vt * vt);
-    const float c2 = gm1 * (Ht - q2);
+    const float w = rcp_approx(__fadd_rn(sl, sr));
+    const float un = __fmul_rn(__fmaf_rn(sl, unl, __fmul_rn(sr, unr)), w);
+    const float vt = __fmul_rn(__fmaf_rn(sl, vtl, __fmul_rn(sr, vtr)), w);
+    const float Ht = __fmul_rn(__fmaf_rn(sl, Hl, __fmul_rn(sr, Hr)), w);
+    const float q2 = __fmul_rn(0.5f, __fmaf_rn(un, un, __fmul_rn(vt, vt)));
+    const float c2 = __fmul_rn(gm1, __fadd_rn(Ht, -q2));
     const float rc = rsqrtf(c2);
-    const float c = c2 * rc;
-    const float b1 = gm1 * (rc * rc), b2 = q2 * b1, uc = un * rc;
+    const float c = __fmul_rn(c2, rc);
+    const float b1 = __fmul_rn(gm1, __fmul_rn(rc, rc)), b2 = __fmul_rn(q2, b1);
     if (!(c2 > 0.f)) flag |= isfinite(c2) ? ERR_NONPHYSICAL : ERR_NONFINITE;
     // rows of L in the rotated component order (rho, normal, tangential, E);
     // row 2 (shear) is (-vt, 0, 1, 0)
-    const float L0[4] = {0.5f * (b2 + uc), -0.5f * (b1 * un + rc), -0.5f * (b1 * vt), 0.5f * b1};
-    const float L1[4] = {1.f - b2, b1 * un, b1 * vt, -b1};
-    const float L3[4] = {0.5f * (b2 - uc), -0.5f * (b1 * un - rc), -0.5f * (b1 * vt), 0.5f * b1};
+    const float b1u = __fmul_rn(b1, un), l02 = __fmul_rn(-0.5f, __fmul_rn(b1, vt)), l03 = __fmul_rn(0.5f, b1);
+    const float L0[4] = {__fmul_rn(0.5f, __fmaf_rn(un, rc, b2)), __fmul_rn(-0.5f, __fadd_rn(b1u, rc)), l02, l03};
+    const float L1[4] = {__fadd_rn(1.f, -b2), b1u, __fmul_rn(b1, vt), -b1};
+    const float L3[4] = {__fmul_rn(0.5f, __fmaf_rn(-un, rc, b2)), __fmul_rn(-0.5f, __fadd_rn(b1u, -rc)), l02, l03};
     constexpr int CN = rot<DIR>(1), CT_ = rot<DIR>(2);  // physical index of the normal / tangential momentum
     float2 g[4][7];
 #pragma unroll
@@ -617,20 +678,21 @@ __device__ __forceinline__ void face2d_f32(float fh[4], unsigned &codes_p, unsig
 #pragma unroll
             for (int t = 1; t < 7; t++) s = __ffma2_rn(make_float2(cpp[t], cmm[t]), P[t], s);
         }
-        f[k] = s.x + s.y;
+        f[k] = __fadd_rn(s.x, s.y);
     }
     // back-projection: rotated rows (rho, normal, tangential, E) of R
-    const float Fr0 = f[0] + f[1] + f[3];
-    const float Fr1 = (un - c) * f[0] + un * f[1] + (un + c) * f[3];
-    const float Fr2 = vt * (f[0] + f[1] + f[3]) + f[2];
-    const float Fr3 = (Ht - un * c) * f[0] + q2 * f[1] + vt * f[2] + (Ht + un * c) * f[3];
+    const float Fr0 = __fadd_rn(__fadd_rn(f[0], f[1]), f[3]);
+    const float Fr1 = __fmaf_rn(__fadd_rn(un, c), f[3], __fmaf_rn(__fadd_rn(un, -c), f[0], __fmul_rn(un, f[1])));
+    const float Fr2 = __fmaf_rn(vt, Fr0, f[2]);
+    const float hm = __fmaf_rn(-un, c, Ht), hp = __fmaf_rn(un, c, Ht);
+    const float Fr3 = __fmaf_rn(hp, f[3], __fmaf_rn(vt, f[2], __fmaf_rn(q2, f[1], __fmul_rn(hm, f[0]))));
     fh[0] = Fr0;
     fh[CN] = Fr1;
     fh[CT_] = Fr2;
     fh[3] = Fr3;
 }
 
-template <typename S>
+template <typename S, bool HALO>
 __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D p) {
     constexpr bool MIXED = sizeof(S) == 8;
     __shared__ float s_gp[WPB][4][WC];
@@ -642,7 +704,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     if (!p.rhs_mode && !fixed && !ctl->active) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     fill_delta_table(s_cf);
-    const float alpha = ctl->alpha_f[p.slot_in][0];
+    const float alpha = alpha2d_in<float, HALO>(p, ctl, 0);
     const float gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_x, CT = p.f_CT;
     const float kt = keep_all_factor(CT);
     const float idx = 1.f / p.f_dx;
@@ -651,6 +713,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     S *R = static_cast<S *>(p.R);
     const int nx = p.nx, ny = p.ny;
     const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N;
     const int ntx = (nx + WT - 1) / WT;
     const long ntiles = (long)ntx * ny;
     float (*sgp)[WC] = s_gp[warp];
@@ -669,8 +732,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         if (gb < 0 || gb >= nx) gb = ghost_map(gb, nx, p.bc[0], p.bc[1]);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            ua[k] = row[(size_t)k * N + ga];
-            ub[k] = (lane < WS - 32) ? row[(size_t)k * N + gb] : S(0);
+            ua[k] = row[(size_t)k * sv + ga];
+            ub[k] = (lane < WS - 32) ? row[(size_t)k * sv + gb] : S(0);
         }
     };
     const long tstride = (long)gridDim.x * WPB;
@@ -738,7 +801,7 @@ constexpr size_t ysweep_f32_smem_bytes() {
            sizeof(float) * (32 * 8 + 2 * WPB);
 }
 
-template <typename S>
+template <typename S, bool HALO>
 __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D p) {
     constexpr bool MIXED = sizeof(S) == 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -758,8 +821,9 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
     const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N, svo = HALO ? p.svo : N;
     const int x0 = blockIdx.x * YB_COLS, r0 = blockIdx.y * YB_ROWS;
-    const float alpha = ctl->alpha_f[p.slot_in][1];
+    const float alpha = alpha2d_in<float, HALO>(p, ctl, 1);
     const float gamma = p.f_gamma, gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_y, CT = p.f_CT;
     const float kt = keep_all_factor(CT);
     const S *Us = static_cast<const S *>(p.Us);
@@ -777,9 +841,9 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
         const int r = q / YB_COLS, x = x0 + q % YB_COLS;
         if (q < YB_STAGE * YB_COLS && x < nx) {
             int y = r0 - 5 + r;
-            if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
+            y = y_row<HALO>(y, p);
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ust[sI][k] = Us[(size_t)k * N + (size_t)y * nx + x];
+            for (int k = 0; k < 4; k++) Ust[sI][k] = Us[st_at<HALO>(k, sv, y, nx, x)];
         }
     }
 #pragma unroll
@@ -861,8 +925,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     Rv[e][k] = R[(size_t)k * N + gi];
-                    Uv[e][k] = p.rhs_mode ? S(0) : Us[(size_t)k * N + gi];
-                    U0v[e][k] = use_u0 ? U0[(size_t)k * N + gi] : S(0);
+                    Uv[e][k] = p.rhs_mode ? S(0) : Us[(size_t)k * sv + gi];
+                    U0v[e][k] = use_u0 ? U0[(size_t)k * sv + gi] : S(0);
                 }
             }
         }
@@ -877,7 +941,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             for (int k = 0; k < 4; k++) {
                 const S rr = Rv[e][k] + s_ry[(k * YB_ROWS + r) * YB_LD + col];
                 if (p.rhs_mode) {
-                    out[(size_t)k * N + gi] = rr;
+                    out[(size_t)k * svo + gi] = rr;
                     continue;
                 }
                 S o;
@@ -900,7 +964,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
                         o = fmaf(2.0f / 3.0f, v - u0, u0);
                     }
                 }
-                out[(size_t)k * N + gi] = o;
+                out[(size_t)k * svo + gi] = o;
                 of[k] = to_f32(o);
             }
             if (!p.rhs_mode) {
@@ -930,7 +994,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)vx));
             atomicMax(&ctl->amax[so][1], (unsigned long long)__double_as_longlong((double)vy));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true,
+                          HALO ? p.alpha_rec : nullptr);
         }
     }
 }
@@ -957,7 +1022,7 @@ inline constexpr size_t ysweep_f32p_smem_bytes() {
                             2 * WPB);
 }
 
-template <typename S>  // float (the FP32 state) only
+template <typename S, bool HALO>  // S = float (the FP32 state) only
 __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2D p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *s_ry = reinterpret_cast<float *>(smem_raw);  // [4][29][33]
@@ -977,8 +1042,9 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
     const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N, svo = HALO ? p.svo : N;
     const int nbx = (nx + YB_COLS - 1) / YB_COLS, nblocks = nbx * ((ny + YB_ROWS - 1) / YB_ROWS);
-    const float alpha = ctl->alpha_f[p.slot_in][1];
+    const float alpha = alpha2d_in<float, HALO>(p, ctl, 1);
     const float gamma = p.f_gamma, gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_y, CT = p.f_CT;
     const float kt = keep_all_factor(CT);
     const float *Us = static_cast<const float *>(p.Us);
@@ -995,18 +1061,18 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
     if (tid < 2) s_amax[tid] = 0;
 
     // rows r0-5 .. r0+33 of columns x0 .. x0+31 of block b into s_in (one
-    // 4-byte asynchronous copy per value; rows outside the grid by the
-    // boundary map, columns beyond it skipped)
+    // 4-byte asynchronous copy per value; rows outside the grid by y_row,
+    // columns beyond it skipped)
     auto copy_block = [&](int b) {
         const int x0 = (b % nbx) * YB_COLS, r0 = (b / nbx) * YB_ROWS;
         for (int q = tid; q < YB_STAGE * YB_COLS; q += WPB * 32) {
             const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col;
             if (x >= nx) continue;
             int y = r0 - 5 + r;
-            if (y < 0 || y >= ny) y = ghost_map(y, ny, p.bc[2], p.bc[3]);
+            y = y_row<HALO>(y, p);
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[(size_t)k * N + (size_t)y * nx + x]);
+                cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[st_at<HALO>(k, sv, y, nx, x)]);
         }
         cp_async_commit();
     };
@@ -1082,8 +1148,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         Rv[e][k] = R[(size_t)k * N + gi];
-                        Uv[e][k] = p.rhs_mode ? 0.f : Us[(size_t)k * N + gi];
-                        U0v[e][k] = use_u0 ? U0[(size_t)k * N + gi] : 0.f;
+                        Uv[e][k] = p.rhs_mode ? 0.f : Us[(size_t)k * sv + gi];
+                        U0v[e][k] = use_u0 ? U0[(size_t)k * sv + gi] : 0.f;
                     }
                 }
             }
@@ -1098,7 +1164,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
                 for (int k = 0; k < 4; k++) {
                     const float rr = Rv[e][k] + s_ry[(k * YB_ROWS + r) * YB_LD + col];
                     if (p.rhs_mode) {
-                        out[(size_t)k * N + gi] = rr;
+                        out[(size_t)k * svo + gi] = rr;
                         continue;
                     }
                     float o;
@@ -1111,7 +1177,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
                         const float u0 = U0v[e][k];
                         o = fmaf(2.0f / 3.0f, v - u0, u0);
                     }
-                    out[(size_t)k * N + gi] = o;
+                    out[(size_t)k * svo + gi] = o;
                     of[k] = o;
                 }
                 if (!p.rhs_mode) {
@@ -1141,66 +1207,67 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
             const int so = (p.stage + 1) % 3;
             atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)vx));
             atomicMax(&ctl->amax[so][1], (unsigned long long)__double_as_longlong((double)vy));
-            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true);
+            finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, true,
+                          HALO ? p.alpha_rec : nullptr);
         }
     }
 }
 
-template <typename S>
+template <typename S, bool HALO = false>
 cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
     const int ntx = (p.nx + WT - 1) / WT;
     long ntiles = (long)ntx * p.ny;
     long gx = (ntiles + WPB - 1) / WPB;
     const long cap = (long)num_sms() * 2 * 4;
     if (gx > cap) gx = cap;
-    xsweep2d_f32_kernel<S><<<(int)gx, WPB * 32, 0, st>>>(p);
+    xsweep2d_f32_kernel<S, HALO><<<(int)gx, WPB * 32, 0, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if constexpr (sizeof(S) == 4) {
         // FP32 state: persistent CTAs (two per SM) with the next block prefetched
         const size_t smem = ysweep_f32p_smem_bytes();
-        e = cudaFuncSetAttribute(ysweep2d_f32p_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(ysweep2d_f32p_kernel<S, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const long nb = (long)((p.nx + YB_COLS - 1) / YB_COLS) * ((p.ny + YB_ROWS - 1) / YB_ROWS);
         const long cap = (long)num_sms() * 2;
-        ysweep2d_f32p_kernel<S><<<(int)(nb < cap ? nb : cap), WPB * 32, smem, st>>>(p);
+        ysweep2d_f32p_kernel<S, HALO><<<(int)(nb < cap ? nb : cap), WPB * 32, smem, st>>>(p);
         return cudaGetLastError();
     }
     const size_t smem = ysweep_f32_smem_bytes<S>();
-    e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
-    ysweep2d_f32_kernel<S><<<grid, WPB * 32, smem, st>>>(p);
+    ysweep2d_f32_kernel<S, HALO><<<grid, WPB * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool HALO = false>
 cudaError_t launch_stage2d(const Stage2D &p, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
-        return launch_stage2d_paired<float>(p, st);
+        return launch_stage2d_paired<float, HALO>(p, st);
     } else {
     const int ntx = (p.nx + WT - 1) / WT;
     long ntiles = (long)ntx * p.ny;
     long gx = (ntiles + WPB - 1) / WPB;
     const long cap = (long)num_sms() * 4;
     if (gx > cap) gx = cap;
-    xsweep2d_kernel<T><<<(int)gx, WPB * 32, 0, st>>>(p);
+    xsweep2d_kernel<T, HALO><<<(int)gx, WPB * 32, 0, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = ysweep_smem_bytes<T>();
-    e = cudaFuncSetAttribute(ysweep2d_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(ysweep2d_kernel<T, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
-    ysweep2d_kernel<T><<<grid, WPB * 32, smem, st>>>(p);
+    ysweep2d_kernel<T, HALO><<<grid, WPB * 32, smem, st>>>(p);
     return cudaGetLastError();
     }
 }
 
-template <typename T>
+template <typename T, bool HALO = false>
 cudaError_t launch_alpha2d(const Alpha2D &p, cudaStream_t st) {
     long grid = ((long)p.nx * p.ny + 255) / 256;
     if (grid > num_sms() * 8) grid = num_sms() * 8;
-    alpha2d_kernel<T><<<(int)grid, 256, 0, st>>>(p);
+    alpha2d_kernel<T, HALO><<<(int)grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 

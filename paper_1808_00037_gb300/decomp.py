@@ -22,7 +22,7 @@ padded by HALO cells (rows) on each side of axis 1, so the stage kernel reads
 its halos in place.  A slab's ``backend`` does the arithmetic:
 ``alpha(P, out)`` (local max wave speed into a one-element float64 tensor)
 and ``stage(k, Us, U0, out, alpha, dt, alpha_out)`` (one Shu-Osher stage).
-``CudaSlab1D`` wraps the library's t7_slab_* entry points, so the RK stages,
+``CudaSlab`` wraps the library's t7_slab_* entry points, so the RK stages,
 the wave-speed reductions and the alpha values never leave the GPU; only dt
 (one double per step) is read on the host.
 """
@@ -57,9 +57,10 @@ def interior(P):
     return P[:, HALO:-HALO]
 
 
-class CudaSlab1D:
-    """A slab backend on the CUDA library: one context per slab (nx = the
-    slab's cells), t7_slab_alpha / t7_slab_stage on padded tensors."""
+class CudaSlab:
+    """A slab backend on the CUDA library: one context per slab (1D: nx = the
+    slab's cells; 2D: nx columns, ny = the slab's rows), t7_slab_alpha /
+    t7_slab_stage on padded tensors (2D: alpha_x and alpha_y, two doubles)."""
 
     def __init__(self, ctx):
         self.ctx = ctx

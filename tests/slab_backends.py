@@ -1,5 +1,5 @@
 """Oracle backends of the slab decomposition (test infrastructure): the same
-stage interface as decomp.CudaSlab1D, computed by the CPU oracle on CPU
+stage interface as decomp.CudaSlab, computed by the CPU oracle on CPU
 tensors, so the multi-rank orchestration can be checked on gloo ranks."""
 import numpy as np
 import torch

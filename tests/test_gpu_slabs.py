@@ -42,7 +42,7 @@ def _slabs(sysid, U, dx, prec, nslabs, periodic):
         st = torch.cuda.Stream()
         ctx = B.Context(sysid, hi - lo, dx, prec=prec, gamma=1.4, stream=st)
         Ul = torch.tensor(U[:, lo:hi], dtype=DTYPE[prec], device="cuda")
-        slabs.append(decomp.Slab(decomp.CudaSlab1D(ctx), Ul))
+        slabs.append(decomp.Slab(decomp.CudaSlab(ctx), Ul))
     torch.cuda.synchronize()
     return decomp.LocalSlabs(slabs, periodic)
 
