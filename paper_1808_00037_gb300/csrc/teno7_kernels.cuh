@@ -1408,13 +1408,16 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
 // ==========================================================================
 constexpr int WT2 = 61;  // cells updated per face-paired warp tile
 constexpr int WS2 = 71;  // cells staged per face-paired warp tile (c0-5 .. c0+65)
-constexpr int WC2 = 72;  // padded row length
+// Staging rows of the face-paired kernel hold PAIRS (value of staged cell i,
+// value of staged cell i + 32), i = 0 .. 38, so that one 64-bit shared load
+// gives a tap of face A (lane l: cells from l) and of face B (cells from l + 32).
+constexpr int WP2 = 40;
 
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <int SYS, int SCH>
-__device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float (*sU)[WC2], float (*sgp)[WC2],
-                                                float (*sgm)[WC2], float (*spr)[WC2], const float (*s_cf)[8],
+__device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2 (*sU)[WP2], float2 (*sgp)[WP2],
+                                                float2 (*sgm)[WP2], float2 (*spr)[WP2], const float (*s_cf)[8],
                                                 int tile0, int tstride) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -1468,10 +1471,17 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
 #pragma unroll
             for (int k = 0; k < M; k++) Ucur[r][k] = ur[r][k];
         if (tile + tstride < ntiles) load_tile(tile + tstride);
+        // staged values (primitives, state, split fluxes) of the cells of rounds
+        // r = 0, 1, 2 (staged cells lane, lane + 32, lane + 64).  Pair i =
+        // (staged cell i, staged cell i + 32): after round 1 lane l writes pair l
+        // (rounds 0, 1), after round 2 lanes l < 7 write pair l + 32 (rounds
+        // 1, 2), one 64-bit store each
+        float vpr[2][NP], vU[2][M], vgp[2][M], vgm[2][M];
 #pragma unroll
         for (int r = 0; r < 3; r++) {
             const int c = lane + 32 * r;
             if (c >= WS2) break;
+            const int h = r & 1;  // this round's slot; the previous round's is 1 - h
             float U[M], F[M];
 #pragma unroll
             for (int k = 0; k < M; k++) U[k] = Ucur[r][k];
@@ -1486,19 +1496,31 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
                 F[0] = U[1];
                 F[1] = U[1] * u + pr;
                 F[2] = u * (U[2] + pr);
-                spr[0][c] = u;
-                spr[NP > 1 ? 1 : 0][c] = (U[2] + pr) * ri;
-                spr[NP > 2 ? 2 : 0][c] = U[0] * rsqrtf(U[0]);
+                vpr[h][0] = u;
+                vpr[h][NP > 1 ? 1 : 0] = (U[2] + pr) * ri;
+                vpr[h][NP > 2 ? 2 : 0] = U[0] * rsqrtf(U[0]);
             }
 #pragma unroll
             for (int k = 0; k < M; k++) {
-                sU[k][c] = U[k];
+                vU[h][k] = U[k];
                 if (SYS == SYS_ADV) {
-                    sgp[k][c] = (0.5f * (a + alpha)) * U[k];
+                    vgp[h][k] = (0.5f * (a + alpha)) * U[k];
                 } else {
-                    sgp[k][c] = 0.5f * fmaf(alpha, U[k], F[k]);
-                    sgm[k][c] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                    vgp[h][k] = 0.5f * fmaf(alpha, U[k], F[k]);
+                    vgm[h][k] = 0.5f * fmaf(-alpha, U[k], F[k]);
                 }
+            }
+            if (r == 0) continue;
+            const int i = lane + 32 * (r - 1);  // the pair: (round r - 1, round r)
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                sU[k][i] = make_float2(vU[1 - h][k], vU[h][k]);
+                sgp[k][i] = make_float2(vgp[1 - h][k], vgp[h][k]);
+                if (SYS != SYS_ADV) sgm[k][i] = make_float2(vgm[1 - h][k], vgm[h][k]);
+            }
+            if (SYS == SYS_EULER1D) {
+#pragma unroll
+                for (int q = 0; q < NP; q++) spr[q][i] = make_float2(vpr[1 - h][q], vpr[h][q]);
             }
         }
         __syncwarp();
@@ -1510,12 +1532,9 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
         if (SYS == SYS_EULER1D) {
             // the roundings of roe_frame_f32, for both faces at once
             const int P0 = NP > 1 ? 1 : 0, P1 = NP > 2 ? 2 : 0;
-            const float2 ul = make_float2(spr[0][lane + 3], spr[0][lane + 35]);
-            const float2 ur_ = make_float2(spr[0][lane + 4], spr[0][lane + 36]);
-            const float2 Hl = make_float2(spr[P0][lane + 3], spr[P0][lane + 35]);
-            const float2 Hr = make_float2(spr[P0][lane + 4], spr[P0][lane + 36]);
-            const float2 sl = make_float2(spr[P1][lane + 3], spr[P1][lane + 35]);
-            const float2 sr = make_float2(spr[P1][lane + 4], spr[P1][lane + 36]);
+            const float2 ul = spr[0][lane + 3], ur_ = spr[0][lane + 4];
+            const float2 Hl = spr[P0][lane + 3], Hr = spr[P0][lane + 4];
+            const float2 sl = spr[P1][lane + 3], sr = spr[P1][lane + 4];
             const float2 ssum = __fadd2_rn(sl, sr);
             const float2 w = make_float2(rcp_approx(ssum.x), rcp_approx(ssum.y));
             ut = __fmul2_rn(__ffma2_rn(sl, ul, __fmul2_rn(sr, ur_)), w);
@@ -1546,7 +1565,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
         unsigned Dsave[2] = {0u, 0u};
 #pragma unroll
         for (int s = 0; s < (PLUS_ONLY ? 1 : 2); s++) {
-            float (*sg)[WC2] = s == 0 ? sgp : sgm;
+            float2 (*sg)[WP2] = s == 0 ? sgp : sgm;
             float2 P[M][7];
 #pragma unroll
             for (int t = 0; t < 7; t++) {
@@ -1559,7 +1578,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
                 const int o = s == 0 ? lane + t : lane + 7 - t;
                 float2 g[M];
 #pragma unroll
-                for (int c = 0; c < M; c++) g[c] = make_float2(sg[c][o], sg[c][o + 32]);
+                for (int c = 0; c < M; c++) g[c] = sg[c][o];
 #pragma unroll
                 for (int k = 0; k < M; k++) {
                     if (M == 1) {
@@ -1712,7 +1731,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float 
                 float2 o[M];
 #pragma unroll
                 for (int k = 0; k < M; k++) {
-                    const float2 v = __ffma2_rn(f2(dtT), r[k], make_float2(sU[k][lane + 3], sU[k][lane + 35]));
+                    const float2 v = __ffma2_rn(f2(dtT), r[k], sU[k][lane + 3]);
                     if (A.stage == 0) {
                         o[k] = v;
                     } else if (A.stage == 1) {
@@ -1754,10 +1773,10 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int MG = (SYS == SYS_ADV) ? 1 : M;  // '-' staging rows (unused for advection)
-    __shared__ float s_U[WPB][M][WC2];
-    __shared__ float s_gp[WPB][M][WC2];
-    __shared__ float s_gm[WPB][MG][WC2];
-    __shared__ float s_pr[WPB][NP][WC2];
+    __shared__ float2 s_U[WPB][M][WP2];
+    __shared__ float2 s_gp[WPB][M][WP2];
+    __shared__ float2 s_gm[WPB][MG][WP2];
+    __shared__ float2 s_pr[WPB][NP][WP2];
     __shared__ __align__(16) float s_cf[32][8];
     __shared__ float s_red[WPB];
 

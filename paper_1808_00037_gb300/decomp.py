@@ -226,17 +226,33 @@ def rk3_run_slabs(comm, dt_of_alpha, *, t_end: float, max_steps: int):
     slabs = comm.slabs
     dev = slabs[0].P[0].device
     g = [torch.zeros_like(slabs[0].a[0]) for _ in range(3)]  # all-reduced alphas
+    cuda = dev.type == "cuda"
+    if cuda:
+        # the all-reduced alpha of U^n reaches the host through a pinned buffer
+        # and an event, so that only the host waits for it
+        a_host = torch.empty(g[0].shape, dtype=g[0].dtype, pin_memory=True)
+        a_ready = torch.cuda.Event()
     for s in slabs:
         with (torch.cuda.stream(s.stream) if s.stream is not None else _null()):
             s.backend.alpha(s.P[0], s.a[0])
     t, steps = 0.0, 0
-    while steps < max_steps and t < t_end:
+    if steps < max_steps and t < t_end:
         comm.allreduce_max(0, g[0])
-        dt = dt_of_alpha(g[0].cpu() if dev.type == "cuda" else g[0])
+    while steps < max_steps and t < t_end:
+        if cuda:
+            a_host.copy_(g[0], non_blocking=True)
+            a_ready.record()
+        # the halos of U^n do not depend on dt: they are queued before the
+        # host waits for it, so the device has them to do meanwhile
+        comm.fill_halos(0)
+        if cuda:
+            a_ready.synchronize()
+        dt = dt_of_alpha(a_host if cuda else g[0])
         if t + dt > t_end:
             dt = t_end - t
         for k in range(3):
-            comm.fill_halos(k)
+            if k > 0:
+                comm.fill_halos(k)
             for s in slabs:
                 Us, U0 = s.P[k], s.P[0]
                 out = s.P[k + 1] if k < 2 else s.P[0]
@@ -246,6 +262,9 @@ def rk3_run_slabs(comm, dt_of_alpha, *, t_end: float, max_steps: int):
                 comm.allreduce_max(k + 1, g[k + 1])
         t = t + dt
         steps += 1
+        if steps < max_steps and t < t_end:
+            # alpha of U^{n+1}: every slab's stage 2 wrote its part into a[0]
+            comm.allreduce_max(0, g[0])
     if any(s.stream is not None for s in slabs):
         cur = torch.cuda.current_stream()
         for s in slabs:
