@@ -1017,6 +1017,298 @@ static __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ==========================================================================
+// FP32 2D faces in PAIRS (the 1D face-paired kernel's design, 4 fields): every
+// float2 holds (face A, face B), the two splits run one after the other, and
+// the fields go in two groups -- fields 0, 1, 3, which read all four
+// components, and the shear field 2, which reads two -- so that one group's
+// projections (7 pairs per field) are live at a time.  Every per-face
+// operation is the one face2d_f32 performs, in the same order, so the results
+// are the same bits.
+//   pr(q, i)     primitive q of staged index i, as the pair (face A's cell,
+//                face B's cell); cell j-3+t of face j+1/2 is staged index lane+t
+//   gs(s, c, i)  split s (0: '+', 1: '-') of physical component c, likewise
+//   WRAP         true: faces A and B of lane l are c0-2+l and c0+30+l of one
+//                row, so face A of lane 31 and face B of lane 0 are
+//                neighbours (the x sweep); false: A and B lie in two columns
+// D[s][g] receives the Delta words of split s and field group g (A slots from
+// bit 0, B slots SH bits higher, 5 bits per field, as in the 1D kernel).
+// ==========================================================================
+template <int G>
+__device__ __forceinline__ unsigned pair_delta(unsigned word, int s, int lane, bool wrap) {
+    constexpr int SH = 5 * G;
+    constexpr unsigned MASK_A = (1u << SH) - 1u;
+    const unsigned wl = __shfl_sync(0xffffffffu, word, (lane + 31) & 31);
+    const unsigned wr = __shfl_sync(0xffffffffu, word, (lane + 1) & 31);
+    // codes of each face's left and right neighbour faces, in its own slots
+    const unsigned LW = (wrap && lane == 0) ? (wl & MASK_A) | (wl << SH) : wl;
+    const unsigned RW = (wrap && lane == 31) ? (wr >> SH) | (wr & ~MASK_A) : wr;
+    return s == 0 ? (((LW << 1) & SLOT_HI) | (word & SLOT_MID) | ((RW >> 1) & SLOT_LO))
+                  : (((RW << 1) & SLOT_HI) | (word & SLOT_MID) | ((LW >> 1) & SLOT_LO));
+}
+
+// Table co2 polynomial of one field of both faces: the all-kept row as
+// constants, any other row from the Delta-indexed table.
+__device__ __forceinline__ float2 pair_poly(const float2 P[7], unsigned codeA, unsigned codeB,
+                                            const float (*s_cf)[8]) {
+    float2 v;
+    if (codeA == 31u && codeB == 31u) {
+        v = __fmul2_rn(f2(-1.f / 140.f), P[0]);
+        v = __ffma2_rn(f2(5.f / 84.f), P[1], v);
+        v = __ffma2_rn(f2(-101.f / 420.f), P[2], v);
+        v = __ffma2_rn(f2(319.f / 420.f), P[3], v);
+        v = __ffma2_rn(f2(107.f / 210.f), P[4], v);
+        v = __ffma2_rn(f2(-19.f / 210.f), P[5], v);
+        v = __ffma2_rn(f2(1.f / 105.f), P[6], v);
+    } else {
+        const float *cA = s_cf[codeA];
+        const float *cB = s_cf[codeB];
+        v = __fmul2_rn(make_float2(cA[0], cB[0]), P[0]);
+#pragma unroll
+        for (int t = 1; t < 7; t++) v = __ffma2_rn(make_float2(cA[t], cB[t]), P[t], v);
+    }
+    return v;
+}
+
+template <int DIR, bool WRAP, typename PR, typename GS>
+__device__ __forceinline__ void face2d_pair(float2 fh[4], unsigned (&D)[2][2], int &flagA, int &flagB, PR pr,
+                                            GS gs, const float (*s_cf)[8], float eps4, float CT, float kt,
+                                            float gm1, int lane) {
+    // ---- Roe frames of both faces (face2d_f32's roundings, packed)
+    const float2 unl = pr(0, lane + 3), unr = pr(0, lane + 4), vtl = pr(1, lane + 3), vtr = pr(1, lane + 4);
+    const float2 Hl = pr(2, lane + 3), Hr = pr(2, lane + 4), sl = pr(3, lane + 3), sr = pr(3, lane + 4);
+    const float2 ssum = __fadd2_rn(sl, sr);
+    const float2 w = make_float2(rcp_approx(ssum.x), rcp_approx(ssum.y));
+    const float2 un = __fmul2_rn(__ffma2_rn(sl, unl, __fmul2_rn(sr, unr)), w);
+    const float2 vt = __fmul2_rn(__ffma2_rn(sl, vtl, __fmul2_rn(sr, vtr)), w);
+    const float2 Ht = __fmul2_rn(__ffma2_rn(sl, Hl, __fmul2_rn(sr, Hr)), w);
+    const float2 q2 = __fmul2_rn(f2(0.5f), __ffma2_rn(un, un, __fmul2_rn(vt, vt)));
+    const float2 c2 = __fmul2_rn(f2(gm1), __fadd2_rn(Ht, f2neg(q2)));
+    const float2 rc = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
+    if (!(c2.x > 0.f)) flagA |= isfinite(c2.x) ? ERR_NONPHYSICAL : ERR_NONFINITE;
+    if (!(c2.y > 0.f)) flagB |= isfinite(c2.y) ? ERR_NONPHYSICAL : ERR_NONFINITE;
+    // only un, vt, Ht, q2 and 1/c stay live through the splits: b1, b2 and c
+    // are formed again where they are used (the same operations, the same bits)
+    constexpr int CN = rot<DIR>(1), CT_ = rot<DIR>(2);  // physical index of the normal / tangential momentum
+    float2 f[4];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        // ---- fields 0, 1, 3
+        {
+            // rows of L of fields 0, 1, 3 in the rotated component order (rho,
+            // normal, tangential, E), formed per split so that they are live
+            // only here; field 2 (shear) is (-vt, 0, 1, 0)
+            const float2 b1 = __fmul2_rn(f2(gm1), __fmul2_rn(rc, rc)), b2 = __fmul2_rn(q2, b1);
+            const float2 b1u = __fmul2_rn(b1, un), l02 = __fmul2_rn(f2(-0.5f), __fmul2_rn(b1, vt));
+            const float2 l03 = __fmul2_rn(f2(0.5f), b1);
+            const float2 L[3][4] = {
+                {__fmul2_rn(f2(0.5f), __ffma2_rn(un, rc, b2)), __fmul2_rn(f2(-0.5f), __fadd2_rn(b1u, rc)), l02, l03},
+                {__fadd2_rn(f2(1.f), f2neg(b2)), b1u, __fmul2_rn(b1, vt), f2neg(b1)},
+                {__fmul2_rn(f2(0.5f), __ffma2_rn(f2neg(un), rc, b2)),
+                 __fmul2_rn(f2(-0.5f), __fadd2_rn(b1u, f2neg(rc))), l02, l03}};
+            float2 P[3][7];
+#pragma unroll
+            for (int t = 0; t < 7; t++) {
+                const int i = s == 0 ? lane + t : lane + 7 - t;
+                const float2 g0 = gs(s, 0, i), gn = gs(s, CN, i), gt = gs(s, CT_, i), ge = gs(s, 3, i);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    float2 q = __fmul2_rn(L[k][0], g0);
+                    q = __ffma2_rn(L[k][1], gn, q);
+                    q = __ffma2_rn(L[k][2], gt, q);
+                    P[k][t] = __ffma2_rn(L[k][3], ge, q);
+                }
+            }
+            bool keep_all = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float2 tau = tau_pair(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5]);
+                keep_all = keep_all && tau.x < kt * eps4 && tau.y < kt * eps4;
+            }
+            unsigned word = 0;
+            if (keep_all) {
+                word = (7u << 1) | (7u << 6) | (7u << 11) | (7u << 16) | (7u << 21) | (7u << 26);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    unsigned cA, cB;
+                    cutoff2(P[k][1], P[k][2], P[k][3], P[k][4], P[k][5], eps4, CT, kt, cA, cB);
+                    word |= (cA << (5 * k + 1)) | (cB << (15 + 5 * k + 1));
+                }
+            }
+            const unsigned Dw = pair_delta<3>(word, s, lane, WRAP);
+            D[s][0] = Dw;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float2 v = pair_poly(P[k], (Dw >> (5 * k)) & 31u, (Dw >> (15 + 5 * k)) & 31u, s_cf);
+                const int fk = k == 2 ? 3 : k;
+                f[fk] = s == 0 ? v : __fadd2_rn(f[fk], v);
+            }
+        }
+        // ---- field 2 (shear)
+        {
+            float2 P[7];
+#pragma unroll
+            for (int t = 0; t < 7; t++) {
+                const int i = s == 0 ? lane + t : lane + 7 - t;
+                P[t] = __ffma2_rn(f2neg(vt), gs(s, 0, i), gs(s, CT_, i));
+            }
+            unsigned cA, cB;
+            cutoff2(P[1], P[2], P[3], P[4], P[5], eps4, CT, kt, cA, cB);
+            const unsigned Dw = pair_delta<1>((cA << 1) | (cB << 6), s, lane, WRAP);
+            D[s][1] = Dw;
+            const float2 v = pair_poly(P, Dw & 31u, (Dw >> 5) & 31u, s_cf);
+            f[2] = s == 0 ? v : __fadd2_rn(f[2], v);
+        }
+    }
+    // ---- back projection: rotated rows (rho, normal, tangential, E) of R
+    const float2 c = __fmul2_rn(__fmul2_rn(f2(gm1), __fadd2_rn(Ht, f2neg(q2))), rc);
+    const float2 Fr0 = __fadd2_rn(__fadd2_rn(f[0], f[1]), f[3]);
+    const float2 Fr1 = __ffma2_rn(__fadd2_rn(un, c), f[3], __ffma2_rn(__fadd2_rn(un, f2neg(c)), f[0], __fmul2_rn(un, f[1])));
+    const float2 Fr2 = __ffma2_rn(vt, Fr0, f[2]);
+    const float2 hm = __ffma2_rn(f2neg(un), c, Ht), hp = __ffma2_rn(un, c, Ht);
+    const float2 Fr3 =
+        __ffma2_rn(hp, f[3], __ffma2_rn(vt, f[2], __ffma2_rn(q2, f[1], __fmul2_rn(hm, f[0]))));
+    fh[0] = Fr0;
+    fh[CN] = Fr1;
+    fh[CT_] = Fr2;
+    fh[3] = Fr3;
+}
+
+// Delta code (5 bits) of split s, field k of face h (0: A, 1: B) from face2d_pair's words.
+__device__ __forceinline__ unsigned pair_code(const unsigned (&D)[2][2], int s, int k, int h) {
+    const int g = k == 2 ? 1 : 0, slot = k == 3 ? 2 : (k == 2 ? 0 : k), SH = g == 0 ? 15 : 5;
+    return (D[s][g] >> (5 * slot + (h ? SH : 0))) & 31u;
+}
+
+// --------------------------------------------------------------------------
+// FP32 x sweep with paired faces: R = Lx(U).  Warp tile = WT2 = 61 cells of a
+// row (cells c0 .. c0+60); lane l owns faces c0-2+l (A) and c0+30+l (B); the
+// 71 cells c0-5 .. c0+65 are staged as pairs (cell i, cell i + 32), one tile
+// ahead in registers.  FP32 state only.
+// --------------------------------------------------------------------------
+template <bool HALO>
+__global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage2D p) {
+    __shared__ float2 s_pr[WPB][4][WP2];
+    __shared__ float2 s_gp[WPB][4][WP2];
+    __shared__ float2 s_gm[WPB][4][WP2];
+    __shared__ float s_raw[WPB][4][3 * 32];  // raw state of the next tile (cp.async)
+    __shared__ __align__(16) float s_cf[32][8];
+    DevCtl *ctl = p.ctl;
+    const bool fixed = p.dt_fixed > 0.0;
+    if (!p.rhs_mode && !fixed && !ctl->active) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    fill_delta_table(s_cf);
+    const float alpha = alpha2d_in<float, HALO>(p, ctl, 0);
+    const float gm1 = p.f_gm1, eps4 = 4.f * p.f_eps_x, CT = p.f_CT;
+    const float kt = keep_all_factor(CT);
+    const float idx = 1.f / p.f_dx;
+    const float *Us = static_cast<const float *>(p.Us);
+    float *R = static_cast<float *>(p.R);
+    const int nx = p.nx, ny = p.ny;
+    const size_t N = (size_t)nx * ny;
+    const size_t sv = HALO ? p.sv : N;
+    const int ntx = (nx + WT2 - 1) / WT2;
+    const long ntiles = (long)ntx * ny;
+    float2 (*spr)[WP2] = s_pr[warp];
+    float2 (*sgp)[WP2] = s_gp[warp];
+    float2 (*sgm)[WP2] = s_gm[warp];
+    float (*sraw)[3 * 32] = s_raw[warp];
+    __syncthreads();
+    // raw state of the staged cells of a tile (rounds r = 0, 1, 2: cells
+    // c0-5+32r+lane) into sraw by asynchronous copies, one tile ahead
+    auto copy_tile = [&](long tile) {
+        const int y = (int)(tile / ntx);
+        const int c0 = (int)(tile % ntx) * WT2;
+        const float *row = Us + (size_t)y * nx;
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            if (lane + 32 * r >= WS2) break;
+            int g = c0 - 5 + 32 * r + lane;
+            if (g < 0 || g >= nx) g = ghost_map(g, nx, p.bc[0], p.bc[1]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) cp_async4(&sraw[k][32 * r + lane], &row[(size_t)k * sv + g]);
+        }
+        cp_async_commit();
+    };
+    const long tstride = (long)gridDim.x * WPB;
+    long tile = (long)blockIdx.x * WPB + warp;
+    if (tile < ntiles) copy_tile(tile);
+    for (; tile < ntiles; tile += tstride) {
+        const int y = (int)(tile / ntx);
+        const int c0 = (int)(tile % ntx) * WT2;
+        cp_async_wait_all();
+        __syncwarp();
+        float cur[3][4];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) cur[r][k] = (lane + 32 * r < WS2) ? sraw[k][32 * r + lane] : 0.f;
+        __syncwarp();  // every lane has read sraw before the next tile's copies land in it
+        if (tile + tstride < ntiles) copy_tile(tile + tstride);
+        // primitives and split fluxes of the staged cells; after round r >= 1
+        // lane l writes pair l + 32 (r - 1) = (round r - 1, round r)
+        float vpr[2][4], vgp[2][4], vgm[2][4];
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            if (lane + 32 * r >= WS2) break;
+            const int h = r & 1;
+            cell2d_f32<0>(cur[r], gm1, alpha, vpr[h], vgp[h], vgm[h]);
+            if (r == 0) continue;
+            const int i = lane + 32 * (r - 1);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                spr[k][i] = make_float2(vpr[1 - h][k], vpr[h][k]);
+                sgp[k][i] = make_float2(vgp[1 - h][k], vgp[h][k]);
+                sgm[k][i] = make_float2(vgm[1 - h][k], vgm[h][k]);
+            }
+        }
+        __syncwarp();
+        float2 fh[4];
+        unsigned D[2][2];
+        int flagA = 0, flagB = 0;
+        face2d_pair<0, true>(
+            fh, D, flagA, flagB, [&](int q, int i) { return spr[q][i]; },
+            [&](int s, int cc, int i) { return s == 0 ? sgp[cc][i] : sgm[cc][i]; }, s_cf, eps4, CT, kt, gm1, lane);
+        const int jA = c0 - 2 + lane, jB = c0 + 30 + lane;  // faces, and the cells they update
+        if (p.rhs_mode && p.masks) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int j = h == 0 ? jA : jB;
+                if (!((h == 0 ? lane >= 1 : lane <= 30) && j >= -1 && j <= nx - 1)) continue;
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        p.masks[((size_t)(4 * s + k) * ny + y) * (nx + 1) + (j + 1)] = (uint8_t)pair_code(D, s, k, h);
+            }
+        }
+        if (flagA && lane >= 1 && jA >= -2 && jA <= nx) latch_error(ctl, flagA, flat_cell(y, jA, nx));
+        if (flagB && lane <= 30 && jB <= nx) latch_error(ctl, flagB, flat_cell(y, jB, nx));
+        // flux difference: the left face of cell jA is lane l-1's A; of cell jB,
+        // lane l-1's B (lane 0: lane 31's A)
+        float2 fprev[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float xr = __shfl_sync(0xffffffffu, fh[k].x, (lane + 31) & 31);
+            const float yr = __shfl_sync(0xffffffffu, fh[k].y, (lane + 31) & 31);
+            fprev[k] = make_float2(xr, lane == 0 ? xr : yr);
+        }
+        const bool updA = lane >= 2 && jA < nx, updB = lane <= 30 && jB < nx;
+        if (updA || updB) {
+            float *Ry = R + (size_t)y * nx;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float2 r = __fmul2_rn(__fadd2_rn(fprev[k], f2neg(fh[k])), f2(idx));
+                if (updA) Ry[(size_t)k * N + jA] = r.x;
+                if (updB) Ry[(size_t)k * N + jB] = r.y;
+            }
+        }
+        __syncwarp();  // the next tile overwrites this warp's staging rows
+    }
+}
+
+
 inline constexpr size_t ysweep_f32p_smem_bytes() {
     return sizeof(float) * (4 * YB_ROWS * YB_LD + 3 * 4 * YB_STAGE * YB_LD + 4 * YB_STAGE * YB_COLS + 32 * 8 +
                             2 * WPB);
@@ -1220,7 +1512,13 @@ cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
     long gx = (ntiles + WPB - 1) / WPB;
     const long cap = (long)num_sms() * 2 * 4;
     if (gx > cap) gx = cap;
-    xsweep2d_f32_kernel<S, HALO><<<(int)gx, WPB * 32, 0, st>>>(p);
+    if constexpr (sizeof(S) == 4) {
+        // FP32 state: paired faces, 61-cell tiles
+        const long gx2 = ((long)((p.nx + WT2 - 1) / WT2) * p.ny + WPB - 1) / WPB;
+        xsweep2d_f32fp_kernel<HALO><<<(int)(gx2 < cap ? gx2 : cap), WPB * 32, 0, st>>>(p);
+    } else {
+        xsweep2d_f32_kernel<S, HALO><<<(int)gx, WPB * 32, 0, st>>>(p);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if constexpr (sizeof(S) == 4) {
