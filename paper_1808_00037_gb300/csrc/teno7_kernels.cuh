@@ -1434,7 +1434,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
     const float *U0 = A.U0;
     float *out = A.out;
     const int n = A.n;
-    const size_t cs = A.cs;
+    const size_t cs = A.cs, cso = A.cso;
     const int ntiles = (n + WT2 - 1) / WT2;
     DevCtl *ctl = A.ctl;
     float wsmax = 0.f;
@@ -1446,7 +1446,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
 #pragma unroll
         for (int r = 0; r < 3; r++) {
             int g = c0 - 5 + 32 * r + lane;
-            if (g < 0 || g >= n) g = ghost_map(g, n, A.bc_lo, A.bc_hi);
+            if (g < 0 || g >= n) g = ghost_or_halo(g, n, A.bc_lo, A.bc_hi, A.halo);
 #pragma unroll
             for (int k = 0; k < M; k++) ur[r][k] = (r < 2 || lane < WS2 - 64) ? Us[(size_t)k * cs + g] : 0.f;
         }
@@ -1724,8 +1724,8 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
             if (A.rhs_mode) {
 #pragma unroll
                 for (int k = 0; k < M; k++) {
-                    if (updA) out[(size_t)k * cs + jA] = r[k].x;
-                    if (updB) out[(size_t)k * cs + jB] = r[k].y;
+                    if (updA) out[(size_t)k * cso + jA] = r[k].x;
+                    if (updB) out[(size_t)k * cso + jB] = r[k].y;
                 }
             } else {
                 float2 o[M];
@@ -1741,8 +1741,8 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                         // grow the solution by 6e-8 every step
                         o[k] = __ffma2_rn(f2(2.0f / 3.0f), __fadd2_rn(v, f2neg(u0r[k])), u0r[k]);
                     }
-                    if (updA) out[(size_t)k * cs + jA] = o[k].x;
-                    if (updB) out[(size_t)k * cs + jB] = o[k].y;
+                    if (updA) out[(size_t)k * cso + jA] = o[k].x;
+                    if (updB) out[(size_t)k * cso + jB] = o[k].y;
                 }
                 float oa[M], ob[M];
 #pragma unroll
@@ -1789,16 +1789,18 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     else
         fill_delta_table(s_cf);
     TileArgs<float> A;
-    A.alpha = ctl->alpha_f[p.slot_in][0];
+    A.alpha = p.alpha_in ? (float)*p.alpha_in : ctl->alpha_f[p.slot_in][0];
     A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
     A.dtD = fixed ? p.dt_fixed : ctl->dt;
-    A.Us = static_cast<const float *>(p.Us);
-    A.U0 = static_cast<const float *>(p.U0);
-    A.out = static_cast<float *>(p.out);
+    // slab mode: cell 0 follows the padding (the RHS output dU/dt is unpadded)
+    const int off = p.halo ? HALO_CELLS : 0, offo = p.rhs_mode ? 0 : off;
+    A.Us = static_cast<const float *>(p.Us) + off;
+    A.U0 = p.U0 ? static_cast<const float *>(p.U0) + off : nullptr;
+    A.out = static_cast<float *>(p.out) + offo;
     A.masks = p.masks;
     A.n = p.n;
-    A.cs = (size_t)p.n;
-    A.cso = A.cs;
+    A.cs = (size_t)p.n + 2 * off;
+    A.cso = (size_t)p.n + 2 * offo;
     A.bc_lo = p.bc_lo;
     A.bc_hi = p.bc_hi;
     A.dx = p.dx;
@@ -1811,7 +1813,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     A.rhs_mode = p.rhs_mode;
     A.stage = p.stage;
     A.ebase = 0;
-    A.halo = 0;
+    A.halo = p.halo;
     A.ctl = ctl;
     __syncthreads();
     float wsmax = tiles1d_f32_fp<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
@@ -1968,13 +1970,13 @@ cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
-    // FP32 state over the whole domain: face-paired tiles (advection when
-    // a > 0, where alpha = a makes the '-' split vanish).  Their results
-    // equal the paired-split kernel's bit for bit (the Roe frame and back
-    // projection share the roundings of roe_frame_f32/back_project_f32), so
-    // parted launches, slabs and batches, which take the paired-split tiles,
-    // agree with them.
-    if (sizeof(S) == 4 && p.tile_lo == 0 && p.tile_hi <= 0 && !p.partial && !p.halo &&
+    // FP32 state over the whole domain or a slab: face-paired tiles
+    // (advection when a > 0, where alpha = a makes the '-' split vanish).
+    // Their results equal the paired-split kernel's bit for bit (the Roe
+    // frame and back projection share the roundings of
+    // roe_frame_f32/back_project_f32), so parted launches and batches, which
+    // take the paired-split tiles, agree with them.
+    if (sizeof(S) == 4 && p.tile_lo == 0 && p.tile_hi <= 0 && !p.partial &&
         ((p.sys == SYS_ADV && p.a > 0.0) || p.sys == SYS_BURGERS || p.sys == SYS_EULER1D)) {
         const int nt2 = (p.n + WT2 - 1) / WT2;
         const int nw2 = warps_per_cta(nt2, false);
