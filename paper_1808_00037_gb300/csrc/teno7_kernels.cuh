@@ -1406,6 +1406,15 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32_kernel(cons
 // identically zero, its windows are all zero, every stencil of them is kept
 // and its polynomial is exactly zero.
 // ==========================================================================
+// 4-byte asynchronous global -> shared copies (cp.async, completion awaited
+// by cp_async_wait_all)
+static __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 constexpr int WT2 = 61;  // cells updated per face-paired warp tile
 constexpr int WS2 = 71;  // cells staged per face-paired warp tile (c0-5 .. c0+65)
 // Staging rows of the face-paired kernel hold PAIRS (value of staged cell i,
@@ -1417,7 +1426,8 @@ __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.
 
 template <int SYS, int SCH>
 __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2 (*sU)[WP2], float2 (*sgp)[WP2],
-                                                float2 (*sgm)[WP2], float2 (*spr)[WP2], const float (*s_cf)[8],
+                                                float2 (*sgm)[WP2], float2 (*spr)[WP2], float2 (*su0)[32],
+                                                const float (*s_cf)[8],
                                                 int tile0, int tstride) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -1458,12 +1468,28 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
         const int c0 = tile * WT2;
         const int jA = c0 - 2 + lane, jB = c0 + 30 + lane;  // faces, and the cells they update
         const bool updA = lane >= 2 && jA < n, updB = lane <= 30 && jB < n;
+        // U^n of cells jA and jB (stages 1 and 2).  Euler: into su0 by
+        // asynchronous copies, awaited only at the RK update, so that no
+        // register holds them through the face computations (held in
+        // registers, the loads were deferred to their use and waited for);
+        // the scalar laws, with registers to spare, load them here
+        constexpr bool U0_ASYNC = SYS == SYS_EULER1D;
+        const bool use_u0 = !A.rhs_mode && A.stage > 0;
         float2 u0r[M];
-        if (!A.rhs_mode && A.stage > 0) {
+        if (use_u0) {
             const int iA = jA < n ? jA : n - 1, iB = jB < n ? jB : n - 1;
+            if constexpr (U0_ASYNC) {
 #pragma unroll
-            for (int k = 0; k < M; k++)
-                u0r[k] = make_float2(U0[(size_t)k * cs + (iA < 0 ? 0 : iA)], U0[(size_t)k * cs + iB]);
+                for (int k = 0; k < M; k++) {
+                    cp_async4(&su0[k][lane].x, &U0[(size_t)k * cs + (iA < 0 ? 0 : iA)]);
+                    cp_async4(&su0[k][lane].y, &U0[(size_t)k * cs + iB]);
+                }
+                cp_async_commit();
+            } else {
+#pragma unroll
+                for (int k = 0; k < M; k++)
+                    u0r[k] = make_float2(U0[(size_t)k * cs + (iA < 0 ? 0 : iA)], U0[(size_t)k * cs + iB]);
+            }
         }
         float Ucur[3][M];
 #pragma unroll
@@ -1717,6 +1743,9 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
             const float yr = __shfl_sync(0xffffffffu, fh[k].y, (lane + 31) & 31);
             fprev[k] = make_float2(xr, lane == 0 ? xr : yr);
         }
+        // every lane's copies have landed before it reads them, or before its
+        // next tile issues new ones into the same slots
+        if (U0_ASYNC && use_u0) cp_async_wait_all();
         if (updA || updB) {
             float2 r[M];
 #pragma unroll
@@ -1728,6 +1757,10 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                     if (updB) out[(size_t)k * cso + jB] = r[k].y;
                 }
             } else {
+                if (U0_ASYNC && use_u0) {
+#pragma unroll
+                    for (int k = 0; k < M; k++) u0r[k] = su0[k][lane];
+                }
                 float2 o[M];
 #pragma unroll
                 for (int k = 0; k < M; k++) {
@@ -1777,6 +1810,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     __shared__ float2 s_gp[WPB][M][WP2];
     __shared__ float2 s_gm[WPB][MG][WP2];
     __shared__ float2 s_pr[WPB][NP][WP2];
+    __shared__ float2 s_u0[WPB][SYS == SYS_EULER1D ? M : 1][32];  // U^n of the cells a lane updates (cp.async)
     __shared__ __align__(16) float s_cf[32][8];
     __shared__ float s_red[WPB];
 
@@ -1816,7 +1850,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     A.halo = p.halo;
     A.ctl = ctl;
     __syncthreads();
-    float wsmax = tiles1d_f32_fp<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_cf,
+    float wsmax = tiles1d_f32_fp<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_u0[warp], s_cf,
                                            blockIdx.x * nw + warp, gridDim.x * nw);
     (void)lane;
     if (!p.rhs_mode) {

@@ -1010,12 +1010,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
 // Dynamic shared memory: ry [4][29][33]; gp, gm, pr [4][39][33]; raw
 // [4][39][32]; Delta table [32][8]; reductions [2][WPB].
 // --------------------------------------------------------------------------
-static __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// (cp_async4, cp_async_commit, cp_async_wait_all: teno7_kernels.cuh)
 
 // ==========================================================================
 // FP32 2D faces in PAIRS (the 1D face-paired kernel's design, 4 fields): every
