@@ -424,11 +424,14 @@ def bench_advection(args, torch, B, dist, world):
     U0, dx, _ = I.advection_sine(n)
     hbm_peak, peak_kind = peaks()
     out = {"workload": f"advection sin(pi x) on [-1,1], N={n}, periodic, CFL 0.2"}
-    for name, prec, dtype, steps in (("f32", B.T7_F32, torch.float32, args.steps),
-                                     ("f64", B.T7_F64, torch.float64, max(2, args.steps // 10))):
+    # FP32: a step takes ~0.25 ms, so 100 timed steps after 10 warm-up steps
+    # (a 20-step region right after the upload read ~15% low: the device had
+    # not settled)
+    for name, prec, dtype, steps, warm in (("f32", B.T7_F32, torch.float32, max(args.steps, 100), max(args.warmup, 10)),
+                                           ("f64", B.T7_F64, torch.float64, max(2, args.steps // 10), args.warmup)):
         ctx = B.Context(B.T7_SCALAR_ADVECTION, n, dx, prec=prec, bc=(0, 0, 0, 0), adv_speed=1.0)
         U = torch.tensor(U0, dtype=dtype, device="cuda")
-        ctx.run(U, 0.2, max_steps=args.warmup)
+        ctx.run(U, 0.2, max_steps=warm)
         torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
