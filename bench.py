@@ -559,33 +559,43 @@ def bench_accuracy(args, torch, B):
 
 
 def bench_strong(args, torch, B, U0, dx, dist, world, rank):
-    """Strong scaling: the one tiled Shu-Osher domain split into `world` slabs,
-    one per rank, each advanced by the CUDA slab stages with 4-cell halos
-    exchanged by NCCL point-to-point messages and the alpha of every stage
-    all-reduced (max) on the device (paper_1808_00037_gb300.decomp).  FP32,
-    CFL steps as in the primary line."""
+    """Strong scaling: one domain split into `world` slabs, one per rank, each
+    advanced by the CUDA slab stages with 4-cell (row) halos exchanged by NCCL
+    point-to-point messages and the alphas of every stage all-reduced (max)
+    on the device (paper_1808_00037_gb300.decomp): the 16.8M-cell tiled
+    Shu-Osher domain (1D) and the 2048^2 quadrant domain (2D, split along y).
+    FP32, CFL steps as in the primary lines."""
     from paper_1808_00037_gb300 import decomp
-    lo, hi = decomp.partition(U0.shape[1], world, rank)
-    ctx = B.Context(B.T7_EULER1D, hi - lo, dx, prec=B.T7_F32, gamma=GAMMA)
-    slab = decomp.Slab(decomp.CudaSlab(ctx), torch.tensor(U0[:, lo:hi], dtype=torch.float32, device="cuda"))
-    comm = decomp.RankSlabs(slab, periodic=False)
-    dt_of = decomp.cfl_dt_1d(dx, CFL)
-    decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.warmup)
-    torch.cuda.synchronize()
-    dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    steps, _ = decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.steps)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    t = torch.tensor([el], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    el = float(t.item())
-    ctx.close()
-    return {"value": U0.shape[1] * steps / el / 1e9, "unit": "Gcell-steps/s", "ms_per_step": el / steps * 1e3,
-            "steps": steps, "scaling": "strong", "cells_total": int(U0.shape[1]),
-            "timing": "host wall clock between barriers and device synchronisations (max over ranks)",
-            "parallelism": f"slab decomposition over {world} ranks, NCCL halos + all-reduce(max) of alpha"}
+    U2, dx2, dy2, _ = I.quadrants_2d(2024, 2048, 2048)
+    out = {"scaling": "strong",
+           "timing": "host wall clock between barriers and device synchronisations (max over ranks)",
+           "parallelism": f"slab decomposition over {world} ranks, NCCL halos + all-reduce(max) of alpha"}
+    for name, U, sysid, dt_of, nalpha in (("euler1d", U0, B.T7_EULER1D, decomp.cfl_dt_1d(dx, CFL), 1),
+                                          ("euler2d", U2, B.T7_EULER2D, decomp.cfl_dt_2d(dx2, dy2, 0.4), 2)):
+        lo, hi = decomp.partition(U.shape[1], world, rank)
+        if sysid == B.T7_EULER2D:
+            ctx = B.Context(sysid, U.shape[2], dx2, ny=hi - lo, dy=dy2, prec=B.T7_F32, bc=(1, 1, 1, 1), gamma=GAMMA)
+        else:
+            ctx = B.Context(sysid, hi - lo, dx, prec=B.T7_F32, gamma=GAMMA)
+        slab = decomp.Slab(decomp.CudaSlab(ctx), torch.tensor(U[:, lo:hi], dtype=torch.float32, device="cuda"),
+                           nalpha=nalpha)
+        comm = decomp.RankSlabs(slab, periodic=False)
+        decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.warmup)
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, _ = decomp.rk3_run_slabs(comm, dt_of, t_end=math.inf, max_steps=args.steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+        ctx.close()
+        cells = U[0].size
+        out[name] = {"value": cells * steps / el / 1e9, "unit": "Gcell-steps/s", "ms_per_step": el / steps * 1e3,
+                     "steps": steps, "cells_total": int(cells)}
+    return out
 
 
 def bench_slabs_local(args, torch, B, U1, dx1, nslabs=2):
