@@ -24,6 +24,14 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                   Sod and Lax tubes; exact shift for advection.
   rhs_2d / run_2d              -- reduces to the 1D scheme on y-independent
                                   data; x/y transpose symmetry.
+  alpha_mode(ALPHA_PER_FIELD)  -- per-field alphas: maxima equal to the closed-form
+  / alpha_fields_1d                 |u - c|, |u|, |u + c| over the cells, their
+  / face_split_1d                   maximum equal to the global alpha bit for bit;
+                                  with every field's alpha set to the global one
+                                  the RHS equals the global split's to round-off;
+                                  conservation; on an entropy wave (u, p
+                                  constant) the entropy field's '-' split
+                                  vanishes (it does with alpha_1 = |u| only).
   rhs_1d_tl / rk3_step_1d_tl   -- tangent linear with frozen selection and alpha:
   / run_1d_tl                     value parts bit-identical to the primal,
                                   derivative against fourth-order central
@@ -90,6 +98,9 @@ def lib() -> ctypes.CDLL:
         _lib.or_rhs_1d_tl.argtypes = [i, p, p, i, d, d, d, i, i, d, p, p, p]
         _lib.or_rk3_step_1d_tl.argtypes = [i, p, p, i, d, d, d, d, d, i, i, d]
         _lib.or_run_1d_tl.argtypes = [i, p, p, i, d, d, d, d, d, i, i, d, i]
+        _lib.or_set_alpha_mode.argtypes = [i]
+        _lib.or_alpha_fields_1d.argtypes = [i, p, i, d, d, p]
+        _lib.or_face_split_1d.argtypes = [i, p, i, d, d, i, i, d, i, p, p]
     return _lib
 
 
@@ -128,6 +139,45 @@ class scheme:
 
     def __exit__(self, *a):
         lib().or_set_scheme(self.prev)
+
+
+ALPHA_GLOBAL, ALPHA_PER_FIELD = 0, 1
+
+
+class alpha_mode:
+    """Context manager selecting the oracle's Lax-Friedrichs alpha for the 1D
+    systems: one global alpha (default, the paper's choice) or one per
+    characteristic field, alpha_k = max_i |lambda_k(U_i)|."""
+
+    def __init__(self, which: int):
+        self.which = which
+
+    def __enter__(self):
+        self.prev = lib().or_get_alpha_mode()
+        lib().or_set_alpha_mode(self.which)
+        return self
+
+    def __exit__(self, *a):
+        lib().or_set_alpha_mode(self.prev)
+
+
+def alpha_fields_1d(sys, U, *, gamma=1.4, a=1.0):
+    """Per-field alphas max_i |lambda_k(U_i)| (Euler: u - c, u, u + c)."""
+    U = _f64(U).reshape(nvars(sys), -1)
+    out = np.zeros(nvars(sys))
+    _check(lib().or_alpha_fields_1d(sys, _ptr(U), U.shape[1], gamma, a, _ptr(out)), "alpha_fields_1d", True)
+    return out
+
+
+def face_split_1d(sys, U, i, *, gamma=1.4, a=1.0, bc=(BC_PERIODIC, BC_PERIODIC), alpha=-1.0):
+    """Characteristic split values of face i+1/2 as the sweep forms them:
+    (Pp[m, 7], Pm[m, 7]) -- '+' of field k at cells i-3+t, '-' at i+4-t."""
+    U = _f64(U).reshape(nvars(sys), -1)
+    m = nvars(sys)
+    Pp, Pm = np.zeros((m, 7)), np.zeros((m, 7))
+    st = lib().or_face_split_1d(sys, _ptr(U), U.shape[1], gamma, a, bc[0], bc[1], alpha, i, _ptr(Pp), _ptr(Pm))
+    _check(st, "face_split_1d", True)
+    return Pp, Pm
 
 
 def coeffs5() -> np.ndarray:

@@ -24,6 +24,10 @@
  * A scheme switch (or_set_scheme) replaces pass 2 by the fifth-order TENO
  * baseline the paper compares with: each face's own three bits select a
  * Table co1 polynomial (epsilon 1e-40 as given with Eq. TENO1).
+ * An alpha switch (or_set_alpha_mode; 1D systems) replaces the one global
+ * Lax-Friedrichs alpha by one per characteristic field, alpha_k = max_i
+ * |lambda_k(U_i)|, each field's split flux formed from the projections of
+ * the flux and the state, q+-_k = (L_k F +- alpha_k L_k U) / 2.
  * The 2D form (or_rhs_2d, or_run_2d) applies the same face procedure
  * dimension by dimension, each direction in its own characteristic frame.
  *
@@ -110,6 +114,12 @@ static const double CO1[7][5] = {
 static int g_scheme = SCHEME_TENO7EXT;
 void or_set_scheme(int scheme) { g_scheme = scheme; }
 int or_get_scheme(void) { return g_scheme; }
+
+/* Alpha switch (1D systems): 0 = one global Lax-Friedrichs alpha (Sec. "One
+ * dimensional Euler equations"), 1 = one alpha per characteristic field. */
+static int g_alpha_mode = 0;
+void or_set_alpha_mode(int mode) { g_alpha_mode = mode; }
+int or_get_alpha_mode(void) { return g_alpha_mode; }
 
 /* Table co1 row for the three cutoff bits d0 | d1<<1 | d2<<2, -1 if none. */
 int or_select5(int bits) {
@@ -398,11 +408,37 @@ static int frame(const sysdef *S, int dir, const double *UL, const double *UR, d
 /* Writes the face fluxes Fh[c][i+1], i = -1..n-1 (face i+1/2) and, if masks  */
 /* is non-null, the Delta codes masks[(s*m + k)*(n+1) + i+1].                 */
 /* ------------------------------------------------------------------------ */
-static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, double eps, double CT, double **Fh,
-                 uint8_t *masks) {
+/* Characteristic split values of field k at padded cell l, split sign
+ * (0: '+', 1: '-').  One alpha (alf == NULL): L_k G+- with the split fluxes
+ * G+- = (F +- alpha U)/2 of the cell; per field (alf[k]): (L_k F +- alf[k]
+ * L_k U)/2 with the cell's flux F and state U (arrays FF and UU). */
+typedef struct {
+    const double *Gp, *Gm, *FF, *UU, *alf;
+    int m, np;
+} splitdef;
+
+static double split_value(const splitdef *D, const double L[4][4], int k, int l, int sign) {
+    if (!D->alf) {
+        const double *G = sign ? D->Gm : D->Gp;
+        double s = L[k][0] * G[l];
+        for (int c = 1; c < D->m; c++) s = s + L[k][c] * G[c * D->np + l];
+        return s;
+    }
+    double lf = L[k][0] * D->FF[l], lu = L[k][0] * D->UU[l];
+    for (int c = 1; c < D->m; c++) {
+        lf = lf + L[k][c] * D->FF[c * D->np + l];
+        lu = lu + L[k][c] * D->UU[c * D->np + l];
+    }
+    return sign ? 0.5 * (lf - D->alf[k] * lu) : 0.5 * (lf + D->alf[k] * lu);
+}
+
+/* alf (nullable): per-field alphas (the alpha switch); NULL: one global alpha */
+static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, const double *alf, double eps, double CT,
+                 double **Fh, uint8_t *masks) {
     int m = S->m, np = n + 2 * NG;
     int status = OR_OK;
-    /* global Lax-Friedrichs split fluxes G+- = (F +- alpha U)/2 per cell */
+    /* global Lax-Friedrichs split fluxes G+- = (F +- alpha U)/2 per cell, or
+     * (per-field alphas) the cell's flux and state */
     double *Gp = (double *)malloc(sizeof(double) * m * np);
     double *Gm = (double *)malloc(sizeof(double) * m * np);
     for (int l = 0; l < np; l++) {
@@ -410,10 +446,16 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
         for (int c = 0; c < m; c++) U[c] = P[c][l];
         flux(S, dir, U, F);
         for (int c = 0; c < m; c++) {
-            Gp[c * np + l] = 0.5 * (F[c] + alpha * U[c]);
-            Gm[c * np + l] = 0.5 * (F[c] - alpha * U[c]);
+            if (alf) {
+                Gp[c * np + l] = F[c];
+                Gm[c * np + l] = U[c];
+            } else {
+                Gp[c * np + l] = 0.5 * (F[c] + alpha * U[c]);
+                Gm[c * np + l] = 0.5 * (F[c] - alpha * U[c]);
+            }
         }
     }
+    splitdef D = {Gp, Gm, Gp, Gm, alf, m, np};
     /* pass 1: every face's bits in its own characteristic frame */
     int nf = n + 3;
     int *bits = (int *)malloc(sizeof(int) * 2 * m * nf); /* [s][k][face] */
@@ -428,13 +470,8 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
             double wp[5], wm[5];
             for (int t = 0; t < 5; t++) {
                 int lp = j - 2 + t + NG, lm = j + 3 - t + NG;
-                double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
-                for (int c = 1; c < m; c++) {
-                    sp = sp + L[k][c] * Gp[c * np + lp];
-                    sm = sm + L[k][c] * Gm[c * np + lm];
-                }
-                wp[t] = sp;
-                wm[t] = sm;
+                wp[t] = split_value(&D, L, k, lp, 0);
+                wm[t] = split_value(&D, L, k, lm, 1);
             }
             bits[(0 * m + k) * nf + j + 2] = or_face_bits(wp, eps, CT, NULL);
             bits[(1 * m + k) * nf + j + 2] = or_face_bits(wm, eps, CT, NULL);
@@ -462,13 +499,8 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
                 double vp[5], vm[5];
                 for (int t = 0; t < 5; t++) {
                     int lp = i - 2 + t + NG, lm = i + 3 - t + NG;
-                    double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
-                    for (int c = 1; c < m; c++) {
-                        sp = sp + L[k][c] * Gp[c * np + lp];
-                        sm = sm + L[k][c] * Gm[c * np + lm];
-                    }
-                    vp[t] = sp;
-                    vm[t] = sm;
+                    vp[t] = split_value(&D, L, k, lp, 0);
+                    vm[t] = split_value(&D, L, k, lm, 1);
                 }
                 f[k] = poly5(rp, vp) + poly5(rm, vm);
                 if (masks) {
@@ -491,13 +523,8 @@ static int sweep(const sysdef *S, int dir, double **P, int n, double alpha, doub
             double vp[7], vm[7];
             for (int t = 0; t < 7; t++) {
                 int lp = i - 3 + t + NG, lm = i + 4 - t + NG;
-                double sp = L[k][0] * Gp[lp], sm = L[k][0] * Gm[lm];
-                for (int c = 1; c < m; c++) {
-                    sp = sp + L[k][c] * Gp[c * np + lp];
-                    sm = sm + L[k][c] * Gm[c * np + lm];
-                }
-                vp[t] = sp;
-                vm[t] = sm;
+                vp[t] = split_value(&D, L, k, lp, 0);
+                vm[t] = split_value(&D, L, k, lm, 1);
             }
             f[k] = poly(mp, vp) + poly(mm, vm);
             if (masks) {
@@ -545,11 +572,48 @@ static double alpha_1d(const sysdef *S, const double *U, int n, int *bad) {
     return a;
 }
 
+/* Per-field alphas of a 1D state: alf[k] = max_i |lambda_k(U_i)| over interior
+ * cells, lambda = (u - c, u, u + c) for Euler, the one wave speed for the
+ * scalar laws.  max_k alf[k] equals the global alpha bit for bit (|u| + c is
+ * the larger of |u - c| and |u + c|, rounded alike). */
+static void alpha_fields_1d(const sysdef *S, const double *U, int n, int *bad, double *alf) {
+    for (int k = 0; k < S->m; k++) alf[k] = 0.0;
+    for (int i = 0; i < n; i++) {
+        double Uc[4];
+        for (int c = 0; c < S->m; c++) Uc[c] = U[c * n + i];
+        if (S->sys != SYS_EULER1D) {
+            double s = wavespeed(S, 0, Uc, bad);
+            if (s > alf[0] || s != s) alf[0] = s;
+            continue;
+        }
+        double u = Uc[1] / Uc[0];
+        double p = (S->gamma - 1.0) * (Uc[2] - 0.5 * Uc[1] * u);
+        double c = sqrt(S->gamma * p / Uc[0]);
+        if (!(Uc[0] > 0.0) || !(p > 0.0)) *bad |= 1;
+        if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2])) *bad |= 2;
+        double lam[3] = {fabs(u - c), fabs(u), fabs(u + c)};
+        for (int k = 0; k < 3; k++)
+            if (lam[k] > alf[k] || lam[k] != lam[k]) alf[k] = lam[k];
+    }
+}
+
+int or_alpha_fields_1d(int sys, const double *U, int n, double gamma, double a, double *alf) {
+    if (n < 1 || !check_sys(sys, BC_PERIODIC, BC_PERIODIC)) return OR_EINVAL;
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int bad = 0;
+    alpha_fields_1d(&S, U, n, &bad, alf);
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 1D right-hand side L(U) = -(F_{i+1/2} - F_{i-1/2})/dx (Eq. app).           */
 /*   U, dUdt: [m][n] row-major (variable-major).  alpha_in < 0: computed from */
 /*   U; otherwise used as given.  masks (nullable): [2][m][n+1] Delta codes.  */
-/*   alpha_out (nullable) receives the alpha used.                            */
+/*   alpha_out (nullable) receives the alpha used.  Alpha switch = 1: the     */
+/*   per-field alphas of U (alpha_in >= 0: that value for every field), and   */
+/*   alpha_out receives their maximum.                                        */
 /* ------------------------------------------------------------------------ */
 int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a, double CT, double eps_in,
               int bc_lo, int bc_hi, double alpha_in, double *dUdt, uint8_t *masks, double *alpha_out) {
@@ -561,6 +625,8 @@ int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a
      * 1e-40 for TENO5 (as given with Eq. TENO1) */
     double eps = (eps_in < 0.0) ? (g_scheme == SCHEME_TENO5 ? 1e-40 : dx * dx * dx) : eps_in;
     double alpha = (alpha_in < 0.0) ? alpha_1d(&S, U, n, &bad) : alpha_in;
+    double alf[4] = {alpha, alpha, alpha, alpha};
+    if (g_alpha_mode && alpha_in < 0.0) alpha_fields_1d(&S, U, n, &bad, alf);
     if (alpha_out) *alpha_out = alpha;
     double *P[4], *Fh[4];
     for (int c = 0; c < m; c++) {
@@ -568,7 +634,7 @@ int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a
         Fh[c] = (double *)malloc(sizeof(double) * (n + 1));
         for (int l = -NG; l < n + NG; l++) P[c][l + NG] = U[c * n + ghost_index(l, n, bc_lo, bc_hi)];
     }
-    int status = sweep(&S, 0, P, n, alpha, eps, CT, Fh, masks);
+    int status = sweep(&S, 0, P, n, alpha, g_alpha_mode ? alf : NULL, eps, CT, Fh, masks);
     for (int c = 0; c < m; c++)
         for (int i = 0; i < n; i++) dUdt[c * n + i] = (Fh[c][i] - Fh[c][i + 1]) / dx;
     for (int c = 0; c < m; c++) {
@@ -578,6 +644,47 @@ int or_rhs_1d(int sys, const double *U, int n, double dx, double gamma, double a
     if (bad & 2) return OR_ENONFINITE;
     if (bad & 1) return OR_ENONPHYSICAL;
     return status;
+}
+
+/* The characteristic split values of face i+1/2 (i = -1 .. n-1) of a 1D
+ * state, as the sweep forms them: Pp[k*7 + t] = '+' value of field k at cell
+ * i-3+t, Pm[k*7 + t] = '-' value at cell i+4-t, in the face's Roe frame, with
+ * the alphas of or_rhs_1d (alpha_in < 0: from U; the alpha switch applies). */
+int or_face_split_1d(int sys, const double *U, int n, double gamma, double a, int bc_lo, int bc_hi, double alpha_in,
+                     int i, double *Pp, double *Pm) {
+    if (n < 1 || i < -1 || i > n - 1 || !check_sys(sys, bc_lo, bc_hi)) return OR_EINVAL;
+    sysdef S = {sys, nvars_of(sys), gamma, a};
+    int m = S.m, np = n + 2 * NG, bad = 0;
+    double alpha = (alpha_in < 0.0) ? alpha_1d(&S, U, n, &bad) : alpha_in;
+    double alf[4] = {alpha, alpha, alpha, alpha};
+    if (g_alpha_mode && alpha_in < 0.0) alpha_fields_1d(&S, U, n, &bad, alf);
+    double *G[2];
+    for (int h = 0; h < 2; h++) G[h] = (double *)malloc(sizeof(double) * m * np);
+    for (int l = 0; l < np; l++) {
+        double Uc[4], F[4];
+        for (int c = 0; c < m; c++) Uc[c] = U[c * n + ghost_index(l - NG, n, bc_lo, bc_hi)];
+        flux(&S, 0, Uc, F);
+        for (int c = 0; c < m; c++) {
+            G[0][c * np + l] = g_alpha_mode ? F[c] : 0.5 * (F[c] + alpha * Uc[c]);
+            G[1][c * np + l] = g_alpha_mode ? Uc[c] : 0.5 * (F[c] - alpha * Uc[c]);
+        }
+    }
+    splitdef D = {G[0], G[1], G[0], G[1], g_alpha_mode ? alf : NULL, m, np};
+    double L[4][4], R[4][4], UL[4], UR[4];
+    for (int c = 0; c < m; c++) {
+        UL[c] = U[c * n + ghost_index(i, n, bc_lo, bc_hi)];
+        UR[c] = U[c * n + ghost_index(i + 1, n, bc_lo, bc_hi)];
+    }
+    if (frame(&S, 0, UL, UR, L, R)) bad |= 1;
+    for (int k = 0; k < m; k++)
+        for (int t = 0; t < 7; t++) {
+            Pp[k * 7 + t] = split_value(&D, L, k, i - 3 + t + NG, 0);
+            Pm[k * 7 + t] = split_value(&D, L, k, i + 4 - t + NG, 1);
+        }
+    for (int h = 0; h < 2; h++) free(G[h]);
+    if (bad & 2) return OR_ENONFINITE;
+    if (bad & 1) return OR_ENONPHYSICAL;
+    return OR_OK;
 }
 
 /* Third-order SSP Runge-Kutta step (Shu-Osher form), in place on U[m][n]. */
@@ -668,7 +775,7 @@ static void alpha_2d(const sysdef *S, const double *U, int nx, int ny, double *a
 int or_rhs_2d(const double *U, int nx, int ny, double dx, double dy, double gamma, double CT, double eps_x_in,
               double eps_y_in, const int *bc, const double *alpha_in, double *dUdt, uint8_t *masks,
               double *alpha_out) {
-    if (nx < 1 || ny < 1) return OR_EINVAL;
+    if (nx < 1 || ny < 1 || g_alpha_mode) return OR_EINVAL;  /* the alpha switch is 1D only */
     sysdef S = {SYS_EULER2D, 4, gamma, 0.0};
     int N = nx * ny, bad = 0, status = OR_OK;
     double ax, ay;
@@ -697,7 +804,7 @@ int or_rhs_2d(const double *U, int nx, int ny, double dx, double dy, double gamm
         uint8_t *mk = masks ? masks + (size_t)y * (nx + 1) : NULL;
         /* per-row masks are scattered below, so sweep into a temporary */
         uint8_t *tmp = masks ? (uint8_t *)malloc(2 * 4 * (nx + 1)) : NULL;
-        int st = sweep(&S, 0, P, nx, ax, epsx, CT, Fh, tmp);
+        int st = sweep(&S, 0, P, nx, ax, NULL, epsx, CT, Fh, tmp);
         if (st) status = st;
         for (int c = 0; c < 4; c++)
             for (int i = 0; i < nx; i++) dUdt[c * N + y * nx + i] = (Fh[c][i] - Fh[c][i + 1]) / dx;
@@ -712,7 +819,7 @@ int or_rhs_2d(const double *U, int nx, int ny, double dx, double dy, double gamm
         for (int c = 0; c < 4; c++)
             for (int l = -NG; l < ny + NG; l++) P[c][l + NG] = U[c * N + ghost_index(l, ny, bc[2], bc[3]) * nx + x];
         uint8_t *tmp = masks ? (uint8_t *)malloc(2 * 4 * (ny + 1)) : NULL;
-        int st = sweep(&S, 1, P, ny, ay, epsy, CT, Fh, tmp);
+        int st = sweep(&S, 1, P, ny, ay, NULL, epsy, CT, Fh, tmp);
         if (st) status = st;
         for (int c = 0; c < 4; c++)
             for (int j = 0; j < ny; j++) {
@@ -990,7 +1097,8 @@ static void sweep_tl(const sysdef *S, dual **P, int n, double alpha, const uint8
  * by or_rhs_1d for U) frozen.  U, dU, L, dL: [m][n]. */
 int or_rhs_1d_tl(int sys, const double *U, const double *dU, int n, double dx, double gamma, double a, int bc_lo,
                  int bc_hi, double alpha, const uint8_t *masks, double *L, double *dL) {
-    if (n < 1 || !check_sys(sys, bc_lo, bc_hi) || !(dx > 0.0) || !masks || g_scheme != SCHEME_TENO7EXT)
+    if (n < 1 || !check_sys(sys, bc_lo, bc_hi) || !(dx > 0.0) || !masks || g_scheme != SCHEME_TENO7EXT ||
+        g_alpha_mode)
         return OR_EINVAL;
     sysdef S = {sys, nvars_of(sys), gamma, a};
     int m = S.m, np = n + 2 * NG;
