@@ -72,6 +72,17 @@ typedef enum { T7_SCALAR_ADVECTION = 0, T7_EULER1D = 1, T7_EULER2D = 2, T7_BURGE
  * 1D systems through t7_euler_rhs, t7_cfl_dt, t7_rk3_step, t7_run and
  * t7_run_host; the other entry points reject a TENO5 context (T7_EINVAL). */
 typedef enum { T7_TENO7EXT = 0, T7_TENO5 = 1 } t7_scheme;
+/* Lax-Friedrichs splitting.  T7_ALPHA_GLOBAL: one alpha = max_i (|u_i| + c_i)
+ * over the domain, the paper's global Lax-Friedrichs splitting (Sec. "One
+ * dimensional Euler equations").  T7_ALPHA_PER_FIELD: one alpha per
+ * characteristic field, alpha_k = max_i |lambda_k(U_i)| (1D Euler: u - c, u,
+ * u + c), each field's split values formed from the projections of the flux
+ * and the state in the face's frame, q+-_k = (L_k F +- alpha_k L_k U) / 2;
+ * the CFL step is that of the global alpha (the largest alpha_k equals it).
+ * Provided for 1D Euler in FP64 and FP32 with TENO7-ext through t7_euler_rhs,
+ * t7_cfl_dt, t7_rk3_step and t7_run; any other combination is refused by
+ * t7_create, and the other entry points refuse such a context (T7_EINVAL). */
+typedef enum { T7_ALPHA_GLOBAL = 0, T7_ALPHA_PER_FIELD = 1 } t7_alpha_mode;
 
 /* Grid and parameters of one problem.  Cell-centred uniform grid with cell
  * widths dx, dy; four ghost cells per side are built inside the kernels from
@@ -83,7 +94,8 @@ typedef enum { T7_TENO7EXT = 0, T7_TENO5 = 1 } t7_scheme;
  *             the paper's choice (Sec. "The parameter epsilon"), or 1e-40
  *             for TENO5 (the value given with Eq. TENO1).
  *   scheme    t7_scheme (zero-initialised grids get TENO7-ext).  In FP32,
- *             TENO5's epsilon is raised to FLT_MIN (1e-40 is subnormal).   */
+ *             TENO5's epsilon is raised to FLT_MIN (1e-40 is subnormal).
+ *   alpha_mode t7_alpha_mode (zero-initialised grids get the global alpha). */
 typedef struct {
     int sys;  /* t7_system */
     int prec; /* t7_prec   */
@@ -92,6 +104,7 @@ typedef struct {
     int bc[4];
     double gamma, adv_speed, CT, eps_x, eps_y;
     int scheme; /* t7_scheme */
+    int alpha_mode; /* t7_alpha_mode */
 } t7_grid;
 
 typedef struct t7_ctx t7_ctx;

@@ -21,6 +21,7 @@ T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
 T7_F64, T7_F32, T7_MIXED = 0, 1, 2
 T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
 T7_TENO7EXT, T7_TENO5 = 0, 1
+T7_ALPHA_GLOBAL, T7_ALPHA_PER_FIELD = 0, 1
 T7_PROBE_F32, T7_PROBE_F32X2, T7_PROBE_F64 = 0, 1, 2
 
 _STATUS = {0: "T7_OK", -1: "T7_EINVAL", -2: "T7_ECUDA", -3: "T7_ENONPHYSICAL", -4: "T7_ENONFINITE",
@@ -37,7 +38,8 @@ class t7_grid(ctypes.Structure):
     _fields_ = [("sys", ctypes.c_int), ("prec", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("gamma", ctypes.c_double), ("adv_speed", ctypes.c_double), ("CT", ctypes.c_double),
-                ("eps_x", ctypes.c_double), ("eps_y", ctypes.c_double), ("scheme", ctypes.c_int)]
+                ("eps_x", ctypes.c_double), ("eps_y", ctypes.c_double), ("scheme", ctypes.c_int),
+                ("alpha_mode", ctypes.c_int)]
 
 
 _lib = None
@@ -99,7 +101,7 @@ class Context:
 
     def __init__(self, sys: int, nx: int, dx: float, *, prec: int = T7_F64, ny: int = 1, dy: float = 0.0,
                  bc=(T7_BC_PERIODIC,) * 4, gamma: float = 1.4, adv_speed: float = 1.0, CT: float = 1e-5,
-                 eps_x: float = -1.0, eps_y: float = -1.0, scheme: int = 0, stream=None):
+                 eps_x: float = -1.0, eps_y: float = -1.0, scheme: int = 0, alpha_mode: int = 0, stream=None):
         import torch
         self._torch = torch
         self.lib = load()
@@ -108,7 +110,8 @@ class Context:
         self.dtype = torch.float32 if prec == T7_F32 else torch.float64  # mixed: FP64 state
         self.np_dtype = np.float32 if prec == T7_F32 else np.float64
         bc = tuple(bc) + (T7_BC_PERIODIC,) * (4 - len(bc))
-        g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y, scheme)
+        g = t7_grid(sys, prec, nx, ny, dx, dy, (ctypes.c_int * 4)(*bc), gamma, adv_speed, CT, eps_x, eps_y, scheme,
+                    alpha_mode)
         self.scheme = scheme
         self.grid = g
         if stream is None:

@@ -91,7 +91,7 @@ double eps_of(double eps, double d, int scheme = T7_TENO7EXT) {
 }
 
 __global__ void ctl_begin_kernel(t7::DevCtl *ctl, double t_end, double cfl, double dx, double dy, int max_steps) {
-    for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = 0ull;
+    for (int s = 0; s < 3; s++) ctl->amax[s][0] = ctl->amax[s][1] = ctl->amax[s][2] = 0ull;
     ctl->t = 0.0;
     ctl->dt = 0.0;
     ctl->t_end = t_end;
@@ -121,6 +121,7 @@ t7::Stage1D stage_params(t7_ctx *c, const void *Us, const void *U0, void *out) {
     p.a = c->g.adv_speed;
     p.ctl = c->ctl;
     p.scheme = c->g.scheme;
+    p.alpha_mode = c->g.alpha_mode;
     p.f_dx = (float)p.dx;
     p.f_eps = (float)p.eps;
     p.f_CT = (float)p.CT;
@@ -189,6 +190,7 @@ cudaError_t alpha_launch(t7_ctx *c, const void *U) {
     a.a = c->g.adv_speed;
     a.ctl = c->ctl;
     a.slot = 0;
+    a.alpha_mode = c->g.alpha_mode;
     // (a mixed-precision state is FP64)
     return c->g.prec != T7_F32 ? t7::launch_alpha1d_f64(a, c->stream) : t7::launch_alpha1d_f32(a, c->stream);
 }
@@ -326,6 +328,11 @@ t7_status t7_create(const t7_grid *g, void *stream, t7_ctx **out) {
     if (!(g->CT > 0.0 && g->CT < 1.0)) return T7_EINVAL;
     if (g->scheme != T7_TENO7EXT && g->scheme != T7_TENO5) return T7_EINVAL;
     if (g->scheme == T7_TENO5 && !is_1d(g->sys)) return T7_EINVAL;  // the baseline runs the 1D systems
+    if (g->alpha_mode != T7_ALPHA_GLOBAL && g->alpha_mode != T7_ALPHA_PER_FIELD) return T7_EINVAL;
+    // per-field alphas: 1D Euler, TENO7-ext, FP64 or FP32
+    if (g->alpha_mode == T7_ALPHA_PER_FIELD &&
+        (g->sys != T7_EULER1D || g->scheme != T7_TENO7EXT || g->prec == T7_MIXED))
+        return T7_EINVAL;
     t7_ctx *c = new (std::nothrow) t7_ctx();  // value-initialised: every pointer and count zero
     if (!c) return T7_ENOMEM;
     c->g = *g;
@@ -475,6 +482,16 @@ t7_status t7_cfl_dt(t7_ctx *c, const void *U, double cfl, double *dt_out) {
     unsigned long long bits = c->ctl_host->amax[0][0], bits_y = c->ctl_host->amax[0][1];
     memcpy(&alpha, &bits, sizeof(alpha));
     memcpy(&alpha_y, &bits_y, sizeof(alpha_y));
+    if (c->g.alpha_mode == T7_ALPHA_PER_FIELD) {
+        // the CFL step of the largest per-field alpha (equal to the global alpha)
+        for (int k = 1; k < 3; k++) {
+            double ak;
+            unsigned long long bk = c->ctl_host->amax[0][k];
+            memcpy(&ak, &bk, sizeof(ak));
+            alpha = fmax(alpha, ak);
+        }
+        alpha_y = 0.0;
+    }
     if (c->g.sys == T7_EULER2D)
         *dt_out = cfl / (alpha / c->g.dx + alpha_y / c->g.dy);
     else
@@ -499,6 +516,7 @@ t7_status t7_rk3_step(t7_ctx *c, void *U, double dt) {
 // alpha passed in as a device value (see include/teno7.h).
 static t7_status slab_check(t7_ctx *c, const char *what) {
     if (!c) return T7_EINVAL;
+    if (c->g.alpha_mode != T7_ALPHA_GLOBAL) return fail(c, T7_EINVAL, "%s: slabs take the global alpha", what);
     if (!is_1d(c->g.sys) && c->g.sys != T7_EULER2D) return fail(c, T7_EINVAL, "%s: not a slab system", what);
     return T7_OK;
 }
@@ -739,6 +757,7 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
     TraceRange trace("t7_run_host");
     t7_status st = check_sys(c);
     if (st) return st;
+    if (c->g.alpha_mode != T7_ALPHA_GLOBAL) return fail(c, T7_EINVAL, "t7_run_host takes the global alpha");
     if (!U_host || !(cfl > 0.0) || max_steps < 0 || !(t_end >= 0.0))
         return fail(c, T7_EINVAL, "t7_run_host: bad argument");
     size_t bytes = c->ncell * c->m * c->esize;
@@ -764,6 +783,7 @@ t7_status t7_run_host(t7_ctx *c, void *U_host, double cfl, double t_end, int max
 // -------------------------------------------------------------- adjoint ----
 static t7_status adj_check(t7_ctx *c) {
     if (!c) return T7_EINVAL;
+    if (c->g.alpha_mode != T7_ALPHA_GLOBAL) return fail(c, T7_EINVAL, "the adjoint takes the global alpha");
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "the adjoint takes a 1D Euler context");
     if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
         return fail(c, T7_EINVAL, "the adjoint takes a TENO7-ext FP64 or FP32 context");
@@ -1127,6 +1147,7 @@ static cudaError_t batch_launch(t7_ctx *c, void *U, int ntubes, double t_end, do
 
 static t7_status batch_check(t7_ctx *c, void *U, const int64_t *offsets, const double *dx, int ntubes) {
     if (!c) return T7_EINVAL;
+    if (c->g.alpha_mode != T7_ALPHA_GLOBAL) return fail(c, T7_EINVAL, "batches take the global alpha");
     if (c->g.sys != T7_EULER1D) return fail(c, T7_EINVAL, "batches take a 1D Euler context");
     if (c->g.scheme != T7_TENO7EXT || c->g.prec == T7_MIXED)
         return fail(c, T7_EINVAL, "batches take a TENO7-ext FP64 or FP32 context");

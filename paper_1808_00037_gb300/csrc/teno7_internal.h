@@ -19,9 +19,11 @@ enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4 };
 // slot the next launch accumulates into, and at the end of an RK step advances
 // t and computes the next CFL step, so that no CTA ever divides in FP64.
 struct DevCtl {
-    unsigned long long amax[3][2];
+    // alphas of slots 0-2 as the bits of non-negative doubles: [slot][0] 1D
+    // global, [slot][0..1] 2D (x, y), [slot][0..2] 1D per characteristic field
+    unsigned long long amax[3][3];
     double t, dt, t_end, cfl, dx, dy;
-    float alpha_f[3][2];
+    float alpha_f[3][3];
     float dt_f, pad_f;
     int steps, max_steps, active, err;
     int err_index;
@@ -57,6 +59,7 @@ struct Stage1D {
     // filled, instead of applying the boundary condition
     int halo;
     const double *alpha_in;  // nullable: alpha of Us from this device value instead of the control block
+    int alpha_mode;          // t7_alpha_mode: 1 = one alpha per characteristic field (1D Euler)
 };
 
 // Ghost cells per side of a slab (the stencil reach of the scheme, Eq. app:
@@ -71,6 +74,7 @@ struct Alpha1D {
     DevCtl *ctl;
     int slot;
     double *alpha_rec;  // nullable: receives the finished alpha
+    int alpha_mode;     // 1: the three per-field alphas of 1D Euler into amax[slot][0..2]
 };
 
 // One stage of the 2D Euler system, dimension by dimension: the x sweep

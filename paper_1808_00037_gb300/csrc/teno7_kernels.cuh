@@ -265,6 +265,31 @@ __device__ __forceinline__ T wavespeed1d(const T *Uc, T gm1, T gamma, T a, int *
     return absval(u) + c;
 }
 
+// |u - c|, |u|, |u + c| of one 1D Euler cell (the characteristic speeds of
+// fields 0, 1, 2, for per-field alphas), with wavespeed1d's operations and
+// flags; the largest equals wavespeed1d's |u| + c bit for bit.
+template <typename T>
+__device__ __forceinline__ void wavespeeds1d(const T *Uc, T gm1, T gamma, T w[3], int *flag) {
+    T u, p, c;
+    if constexpr (sizeof(T) == 8) {
+        u = Uc[1] / Uc[0];
+        p = gm1 * (Uc[2] - T(0.5) * Uc[1] * u);
+        c = sq_root(gamma * p / Uc[0]);
+    } else {
+        const float ri = __frcp_rn(Uc[0]);
+        u = Uc[1] * ri;
+        p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
+        c = __fsqrt_rn(gamma * p * ri);
+    }
+    if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2]))
+        *flag |= ERR_NONFINITE;
+    else if (!(Uc[0] > T(0)) || !(p > T(0)))
+        *flag |= ERR_NONPHYSICAL;
+    w[0] = absval(u - c);
+    w[1] = absval(u);
+    w[2] = absval(u + c);
+}
+
 template <typename T>
 __device__ __forceinline__ T pick(double d, float f) {
     if constexpr (sizeof(T) == 8) {
@@ -340,21 +365,26 @@ __device__ __forceinline__ T poly5(const T *__restrict__ c, const T v0, const T 
 //                alpha(U^n) = amax[slot_out] (oracle's expression order)
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zero_slot, bool end_of_step,
-                                              bool plan_step, bool two_d = false, double *alpha_rec = nullptr) {
+                                              bool plan_step, bool two_d = false, double *alpha_rec = nullptr,
+                                              int nfield = 1) {
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
     if (prev != gridDim.x * gridDim.y - 1) return;
     __threadfence();
     const double a = __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][0], 0ull));
-    const double ay = two_d ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][1], 0ull)) : 0.0;
+    const double ay = (two_d || nfield > 1) ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][1], 0ull))
+                                            : 0.0;
+    const double a2 = nfield > 2 ? __longlong_as_double((long long)atomicAdd(&ctl->amax[slot_out][2], 0ull)) : 0.0;
     ctl->alpha_f[slot_out][0] = (float)a;
     ctl->alpha_f[slot_out][1] = (float)ay;
+    ctl->alpha_f[slot_out][2] = (float)a2;
     if (alpha_rec) {  // recorded for a later adjoint, or for a slab's all-reduce
         alpha_rec[0] = a;
         if (two_d) alpha_rec[1] = ay;
     }
     ctl->amax[zero_slot][0] = 0ull;
     ctl->amax[zero_slot][1] = 0ull;
+    ctl->amax[zero_slot][2] = 0ull;
     if (end_of_step) {
         ctl->t = ctl->t + ctl->dt;
         ctl->steps = ctl->steps + 1;
@@ -362,8 +392,10 @@ __device__ __forceinline__ void finish_launch(DevCtl *ctl, int slot_out, int zer
     if (plan_step) {
         const double t = ctl->t, t_end = ctl->t_end;
         const int active = (ctl->steps < ctl->max_steps) && (t < t_end);
-        // CFL step in the oracle's expression order: 1D cfl dx / a, 2D cfl / (ax/dx + ay/dy)
-        double dt = two_d ? ctl->cfl / (a / ctl->dx + ay / ctl->dy) : (ctl->cfl * ctl->dx) / a;
+        // CFL step in the oracle's expression order: 1D cfl dx / a, 2D cfl / (ax/dx + ay/dy); per-field
+        // alphas: the largest of the three, which equals the global alpha
+        const double a1d = nfield > 2 ? fmax(fmax(a, ay), a2) : a;
+        double dt = two_d ? ctl->cfl / (a / ctl->dx + ay / ctl->dy) : (ctl->cfl * ctl->dx) / a1d;
         if (t + dt > t_end) dt = t_end - t;
         ctl->active = active;
         ctl->dt = dt;
@@ -402,6 +434,7 @@ struct TileArgs {
     double dx;
     float f_dx;
     T alpha, dtT, gamma, gm1, a, eps, CT;
+    T alf[3];        // per-field alphas (1D Euler, the per-field alpha mode)
     double dtD;      // FP64 step (mixed precision: FP64 state, FP32 reconstruction)
     int rhs_mode, stage;
     int ebase;       // added to cell/face indices in error reports
@@ -417,9 +450,14 @@ __device__ __forceinline__ int ghost_or_halo(int l, int n, int bc_lo, int bc_hi,
     return ghost_map(l, n, bc_lo, bc_hi);
 }
 
-template <typename T, int SYS, int SCH = SCH_TENO7EXT>
+// PF (1D Euler, TENO7-ext): per-field alphas A.alf -- each field's split values
+// (L_k F +- alf[k] L_k U) / 2 from the staged flux (sgp) and state (sU), in the
+// oracle's operation order; ws3 receives the output's three characteristic
+// speed maxima (the function then returns 0).
+template <typename T, int SYS, int SCH = SCH_TENO7EXT, bool PF = false>
 __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)[WC], T (*sgm)[WC], T (*spr)[WC],
-                                     const T *scoef, int tile0, int tstride, int tile_end = 0x7fffffff) {
+                                     const T *scoef, int tile0, int tstride, int tile_end = 0x7fffffff,
+                                     T *ws3 = nullptr) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;  // u, H, sqrt(rho)
     constexpr bool F64 = sizeof(T) == 8;
@@ -472,8 +510,12 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
 #pragma unroll
             for (int k = 0; k < M; k++) {
                 sU[k][c] = U[k];
-                sgp[k][c] = T(0.5) * (F[k] + alpha * U[k]);
-                sgm[k][c] = T(0.5) * (F[k] - alpha * U[k]);
+                if constexpr (PF) {
+                    sgp[k][c] = F[k];
+                } else {
+                    sgp[k][c] = T(0.5) * (F[k] + alpha * U[k]);
+                    sgm[k][c] = T(0.5) * (F[k] - alpha * U[k]);
+                }
             }
         }
         __syncwarp();
@@ -540,7 +582,20 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                     qp[k][t] = qm[k][t] = T(0);
                     continue;
                 }
-                if (M == 1) {
+                if constexpr (PF) {
+                    // '+' at cell lane+t, '-' at cell lane+1+t (forward order, as qm)
+                    T lf = L[k][0] * sgp[0][lane + t], lu = L[k][0] * sU[0][lane + t];
+                    T mf = L[k][0] * sgp[0][lane + 1 + t], mu = L[k][0] * sU[0][lane + 1 + t];
+#pragma unroll
+                    for (int c = 1; c < M; c++) {
+                        lf = lf + L[k][c] * sgp[c][lane + t];
+                        lu = lu + L[k][c] * sU[c][lane + t];
+                        mf = mf + L[k][c] * sgp[c][lane + 1 + t];
+                        mu = mu + L[k][c] * sU[c][lane + 1 + t];
+                    }
+                    qp[k][t] = T(0.5) * (lf + A.alf[k] * lu);
+                    qm[k][t] = T(0.5) * (mf - A.alf[k] * mu);
+                } else if (M == 1) {
                     qp[k][t] = sgp[0][lane + t];
                     qm[k][t] = sgm[0][lane + 1 + t];
                 } else {
@@ -672,7 +727,14 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                     out[(size_t)k * A.cso + i] = o[k];
                 }
                 int wflag = 0;
-                wsmax = fmax(wsmax, wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag));
+                if constexpr (PF) {
+                    T w[3];
+                    wavespeeds1d<T>(o, gm1, gamma, w, &wflag);
+#pragma unroll
+                    for (int q = 0; q < 3; q++) ws3[q] = fmax(ws3[q], w[q]);
+                } else {
+                    wsmax = fmax(wsmax, wavespeed1d<T, SYS>(o, gm1, gamma, a, &wflag));
+                }
                 if (wflag) latch_error(ctl, wflag, A.ebase + i);
             }
         }
@@ -685,7 +747,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
 // ==========================================================================
 // Fused 1D stage kernel (grid-wide), SYS in {SYS_ADV, SYS_BURGERS, SYS_EULER1D}.
 // ==========================================================================
-template <typename T, int SYS, int SCH>
+template <typename T, int SYS, int SCH, bool PF = false>
 __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -694,7 +756,7 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     __shared__ T s_gm[WPB][M][WC];
     __shared__ T s_pr[WPB][NP][WC];
     __shared__ T s_coef[WPB][92];
-    __shared__ T s_red[WPB];
+    __shared__ T s_red[PF ? 3 : 1][WPB];
 
     DevCtl *ctl = p.ctl;
     const bool fixed = p.dt_fixed > 0.0;
@@ -710,6 +772,10 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     if constexpr (sizeof(T) == 8) {
         A.alpha = p.alpha_in ? *p.alpha_in : __longlong_as_double((long long)ctl->amax[p.slot_in][0]);
         A.dtT = fixed ? p.dt_fixed : ctl->dt;
+        if constexpr (PF) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) A.alf[q] = __longlong_as_double((long long)ctl->amax[p.slot_in][q]);
+        }
     } else {
         A.alpha = p.alpha_in ? (float)*p.alpha_in : ctl->alpha_f[p.slot_in][0];
         A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
@@ -738,22 +804,32 @@ __global__ void __launch_bounds__(WPB * 32, (sizeof(T) == 4 ? 2 : 1)) stage1d_ke
     A.ebase = 0;
     A.ctl = ctl;
     __syncwarp();
-    T wsmax = tiles1d<T, SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
-                                   p.tile_lo + blockIdx.x * nw + warp, gridDim.x * nw,
-                                   p.tile_hi > 0 ? p.tile_hi : 0x7fffffff);
+    constexpr int NA = PF ? 3 : 1;
+    T ws[NA];
+#pragma unroll
+    for (int q = 0; q < NA; q++) ws[q] = T(0);
+    const T w0 = tiles1d<T, SYS, SCH, PF>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_coef[warp],
+                                          p.tile_lo + blockIdx.x * nw + warp, gridDim.x * nw,
+                                          p.tile_hi > 0 ? p.tile_hi : 0x7fffffff, ws);
+    if constexpr (!PF) ws[0] = w0;
 
     if (!p.rhs_mode) {
-        wsmax = warp_max(wsmax);
-        if (lane == 0) s_red[warp] = wsmax;
+#pragma unroll
+        for (int q = 0; q < NA; q++) {
+            ws[q] = warp_max(ws[q]);
+            if (lane == 0) s_red[q][warp] = ws[q];
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            T v = s_red[0];
-#pragma unroll
-            for (int w = 1; w < nw; w++) v = fmax(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
-            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
+#pragma unroll
+            for (int q = 0; q < NA; q++) {
+                T v = s_red[q][0];
+                for (int w = 1; w < nw; w++) v = fmax(v, s_red[q][w]);
+                atomicMax(&ctl->amax[so][q], (unsigned long long)__double_as_longlong((double)v));
+            }
             finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed && !p.partial,
-                          p.stage == 2 && !fixed && !p.partial, false, p.alpha_rec);
+                          p.stage == 2 && !fixed && !p.partial, false, p.alpha_rec, NA);
         }
     }
 }
@@ -884,6 +960,23 @@ __device__ __forceinline__ float wavespeed1d_fast(const float *Uc, float gm1, fl
     else if (!(Uc[0] > 0.f) || !(p > 0.f))
         *flag |= ERR_NONPHYSICAL;
     return fabsf(u) + c;
+}
+
+// |u - c|, |u|, |u + c| of one FP32 1D Euler cell with wavespeed1d_fast's
+// operations and flags (per-field alphas of a stage's output).
+__device__ __forceinline__ void wavespeeds1d_fast(const float *Uc, float gm1, float gamma, float w[3], int *flag) {
+    const float ri = rcp_approx(Uc[0]);
+    const float u = Uc[1] * ri;
+    const float p = gm1 * (Uc[2] - 0.5f * Uc[1] * u);
+    const float c2 = gamma * p * ri;
+    const float c = c2 * rsqrtf(c2);
+    if (!isfinite(Uc[0]) || !isfinite(Uc[1]) || !isfinite(Uc[2]))
+        *flag |= ERR_NONFINITE;
+    else if (!(Uc[0] > 0.f) || !(p > 0.f))
+        *flag |= ERR_NONPHYSICAL;
+    w[0] = fabsf(u - c);
+    w[1] = fabsf(u);
+    w[2] = fabsf(u + c);
 }
 
 // Conversions between the FP64 state and the FP32 reconstruction of the
@@ -1424,11 +1517,15 @@ constexpr int WP2 = 40;
 
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 
-template <int SYS, int SCH>
+// PF (1D Euler, TENO7-ext): per-field alphas A.alf -- the staged rows hold the
+// flux F (sgp) and the state (sU), and each field's split values are
+// (L_k F +- alf[k] L_k U) / 2; ws3 receives the output's three characteristic
+// speed maxima (the function then returns 0).
+template <int SYS, int SCH, bool PF = false>
 __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2 (*sU)[WP2], float2 (*sgp)[WP2],
                                                 float2 (*sgm)[WP2], float2 (*spr)[WP2], float2 (*su0)[32],
                                                 const float (*s_cf)[8],
-                                                int tile0, int tstride) {
+                                                int tile0, int tstride, float *ws3 = nullptr) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr bool PLUS_ONLY = SYS == SYS_ADV;
@@ -1532,8 +1629,13 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                 if (SYS == SYS_ADV) {
                     vgp[h][k] = (0.5f * (a + alpha)) * U[k];
                 } else {
-                    vgp[h][k] = 0.5f * fmaf(alpha, U[k], F[k]);
-                    vgm[h][k] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                    if constexpr (PF) {
+                        vgp[h][k] = F[k];
+                        vgm[h][k] = F[k];  // (unused)
+                    } else {
+                        vgp[h][k] = 0.5f * fmaf(alpha, U[k], F[k]);
+                        vgm[h][k] = 0.5f * fmaf(-alpha, U[k], F[k]);
+                    }
                 }
             }
             if (r == 0) continue;
@@ -1591,7 +1693,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
         unsigned Dsave[2] = {0u, 0u};
 #pragma unroll
         for (int s = 0; s < (PLUS_ONLY ? 1 : 2); s++) {
-            float2 (*sg)[WP2] = s == 0 ? sgp : sgm;
+            float2 (*sg)[WP2] = (PF || s == 0) ? sgp : sgm;
             float2 P[M][7];
 #pragma unroll
             for (int t = 0; t < 7; t++) {
@@ -1605,15 +1707,32 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                 float2 g[M];
 #pragma unroll
                 for (int c = 0; c < M; c++) g[c] = sg[c][o];
+                if constexpr (PF) {
+                    // the state at the same cells: q = (L_k F +- alf[k] L_k U) / 2
+                    float2 gu[M];
 #pragma unroll
-                for (int k = 0; k < M; k++) {
-                    if (M == 1) {
-                        P[k][t] = g[0];
-                    } else {
-                        float2 q = __fmul2_rn(L2[k][0], g[0]);
+                    for (int c = 0; c < M; c++) gu[c] = sU[c][o];
 #pragma unroll
-                        for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
-                        P[k][t] = q;
+                    for (int k = 0; k < M; k++) {
+                        float2 lf = __fmul2_rn(L2[k][0], g[0]), lu = __fmul2_rn(L2[k][0], gu[0]);
+#pragma unroll
+                        for (int c = 1; c < M; c++) {
+                            lf = __ffma2_rn(L2[k][c], g[c], lf);
+                            lu = __ffma2_rn(L2[k][c], gu[c], lu);
+                        }
+                        P[k][t] = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(s == 0 ? A.alf[k] : -A.alf[k]), lu, lf));
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < M; k++) {
+                        if (M == 1) {
+                            P[k][t] = g[0];
+                        } else {
+                            float2 q = __fmul2_rn(L2[k][0], g[0]);
+#pragma unroll
+                            for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
+                            P[k][t] = q;
+                        }
                     }
                 }
             }
@@ -1784,15 +1903,28 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                     ob[k] = o[k].y;
                 }
                 int wfA = 0, wfB = 0;
-                const float wa = wavespeed1d_fast<SYS>(oa, gm1, gamma, a, &wfA);
-                const float wb = wavespeed1d_fast<SYS>(ob, gm1, gamma, a, &wfB);
-                if (updA) {
-                    wsmax = fmaxf(wsmax, wa);
-                    if (wfA) latch_error(ctl, wfA, A.ebase + jA);
-                }
-                if (updB) {
-                    wsmax = fmaxf(wsmax, wb);
-                    if (wfB) latch_error(ctl, wfB, A.ebase + jB);
+                if constexpr (PF) {
+                    float w3a[3], w3b[3];
+                    wavespeeds1d_fast(oa, gm1, gamma, w3a, &wfA);
+                    wavespeeds1d_fast(ob, gm1, gamma, w3b, &wfB);
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        if (updA) ws3[q] = fmaxf(ws3[q], w3a[q]);
+                        if (updB) ws3[q] = fmaxf(ws3[q], w3b[q]);
+                    }
+                    if (updA && wfA) latch_error(ctl, wfA, A.ebase + jA);
+                    if (updB && wfB) latch_error(ctl, wfB, A.ebase + jB);
+                } else {
+                    const float wa = wavespeed1d_fast<SYS>(oa, gm1, gamma, a, &wfA);
+                    const float wb = wavespeed1d_fast<SYS>(ob, gm1, gamma, a, &wfB);
+                    if (updA) {
+                        wsmax = fmaxf(wsmax, wa);
+                        if (wfA) latch_error(ctl, wfA, A.ebase + jA);
+                    }
+                    if (updB) {
+                        wsmax = fmaxf(wsmax, wb);
+                        if (wfB) latch_error(ctl, wfB, A.ebase + jB);
+                    }
                 }
             }
         }
@@ -1801,7 +1933,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
     return wsmax;
 }
 
-template <int SYS, int SCH>
+template <int SYS, int SCH, bool PF = false>
 __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(const Stage1D p) {
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
     constexpr int NP = (SYS == SYS_EULER1D) ? 3 : 1;
@@ -1812,7 +1944,7 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     __shared__ float2 s_pr[WPB][NP][WP2];
     __shared__ float2 s_u0[WPB][SYS == SYS_EULER1D ? M : 1][32];  // U^n of the cells a lane updates (cp.async)
     __shared__ __align__(16) float s_cf[32][8];
-    __shared__ float s_red[WPB];
+    __shared__ float s_red[PF ? 3 : 1][WPB];
 
     DevCtl *ctl = p.ctl;
     const bool fixed = p.dt_fixed > 0.0;
@@ -1824,6 +1956,10 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
         fill_delta_table(s_cf);
     TileArgs<float> A;
     A.alpha = p.alpha_in ? (float)*p.alpha_in : ctl->alpha_f[p.slot_in][0];
+    if constexpr (PF) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) A.alf[q] = ctl->alpha_f[p.slot_in][q];
+    }
     A.dtT = fixed ? p.f_dt_fixed : ctl->dt_f;
     A.dtD = fixed ? p.dt_fixed : ctl->dt;
     // slab mode: cell 0 follows the padding (the RHS output dU/dt is unpadded)
@@ -1850,34 +1986,49 @@ __global__ void __launch_bounds__(WPB * 32, T7_F32_MINB) stage1d_f32fp_kernel(co
     A.halo = p.halo;
     A.ctl = ctl;
     __syncthreads();
-    float wsmax = tiles1d_f32_fp<SYS, SCH>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_u0[warp], s_cf,
-                                           blockIdx.x * nw + warp, gridDim.x * nw);
+    constexpr int NA = PF ? 3 : 1;
+    float ws[NA];
+#pragma unroll
+    for (int q = 0; q < NA; q++) ws[q] = 0.f;
+    const float w0 = tiles1d_f32_fp<SYS, SCH, PF>(A, s_U[warp], s_gp[warp], s_gm[warp], s_pr[warp], s_u0[warp], s_cf,
+                                                  blockIdx.x * nw + warp, gridDim.x * nw, ws);
+    if constexpr (!PF) ws[0] = w0;
     (void)lane;
     if (!p.rhs_mode) {
-        wsmax = warp_max(wsmax);
-        if ((threadIdx.x & 31) == 0) s_red[warp] = wsmax;
+#pragma unroll
+        for (int q = 0; q < NA; q++) {
+            ws[q] = warp_max(ws[q]);
+            if ((threadIdx.x & 31) == 0) s_red[q][warp] = ws[q];
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float v = s_red[0];
-#pragma unroll
-            for (int w = 1; w < nw; w++) v = fmaxf(v, s_red[w]);
             const int so = (p.stage + 1) % 3;
-            atomicMax(&ctl->amax[so][0], (unsigned long long)__double_as_longlong((double)v));
+#pragma unroll
+            for (int q = 0; q < NA; q++) {
+                float v = s_red[q][0];
+                for (int w = 1; w < nw; w++) v = fmaxf(v, s_red[q][w]);
+                atomicMax(&ctl->amax[so][q], (unsigned long long)__double_as_longlong((double)v));
+            }
             finish_launch(ctl, so, (p.stage + 2) % 3, p.stage == 2 && !fixed, p.stage == 2 && !fixed, false,
-                          p.alpha_rec);
+                          p.alpha_rec, NA);
         }
     }
 }
 
-// alpha of a 1D state into ctl->amax[slot][0]; grid-stride, one atomic per CTA;
-// the last CTA converts it and plans the first RK step (see finish_launch).
-template <typename T, int SYS>
+// alpha of a 1D state into ctl->amax[slot][0] (PF: the three per-field
+// alphas of 1D Euler into amax[slot][0..2]); grid-stride, one atomic per CTA
+// and alpha; the last CTA converts them and plans the first RK step (see
+// finish_launch).
+template <typename T, int SYS, bool PF = false>
 __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
-    __shared__ T s_red[8];
+    constexpr int NA = PF ? 3 : 1;
+    __shared__ T s_red[NA][8];
     const T *U = static_cast<const T *>(p.U);
     const T gamma = T(p.gamma), gm1 = T(p.gamma - 1.0), a = T(p.a);
     constexpr int M = (SYS == SYS_EULER1D) ? 3 : 1;
-    T m = T(0);
+    T m[NA];
+#pragma unroll
+    for (int q = 0; q < NA; q++) m[q] = T(0);
     int flag = 0, first = 0x7fffffff;
     const size_t cs = p.stride > 0 ? (size_t)p.stride : (size_t)p.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
@@ -1885,22 +2036,34 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
 #pragma unroll
         for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * cs + i];
         int f = 0;
-        const T w = wavespeed1d<T, SYS>(Uc, gm1, gamma, a, &f);
+        if constexpr (PF) {
+            T w[3];
+            wavespeeds1d<T>(Uc, gm1, gamma, w, &f);
+#pragma unroll
+            for (int q = 0; q < 3; q++) m[q] = fmax(m[q], w[q]);
+        } else {
+            m[0] = fmax(m[0], wavespeed1d<T, SYS>(Uc, gm1, gamma, a, &f));
+        }
         if (f) {
             flag |= f;
             first = min(first, i);
         }
-        m = fmax(m, w);
     }
     if (flag) latch_error(p.ctl, flag, first);
-    m = warp_max(m);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+#pragma unroll
+    for (int q = 0; q < NA; q++) {
+        m[q] = warp_max(m[q]);
+        if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = m[q];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        T v = s_red[0];
-        for (int w = 1; w < 8; w++) v = fmax(v, s_red[w]);
-        atomicMax(&p.ctl->amax[p.slot][0], (unsigned long long)__double_as_longlong((double)v));
-        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true, false, p.alpha_rec);
+#pragma unroll
+        for (int q = 0; q < NA; q++) {
+            T v = s_red[q][0];
+            for (int w = 1; w < 8; w++) v = fmax(v, s_red[q][w]);
+            atomicMax(&p.ctl->amax[p.slot][q], (unsigned long long)__double_as_longlong((double)v));
+        }
+        finish_launch(p.ctl, p.slot, (p.slot + 1) % 3, false, true, false, p.alpha_rec, NA);
     }
 }
 
@@ -2004,6 +2167,18 @@ cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
+    if (p.alpha_mode) {
+        // per-field alphas: 1D Euler, TENO7-ext, FP32 state, whole-domain launches only
+        if (sizeof(S) != 4 || p.sys != SYS_EULER1D || t5 || p.tile_lo != 0 || p.tile_hi > 0 || p.partial || p.halo)
+            return cudaErrorInvalidValue;
+        const int nt2 = (p.n + WT2 - 1) / WT2;
+        const int nw2 = warps_per_cta(nt2, false);
+        const int res2 = num_sms() * T7_F32_MINB * 4 * (WPB / nw2);
+        int grid2 = (nt2 + nw2 - 1) / nw2;
+        if (grid2 > res2) grid2 = res2;
+        stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT, true><<<grid2, nw2 * 32, 0, st>>>(p);
+        return cudaGetLastError();
+    }
     // FP32 state over the whole domain or a slab: face-paired tiles
     // (advection when a > 0, where alpha = a makes the '-' split vanish).
     // Their results equal the paired-split kernel's bit for bit (the Roe
@@ -2065,6 +2240,11 @@ cudaError_t launch_stage1d(const Stage1D &p, cudaStream_t st) {
         if (grid > resident) grid = resident;
         if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
         const bool t5 = p.scheme == SCH_TENO5;
+        if (p.alpha_mode) {  // per-field alphas: 1D Euler with TENO7-ext only
+            if (p.sys != SYS_EULER1D || t5) return cudaErrorInvalidValue;
+            stage1d_kernel<T, SYS_EULER1D, SCH_TENO7EXT, true><<<grid, nw * 32, 0, st>>>(p);
+            return cudaGetLastError();
+        }
         switch (p.sys) {
             case SYS_ADV:
                 if (t5) stage1d_kernel<T, SYS_ADV, SCH_TENO5><<<grid, nw * 32, 0, st>>>(p);
@@ -2091,7 +2271,12 @@ cudaError_t launch_alpha1d(const Alpha1D &p, cudaStream_t st) {
     switch (p.sys) {
         case SYS_ADV: alpha1d_kernel<T, SYS_ADV><<<grid, 256, 0, st>>>(p); break;
         case SYS_BURGERS: alpha1d_kernel<T, SYS_BURGERS><<<grid, 256, 0, st>>>(p); break;
-        case SYS_EULER1D: alpha1d_kernel<T, SYS_EULER1D><<<grid, 256, 0, st>>>(p); break;
+        case SYS_EULER1D:
+            if (p.alpha_mode)
+                alpha1d_kernel<T, SYS_EULER1D, true><<<grid, 256, 0, st>>>(p);
+            else
+                alpha1d_kernel<T, SYS_EULER1D><<<grid, 256, 0, st>>>(p);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

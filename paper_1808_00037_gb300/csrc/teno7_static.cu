@@ -53,8 +53,8 @@ extern "C" t7_status t7_rk3_step_static(const t7_grid *g, void *U, double dt, vo
     if ((g->prec != T7_F64 && g->prec != T7_F32) || g->nx < 1 || g->ny != 1 || !(g->dx > 0.0) ||
         !(g->CT > 0.0 && g->CT < 1.0) || g->bc[0] < 0 || g->bc[0] > 1 || g->bc[1] < 0 || g->bc[1] > 1)
         return report(errbuf, errlen, T7_EINVAL, "t7_rk3_step_static: bad grid");
-    if (g->scheme != T7_TENO7EXT)
-        return report(errbuf, errlen, T7_EINVAL, "t7_rk3_step_static: runs the TENO7-ext scheme only");
+    if (g->scheme != T7_TENO7EXT || g->alpha_mode != T7_ALPHA_GLOBAL)
+        return report(errbuf, errlen, T7_EINVAL, "t7_rk3_step_static: runs TENO7-ext with the global alpha only");
     const int m = g->sys == T7_EULER1D ? 3 : 1;
     const size_t esize = g->prec == T7_F64 ? 8 : 4;
     const size_t buf = ((size_t)m * g->nx * esize + 255) / 256 * 256;
