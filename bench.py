@@ -380,6 +380,30 @@ def bench_teno5(args, torch, B, U0, dx, res, dist, world):
     return out
 
 
+def bench_alpha_mode(args, torch, B, U0, dx, res, dist, world):
+    """The per-field Lax-Friedrichs alpha (t7_grid.alpha_mode = per field:
+    alpha_k = max |lambda_k| per characteristic field, splits formed from
+    the projections of F and U) on the same workload in FP32: its throughput
+    and its time against the global alpha's."""
+    n = U0.shape[1]
+    steps = args.steps
+    ctx = B.Context(B.T7_EULER1D, n, dx, prec=B.T7_F32, bc=(1, 1, 0, 0), gamma=GAMMA,
+                    alpha_mode=B.T7_ALPHA_PER_FIELD)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    ctx.run(U, CFL, max_steps=args.warmup)
+    torch.cuda.synchronize()
+    ms, _ = time_run(torch, ctx, U, steps, dist, world)
+    out = {"workload": "same tiled Shu-Osher state and step count as the primary line, FP32",
+           "value": n * steps * world / (ms * 1e-3) / 1e9, "unit": "Gcell-steps/s", "ms_per_step": ms / steps,
+           "steps": steps}
+    if "f32" in res:
+        out["time_vs_global_alpha"] = (ms / steps) / res["f32"]["ms_per_step"]
+    ctx.close()
+    del U
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_mixed(args, torch, B, U0, dx, res, dist, world):
     """Mixed precision (FP64 state, FP32 reconstruction, FP64 flux difference
     and RK combination) on the same workload: throughput, its speedup over the
@@ -809,6 +833,7 @@ def main():
         return 0
     res5 = None if args.no_teno5 else bench_teno5(args, torch, B, U0, dx, res, dist, world)
     resm = None if args.no_mixed else bench_mixed(args, torch, B, U0, dx, res, dist, world)
+    resp = None if args.no_mixed else bench_alpha_mode(args, torch, B, U0, dx, res, dist, world)
     resv = None if args.no_advection else bench_advection(args, torch, B, dist, world)
     res2d = None if args.no_2d else bench_2d(args, torch, B, dist, world, rank)
     resb = None if args.no_batch else bench_batch(args, torch, B, dist, world, rank)
@@ -843,7 +868,8 @@ def main():
         "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"],
         "e2e": main_res.get("e2e"),
         "f64": res["f64"], "mixed": resm, "teno5": res5, "advection": resv, "accuracy": acc, "euler2d": res2d,
-        "batch": resb, "adjoint": resa, "strong": strong, "slabs_1gpu": slabs1, "alu_peaks": alu,
+        "batch": resb, "adjoint": resa, "strong": strong, "slabs_1gpu": slabs1, "per_field_alpha": resp,
+        "alu_peaks": alu,
         "cpu_baseline": cpu,
     }
     # compact FP64 figures at the end of the line, where a reader of its tail finds them
