@@ -1695,6 +1695,38 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
         for (int s = 0; s < (PLUS_ONLY ? 1 : 2); s++) {
             float2 (*sg)[WP2] = (PF || s == 0) ? sgp : sgm;
             float2 P[M][7];
+            if constexpr (PF) {
+                // two passes over the taps, so that one tap's loads are live at a
+                // time: P <- L_k U, then P <- (L_k F +- alf[k] P) / 2
+#pragma unroll
+                for (int t = 0; t < 7; t++) {
+                    const int o = s == 0 ? lane + t : lane + 7 - t;
+                    float2 gu[M];
+#pragma unroll
+                    for (int c = 0; c < M; c++) gu[c] = sU[c][o];
+#pragma unroll
+                    for (int k = 0; k < M; k++) {
+                        float2 lu = __fmul2_rn(L2[k][0], gu[0]);
+#pragma unroll
+                        for (int c = 1; c < M; c++) lu = __ffma2_rn(L2[k][c], gu[c], lu);
+                        P[k][t] = lu;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 7; t++) {
+                    const int o = s == 0 ? lane + t : lane + 7 - t;
+                    float2 g[M];
+#pragma unroll
+                    for (int c = 0; c < M; c++) g[c] = sgp[c][o];
+#pragma unroll
+                    for (int k = 0; k < M; k++) {
+                        float2 lf = __fmul2_rn(L2[k][0], g[0]);
+#pragma unroll
+                        for (int c = 1; c < M; c++) lf = __ffma2_rn(L2[k][c], g[c], lf);
+                        P[k][t] = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(s == 0 ? A.alf[k] : -A.alf[k]), P[k][t], lf));
+                    }
+                }
+            } else {
 #pragma unroll
             for (int t = 0; t < 7; t++) {
                 if (SCH == SCH_TENO5 && (t == 0 || t == 6)) {
@@ -1707,34 +1739,18 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                 float2 g[M];
 #pragma unroll
                 for (int c = 0; c < M; c++) g[c] = sg[c][o];
-                if constexpr (PF) {
-                    // the state at the same cells: q = (L_k F +- alf[k] L_k U) / 2
-                    float2 gu[M];
 #pragma unroll
-                    for (int c = 0; c < M; c++) gu[c] = sU[c][o];
+                for (int k = 0; k < M; k++) {
+                    if (M == 1) {
+                        P[k][t] = g[0];
+                    } else {
+                        float2 q = __fmul2_rn(L2[k][0], g[0]);
 #pragma unroll
-                    for (int k = 0; k < M; k++) {
-                        float2 lf = __fmul2_rn(L2[k][0], g[0]), lu = __fmul2_rn(L2[k][0], gu[0]);
-#pragma unroll
-                        for (int c = 1; c < M; c++) {
-                            lf = __ffma2_rn(L2[k][c], g[c], lf);
-                            lu = __ffma2_rn(L2[k][c], gu[c], lu);
-                        }
-                        P[k][t] = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(s == 0 ? A.alf[k] : -A.alf[k]), lu, lf));
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < M; k++) {
-                        if (M == 1) {
-                            P[k][t] = g[0];
-                        } else {
-                            float2 q = __fmul2_rn(L2[k][0], g[0]);
-#pragma unroll
-                            for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
-                            P[k][t] = q;
-                        }
+                        for (int c = 1; c < M; c++) q = __ffma2_rn(L2[k][c], g[c], q);
+                        P[k][t] = q;
                     }
                 }
+            }
             }
             // Every stencil of every window kept (tau < kt eps, see
             // keep_all_factor) is tested for all fields at once, without
