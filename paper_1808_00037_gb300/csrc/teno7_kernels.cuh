@@ -28,8 +28,12 @@
 //      lanes 2..30 take the flux difference (Eq. app), apply the SSP-RK3 stage,
 //      write the new state and fold max(|u| + c) of it into the next stage's
 //      alpha (a warp/CTA reduction, one atomicMax per CTA).
-// The FP32 kernel (stage1d_f32_kernel below) keeps this structure with the two
-// splits paired in float2 registers.
+// The FP32 kernels keep this structure with packed f32x2 arithmetic:
+// stage1d_f32_kernel pairs the two splits of one face in a float2 (it runs the
+// mixed precision form, the batch tubes and parted launches); stage1d_f32fp_kernel
+// pairs two faces of a 61-cell tile (lane l: faces c0-2+l and c0+30+l) and runs
+// the splits one after the other (whole-domain and slab launches of the FP32
+// state).  Both give the same bits.
 #pragma once
 #include <math.h>
 #include <stdint.h>

@@ -2,13 +2,16 @@
 // TENO7-ext reconstruction of each direction in its own characteristic frame
 // (Roe average of the two cells of the face; fields un-c, un, shear, un+c).
 //
-//   x sweep  warp tiles along rows, exactly as the 1D kernels (lane = face);
-//            writes Lx(U) into R (coalesced along x).
+//   x sweep  warp tiles along rows, as the 1D kernels (lane = face; the FP32
+//            state's kernel pairs two faces per lane in 61-cell tiles, as the
+//            1D face-paired kernel); writes Lx(U) into R (coalesced along x).
 //   y sweep  one CTA stages a block of 39 rows x 32 columns (29-row tile + halo)
 //            in padded shared memory; each warp runs the lane = face logic down
 //            4 of the columns, exchanging cutoff words and face fluxes by
 //            __shfl along y; after a barrier the CTA adds Lx, applies the RK
-//            stage and reduces max(|u|+c), max(|v|+c) in row-major order.
+//            stage and reduces max(|u|+c), max(|v|+c) in row-major order (the
+//            FP32 state's kernel is persistent and copies the next block's
+//            state in by cp.async while the current one computes).
 //
 // Templated on T; instantiated for FP64 (-fmad=false: the oracle's operation
 // order, including the component permutation of the y frame) and FP32.
