@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_runs
 from oracle import riemann
 from paper_1808_00037_gb300 import binding as B
 from paper_1808_00037_gb300 import inputs as I
@@ -296,6 +297,24 @@ def test_full_size_rhs_sampled_f32_and_mixed(prec, dtype):
             assert np.max(np.abs(host(rg[:, i:i + 1])[:, 0] - ro[:, k])) <= bound, i
     assert same >= 0.99 * total, (same, total)
     assert checked >= 150
+
+
+@pytest.mark.parametrize("row", oracle_runs.rows("euler1d"), ids=lambda r: r[0])
+def test_full_size_run_f64_bitexact(row):
+    """The benchmark's workload run whole: the tiled Shu-Osher profile
+    (16,777,600 cells, zero-gradient ends, CFL 0.5) for 20 SSP-RK3 steps in
+    FP64.  End state, step count and time equal the oracle's bit for bit (the
+    oracle's end state is stored as a hash, golden/make_runs.py: the run takes
+    minutes on the CPU)."""
+    name, tiles, n, _, steps, t_end, digest = row
+    U, dx = I.shu_osher(1600, tiles=tiles)
+    assert U.shape[1] == n
+    c = ctx(oracle.SYS_EULER1D, n, dx, bc=(1, 1))
+    Ug = dev(U)
+    sg, tg = c.run(Ug, 0.5, max_steps=steps)
+    assert (sg, tg) == (steps, t_end)
+    assert oracle_runs.state_hash(host(Ug)) == digest
+    c.close()
 
 
 @pytest.mark.parametrize("prec,dtype", [(B.T7_F64, torch.float64), (B.T7_F32, torch.float32)])

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_runs
 from paper_1808_00037_gb300 import binding as B
 from paper_1808_00037_gb300 import inputs as I
 
@@ -82,6 +83,23 @@ def test_quadrant_run_2d_f64_bitexact():
     sg, tg = c.run(Ug, 0.4, max_steps=40)
     assert (sg, tg) == (so, to)
     assert np.array_equal(host(Ug), Uo)
+
+
+@pytest.mark.parametrize("row", oracle_runs.rows("euler2d"), ids=lambda r: r[0])
+def test_long_quadrant_runs_f64_bitexact(row):
+    """The 2D gate's long runs on the benchmark's quadrant states: 256^2 for
+    500 steps and the full 2048^2 for 20 steps, transmissive, CFL 0.4.  The
+    FP64 end state, step count and time equal the oracle's bit for bit (the
+    oracle's end state is stored as a hash: the runs take minutes on the CPU,
+    golden/make_runs.py)."""
+    name, seed, nx, ny, steps, t_end, digest = row
+    U, dx, dy, _ = I.quadrants_2d(seed, nx, ny)
+    c = ctx(nx, ny, dx, dy)
+    Ug = dev(U)
+    sg, tg = c.run(Ug, 0.4, max_steps=steps)
+    assert (sg, tg) == (steps, t_end)
+    assert oracle_runs.state_hash(host(Ug)) == digest
+    c.close()
 
 
 def test_smooth_run_2d_f32_tolerance():
