@@ -38,6 +38,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "teno7_internal.h"
 
 namespace t7 {
@@ -1103,6 +1105,17 @@ __device__ __forceinline__ void back_project_f32(const RoeF32 &F, const float f[
 #ifndef T7_F32_MINB
 #define T7_F32_MINB 2  // resident CTAs per SM the FP32 stage kernel is compiled for
 #endif
+// Waves of resident CTAs an FP32 launch's grid covers (see stage_grid): 1D
+// Euler stages, scalar-law stages, 2D x sweeps
+#ifndef T7_WAVES_EULER
+#define T7_WAVES_EULER 2
+#endif
+#ifndef T7_WAVES_SCALAR
+#define T7_WAVES_SCALAR 1
+#endif
+#ifndef T7_WAVES_X2D
+#define T7_WAVES_X2D 2
+#endif
 
 // FP32 warp-tile sweep (paired splits); same contract as tiles1d.  s_cf is
 // the Delta-indexed coefficient table [32][8].  S is the state type: float,
@@ -2155,6 +2168,33 @@ inline int num_sms() {
     return sms;
 }
 
+// CTAs of a kernel resident on one SM at `threads` threads and `smem` bytes of
+// dynamic shared memory (the CUDA occupancy calculator; at least 1), cached
+// per (kernel, threads, smem), so that each launch configuration is queried
+// once.
+inline int resident_ctas(const void *kernel, int threads, size_t smem = 0) {
+    struct Entry {
+        const void *kernel;
+        int threads;
+        size_t smem;
+        int ctas;
+    };
+    static Entry cache[64];
+    static int used = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; i++)
+        if (cache[i].kernel == kernel && cache[i].threads == threads && cache[i].smem == smem) return cache[i].ctas;
+    int ctas = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kernel, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();  // not left for the launch's own error check
+        ctas = 0;
+    }
+    if (ctas < 1) ctas = 1;
+    if (used < 64) cache[used++] = {kernel, threads, smem, ctas};
+    return ctas;
+}
+
 // Warps per CTA of the 1D stage and adjoint kernels: WPB, or -- for the
 // FP64-pipe-bound kernels (spread = true) -- halved while that would leave SMs
 // without a CTA, so small problems run one warp tile per SM instead of eight
@@ -2176,27 +2216,39 @@ inline int stage_tiles(const Stage1D &p) {
     return hi - p.tile_lo;
 }
 
+using Stage1DKernel = void (*)(const Stage1D);
+
+// Grid of an FP32 stage launch: nctas CTAs of `threads` threads, capped at
+// `waves` whole waves of the kernel's resident CTAs (the tiles are spread over
+// the grid by a grid-stride loop, each warp loading its next tile while it
+// computes the current one).  Measured on the 16.8M-cell workloads: the
+// scalar laws run fastest as one wave (advection 70.6 -> 81.2, Burgers 42.3 ->
+// 46.4 Gcell-steps/s against four waves: a warp's first tile load is not
+// hidden, and one wave has the fewest), Euler as two (15.82 -> 15.90 against
+// four, 15.76 as one: the shock tiles cost more, and the second wave evens
+// out the SMs' loads).
+inline int stage_grid(Stage1DKernel k, int nctas, int threads, int waves) {
+    const int cap = num_sms() * resident_ctas(reinterpret_cast<const void *>(k), threads) * waves;
+    return nctas < cap ? nctas : cap;
+}
+
 // FP32 paired-split stage kernels; S = float (FP32 state) or double (mixed).
 template <typename S>
 cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     const int ntiles = stage_tiles(p);
     if (ntiles < 1) return cudaErrorInvalidValue;
     const int nw = warps_per_cta(ntiles, false);
-    const int resident = num_sms() * T7_F32_MINB * 4 * (WPB / nw);  // a few waves of resident CTAs
-    int grid = (ntiles + nw - 1) / nw;
-    if (grid > resident) grid = resident;
     if (p.scheme != SCH_TENO7EXT && p.scheme != SCH_TENO5) return cudaErrorInvalidValue;
     const bool t5 = p.scheme == SCH_TENO5;
+    const int nt2 = (p.n + WT2 - 1) / WT2;
+    const int nw2 = warps_per_cta(nt2, false);
+    Stage1DKernel k = nullptr;
     if (p.alpha_mode) {
         // per-field alphas: 1D Euler, TENO7-ext, FP32 state, whole-domain launches only
         if (sizeof(S) != 4 || p.sys != SYS_EULER1D || t5 || p.tile_lo != 0 || p.tile_hi > 0 || p.partial || p.halo)
             return cudaErrorInvalidValue;
-        const int nt2 = (p.n + WT2 - 1) / WT2;
-        const int nw2 = warps_per_cta(nt2, false);
-        const int res2 = num_sms() * T7_F32_MINB * 4 * (WPB / nw2);
-        int grid2 = (nt2 + nw2 - 1) / nw2;
-        if (grid2 > res2) grid2 = res2;
-        stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT, true><<<grid2, nw2 * 32, 0, st>>>(p);
+        k = stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT, true>;
+        k<<<stage_grid(k, (nt2 + nw2 - 1) / nw2, nw2 * 32, T7_WAVES_EULER), nw2 * 32, 0, st>>>(p);
         return cudaGetLastError();
     }
     // FP32 state over the whole domain or a slab: face-paired tiles
@@ -2207,43 +2259,38 @@ cudaError_t launch_stage1d_paired(const Stage1D &p, cudaStream_t st) {
     // take the paired-split tiles, agree with them.
     if (sizeof(S) == 4 && p.tile_lo == 0 && p.tile_hi <= 0 && !p.partial &&
         ((p.sys == SYS_ADV && p.a > 0.0) || p.sys == SYS_BURGERS || p.sys == SYS_EULER1D)) {
-        const int nt2 = (p.n + WT2 - 1) / WT2;
-        const int nw2 = warps_per_cta(nt2, false);
-        const int res2 = num_sms() * T7_F32_MINB * 4 * (WPB / nw2);
-        int grid2 = (nt2 + nw2 - 1) / nw2;
-        if (grid2 > res2) grid2 = res2;
         switch (p.sys) {
             case SYS_ADV:
-                if (t5) stage1d_f32fp_kernel<SYS_ADV, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
-                else stage1d_f32fp_kernel<SYS_ADV, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                k = t5 ? stage1d_f32fp_kernel<SYS_ADV, SCH_TENO5> : stage1d_f32fp_kernel<SYS_ADV, SCH_TENO7EXT>;
                 break;
             case SYS_BURGERS:
-                if (t5) stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
-                else stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                k = t5 ? stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO5>
+                       : stage1d_f32fp_kernel<SYS_BURGERS, SCH_TENO7EXT>;
                 break;
             case SYS_EULER1D:
-                if (t5) stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO5><<<grid2, nw2 * 32, 0, st>>>(p);
-                else stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT><<<grid2, nw2 * 32, 0, st>>>(p);
+                k = t5 ? stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO5>
+                       : stage1d_f32fp_kernel<SYS_EULER1D, SCH_TENO7EXT>;
                 break;
             default: return cudaErrorInvalidValue;
         }
+        const int waves = p.sys == SYS_EULER1D ? T7_WAVES_EULER : T7_WAVES_SCALAR;
+        k<<<stage_grid(k, (nt2 + nw2 - 1) / nw2, nw2 * 32, waves), nw2 * 32, 0, st>>>(p);
         return cudaGetLastError();
     }
     switch (p.sys) {
         case SYS_ADV:
-            if (t5) stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
+            k = t5 ? stage1d_f32_kernel<SYS_ADV, SCH_TENO5, S> : stage1d_f32_kernel<SYS_ADV, SCH_TENO7EXT, S>;
             break;
         case SYS_BURGERS:
-            if (t5) stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
+            k = t5 ? stage1d_f32_kernel<SYS_BURGERS, SCH_TENO5, S> : stage1d_f32_kernel<SYS_BURGERS, SCH_TENO7EXT, S>;
             break;
         case SYS_EULER1D:
-            if (t5) stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5, S><<<grid, nw * 32, 0, st>>>(p);
-            else stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT, S><<<grid, nw * 32, 0, st>>>(p);
+            k = t5 ? stage1d_f32_kernel<SYS_EULER1D, SCH_TENO5, S> : stage1d_f32_kernel<SYS_EULER1D, SCH_TENO7EXT, S>;
             break;
         default: return cudaErrorInvalidValue;
     }
+    const int waves = p.sys == SYS_EULER1D ? T7_WAVES_EULER : T7_WAVES_SCALAR;
+    k<<<stage_grid(k, (ntiles + nw - 1) / nw, nw * 32, waves), nw * 32, 0, st>>>(p);
     return cudaGetLastError();
 }
 
