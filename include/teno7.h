@@ -34,6 +34,13 @@
  *     occurred (a state that went non-physical and then produced NaN).
  *     t7_last_error() names the lowest flat cell index (1D: i; 2D: y nx + x;
  *     batches: the index in the concatenated array) near which one was met.
+ *   - Checked build (libteno7_checked.so, compiled with T7_CHECKED=1, a
+ *     stand-in for a memory checker): every cell, row and column index a
+ *     kernel forms for a global-memory access is tested against the extent of
+ *     the array; a failing one is latched, the access is clamped into the
+ *     array, and the next synchronising call returns T7_EINDEX (before any
+ *     other status) with the lowest failing index in t7_last_error().  The
+ *     release build never returns T7_EINDEX.
  *   - A call never aborts the process; it returns a t7_status and, on
  *     failure, t7_last_error() describes the cause.
  */
@@ -54,7 +61,8 @@ typedef enum {
     T7_ENONPHYSICAL = -3, /* rho <= 0, p <= 0 or Roe c^2 <= 0 was met          */
     T7_ENONFINITE = -4,   /* Inf/NaN met (or the "no exist" pattern of Table co3) */
     T7_ETIMEOUT = -5,     /* a bounded device wait gave up                    */
-    T7_ENOMEM = -6        /* workspace allocation failed                      */
+    T7_ENOMEM = -6,       /* workspace allocation failed                      */
+    T7_EINDEX = -7        /* checked build only: an array index failed its check */
 } t7_status;
 
 typedef enum { T7_BC_PERIODIC = 0, T7_BC_ZERO_GRADIENT = 1 /* = transmissive */ } t7_bc;

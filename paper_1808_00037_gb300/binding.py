@@ -9,14 +9,18 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 from pathlib import Path
 
 import numpy as np
 
 PKG = Path(__file__).resolve().parent
-LIB_PATH = PKG / "libteno7.so"
+# the release build; T7_LIBRARY names another build of the same library (the
+# index-checked libteno7_checked.so)
+LIB_PATH = Path(os.environ["T7_LIBRARY"]) if os.environ.get("T7_LIBRARY") else PKG / "libteno7.so"
 
 T7_OK, T7_EINVAL, T7_ECUDA, T7_ENONPHYSICAL, T7_ENONFINITE, T7_ETIMEOUT, T7_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+T7_EINDEX = -7
 T7_BC_PERIODIC, T7_BC_ZERO_GRADIENT = 0, 1
 T7_F64, T7_F32, T7_MIXED = 0, 1, 2
 T7_SCALAR_ADVECTION, T7_EULER1D, T7_EULER2D, T7_BURGERS = 0, 1, 2, 3
@@ -25,7 +29,7 @@ T7_ALPHA_GLOBAL, T7_ALPHA_PER_FIELD = 0, 1
 T7_PROBE_F32, T7_PROBE_F32X2, T7_PROBE_F64 = 0, 1, 2
 
 _STATUS = {0: "T7_OK", -1: "T7_EINVAL", -2: "T7_ECUDA", -3: "T7_ENONPHYSICAL", -4: "T7_ENONFINITE",
-           -5: "T7_ETIMEOUT", -6: "T7_ENOMEM"}
+           -5: "T7_ETIMEOUT", -6: "T7_ENOMEM", -7: "T7_EINDEX"}
 
 
 class T7Error(RuntimeError):

@@ -3,7 +3,9 @@
 Each translation unit is compiled in parallel, then linked into one shared
 library next to this file.  teno7_f64.cu and teno7_slab2d_f64.cu are compiled
 with -fmad=false so that the FP64 path evaluates every expression operation by
-operation.
+operation.  build(checked=True) makes libteno7_checked.so from the same
+sources with T7_CHECKED=1: every array index the kernels form is checked (a
+stand-in for a memory checker, for tests; see include/teno7.h).
 """
 from __future__ import annotations
 
@@ -46,16 +48,18 @@ def _sources_newer_than(target: Path) -> bool:
     return any(p.stat().st_mtime > t for p in deps if p.is_file())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> Path:
-    if not force and not _sources_newer_than(LIB):
-        return LIB
-    BUILD.mkdir(exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> Path:
+    lib = LIB.with_name("libteno7_checked.so") if checked else LIB
+    objdir = BUILD / "checked" if checked else BUILD
+    if not force and not _sources_newer_than(lib):
+        return lib
+    objdir.mkdir(parents=True, exist_ok=True)
     nv = nvcc()
-    extra = extra or []
+    extra = (extra or []) + (["-DT7_CHECKED=1"] if checked else [])
 
     def compile_unit(item):
         src, flags = item
-        obj = BUILD / (Path(src).stem + ".o")
+        obj = objdir / (Path(src).stem + ".o")
         cmd = [nv, *ARCH, *COMMON, *flags, *extra, "-c", str(CSRC / src), "-o", str(obj)]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -68,15 +72,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS.items()))
-    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    tmp = lib.with_suffix(f".{os.getpid()}.tmp")
     cmd = [nv, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                checked="--checked" in sys.argv))

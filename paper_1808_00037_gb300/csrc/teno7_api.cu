@@ -290,6 +290,8 @@ t7_status collect(t7_ctx *c) {
         int zero = 0, big = 0x7fffffff;
         cudaMemcpy(&c->ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(&c->ctl->err_index, &big, sizeof(int), cudaMemcpyHostToDevice);
+        if (err & t7::ERR_INDEX)
+            return fail(c, T7_EINDEX, "index check failed (checked build): index %d", idx);
         if (err & t7::ERR_NONPHYSICAL)
             return fail(c, T7_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or c^2 <= 0) near index %d", idx);
         return fail(c, T7_ENONFINITE, "non-finite state or unreachable stencil pattern near index %d", idx);

@@ -8,7 +8,7 @@ namespace t7 {
 
 enum { SYS_ADV = 0, SYS_EULER1D = 1, SYS_EULER2D = 2, SYS_BURGERS = 3 };
 enum { BC_PERIODIC = 0, BC_ZG = 1 };
-enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4 };
+enum { ERR_NONPHYSICAL = 1, ERR_NONFINITE = 2, ERR_NOEXIST = 4, ERR_INDEX = 8 };
 
 // Device-resident control block of a context.  amax[slot][dir] holds the bit
 // pattern of a non-negative double (max characteristic speed) so that it can

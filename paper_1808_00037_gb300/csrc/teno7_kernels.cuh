@@ -236,6 +236,30 @@ __device__ __forceinline__ void latch_error(DevCtl *ctl, int flag, int index) {
     atomicMin(&ctl->err_index, index);
 }
 
+// Checked build (compiled with T7_CHECKED=1; compute-sanitizer is not
+// available to this project): every cell, row and column index a kernel forms
+// for a global-memory access is tested against the extent of the array it
+// addresses.  An index outside [lo, hi) is latched as ERR_INDEX with its value
+// and replaced by lo, so that the access stays inside the buffer and the
+// launch completes; the host reports T7_EINDEX.  In the release build
+// (T7_CHECKED=0) chk is the identity and adds no instruction.
+#ifndef T7_CHECKED
+#define T7_CHECKED 0
+#endif
+__device__ __forceinline__ int chk(DevCtl *ctl, int i, int lo, int hi) {
+#if T7_CHECKED
+    if (i < lo || i >= hi) {
+        latch_error(ctl, ERR_INDEX, i);
+        return lo;
+    }
+#else
+    (void)ctl;
+    (void)lo;
+    (void)hi;
+#endif
+    return i;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
@@ -484,6 +508,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
             if (gi < 0 || gi >= n) gi = ghost_or_halo(gi, n, A.bc_lo, A.bc_hi, A.halo);
+            gi = chk(ctl, gi, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
             T U[M], F[M];
 #pragma unroll
             for (int k = 0; k < M; k++) U[k] = Us[(size_t)k * cs + gi];
@@ -699,6 +724,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
         for (int k = 0; k < M; k++) fprev[k] = __shfl_up_sync(0xffffffffu, fh[k], 1);
         const int i = j;  // cell i: faces i-1/2 (lane-1) and i+1/2 (this lane)
         if (lane >= 2 && lane <= 30 && i < n) {
+            const int ii = chk(ctl, i, 0, n);
             T r[M];
             if constexpr (F64) {
 #pragma unroll
@@ -710,7 +736,7 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
             }
             if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + ii] = r[k];
             } else {
                 T o[M];
 #pragma unroll
@@ -719,18 +745,18 @@ __device__ __forceinline__ T tiles1d(const TileArgs<T> &A, T (*sU)[WC], T (*sgp)
                     if (A.stage == 0) {
                         o[k] = us + dtT * r[k];
                     } else if (A.stage == 1) {
-                        o[k] = T(0.75) * U0[(size_t)k * cs + i] + T(0.25) * (us + dtT * r[k]);
+                        o[k] = T(0.75) * U0[(size_t)k * cs + ii] + T(0.25) * (us + dtT * r[k]);
                     } else {
                         if constexpr (F64) {
-                            o[k] = T(1.0 / 3.0) * U0[(size_t)k * cs + i] + T(2.0 / 3.0) * (us + dtT * r[k]);
+                            o[k] = T(1.0 / 3.0) * U0[(size_t)k * cs + ii] + T(2.0 / 3.0) * (us + dtT * r[k]);
                         } else {
                             // in FP32, float(1/3) + float(2/3) = 1 + 6e-8 would grow the
                             // solution by that factor every step: use u0 + 2/3 (v - u0)
-                            const T u0 = U0[(size_t)k * cs + i];
+                            const T u0 = U0[(size_t)k * cs + ii];
                             o[k] = fmaf(2.0f / 3.0f, (us + dtT * r[k]) - u0, u0);
                         }
                     }
-                    out[(size_t)k * A.cso + i] = o[k];
+                    out[(size_t)k * A.cso + ii] = o[k];
                 }
                 int wflag = 0;
                 if constexpr (PF) {
@@ -1160,6 +1186,8 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
         if (ga < 0 || ga >= n) ga = ghost_or_halo(ga, n, A.bc_lo, A.bc_hi, A.halo);
         if (gb < 0 || gb >= n) gb = ghost_or_halo(gb, n, A.bc_lo, A.bc_hi, A.halo);
+        ga = chk(ctl, ga, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
+        gb = chk(ctl, gb, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
 #pragma unroll
         for (int k = 0; k < M; k++) {
             ua[k] = Us[(size_t)k * cs + ga];
@@ -1176,7 +1204,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (!A.rhs_mode && A.stage > 0) {
             const int ic = jc < n ? jc : n - 1;
 #pragma unroll
-            for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * cs + (ic < 0 ? 0 : ic)];
+            for (int k = 0; k < M; k++) u0r[k] = U0[(size_t)k * cs + chk(ctl, ic < 0 ? 0 : ic, 0, n)];
         }
         // mixed: the FP64 stage input of the tile's own cells, which the RK
         // update needs unrounded, loaded here so that its latency overlaps the
@@ -1185,7 +1213,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
         if (MIXED && !A.rhs_mode) {
             const int ic = jc < n ? jc : n - 1;
 #pragma unroll
-            for (int k = 0; k < M; k++) usr[k] = Us[(size_t)k * cs + (ic < 0 ? 0 : ic)];
+            for (int k = 0; k < M; k++) usr[k] = Us[(size_t)k * cs + chk(ctl, ic < 0 ? 0 : ic, 0, n)];
         }
         float Ucur[2][M];
 #pragma unroll
@@ -1386,7 +1414,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                     else
                         o[k] = fma(2.0 / 3.0, v, (1.0 / 3.0) * (double)u0r[k]);
                 }
-                out[(size_t)k * A.cso + i] = (S)o[k];
+                out[(size_t)k * A.cso + chk(ctl, i, 0, n)] = (S)o[k];
                 of[k] = to_f32(o[k]);
             }
             if (!A.rhs_mode) {
@@ -1400,7 +1428,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
             for (int k = 0; k < M; k++) r[k] = (fprev[k] - fh[k]) * idx;
             if (A.rhs_mode) {
 #pragma unroll
-                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + i] = r[k];
+                for (int k = 0; k < M; k++) out[(size_t)k * A.cso + chk(ctl, i, 0, n)] = r[k];
             } else {
                 float o[M];
 #pragma unroll
@@ -1415,7 +1443,7 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
                         // grow the solution by 6e-8 every step
                         o[k] = fmaf(2.0f / 3.0f, v - (float)u0r[k], (float)u0r[k]);
                     }
-                    out[(size_t)k * A.cso + i] = (S)o[k];
+                    out[(size_t)k * A.cso + chk(ctl, i, 0, n)] = (S)o[k];
                 }
                 int wflag = 0;
                 wsmax = fmaxf(wsmax, wavespeed1d_fast<SYS>(o, gm1, gamma, a, &wflag));
@@ -1571,6 +1599,7 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
         for (int r = 0; r < 3; r++) {
             int g = c0 - 5 + 32 * r + lane;
             if (g < 0 || g >= n) g = ghost_or_halo(g, n, A.bc_lo, A.bc_hi, A.halo);
+            g = chk(ctl, g, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
 #pragma unroll
             for (int k = 0; k < M; k++) ur[r][k] = (r < 2 || lane < WS2 - 64) ? Us[(size_t)k * cs + g] : 0.f;
         }
@@ -1595,14 +1624,14 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
             if constexpr (U0_ASYNC) {
 #pragma unroll
                 for (int k = 0; k < M; k++) {
-                    cp_async4(&su0[k][lane].x, &U0[(size_t)k * cs + (iA < 0 ? 0 : iA)]);
-                    cp_async4(&su0[k][lane].y, &U0[(size_t)k * cs + iB]);
+                    cp_async4(&su0[k][lane].x, &U0[(size_t)k * cs + chk(ctl, iA < 0 ? 0 : iA, 0, n)]);
+                    cp_async4(&su0[k][lane].y, &U0[(size_t)k * cs + chk(ctl, iB, 0, n)]);
                 }
                 cp_async_commit();
             } else {
 #pragma unroll
                 for (int k = 0; k < M; k++)
-                    u0r[k] = make_float2(U0[(size_t)k * cs + (iA < 0 ? 0 : iA)], U0[(size_t)k * cs + iB]);
+                    u0r[k] = make_float2(U0[(size_t)k * cs + chk(ctl, iA < 0 ? 0 : iA, 0, n)], U0[(size_t)k * cs + chk(ctl, iB, 0, n)]);
             }
         }
         float Ucur[3][M];
@@ -1905,8 +1934,8 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
             if (A.rhs_mode) {
 #pragma unroll
                 for (int k = 0; k < M; k++) {
-                    if (updA) out[(size_t)k * cso + jA] = r[k].x;
-                    if (updB) out[(size_t)k * cso + jB] = r[k].y;
+                    if (updA) out[(size_t)k * cso + chk(ctl, jA, 0, n)] = r[k].x;
+                    if (updB) out[(size_t)k * cso + chk(ctl, jB, 0, n)] = r[k].y;
                 }
             } else {
                 if (U0_ASYNC && use_u0) {
@@ -1926,8 +1955,8 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
                         // grow the solution by 6e-8 every step
                         o[k] = __ffma2_rn(f2(2.0f / 3.0f), __fadd2_rn(v, f2neg(u0r[k])), u0r[k]);
                     }
-                    if (updA) out[(size_t)k * cso + jA] = o[k].x;
-                    if (updB) out[(size_t)k * cso + jB] = o[k].y;
+                    if (updA) out[(size_t)k * cso + chk(ctl, jA, 0, n)] = o[k].x;
+                    if (updB) out[(size_t)k * cso + chk(ctl, jB, 0, n)] = o[k].y;
                 }
                 float oa[M], ob[M];
 #pragma unroll
@@ -2067,7 +2096,7 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const Alpha1D p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
         T Uc[M];
 #pragma unroll
-        for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * cs + i];
+        for (int k = 0; k < M; k++) Uc[k] = U[(size_t)k * cs + chk(p.ctl, i, 0, p.n)];
         int f = 0;
         if constexpr (PF) {
             T w[3];

@@ -222,11 +222,12 @@ __device__ __forceinline__ T alpha_of(const DevCtl *ctl, int slot, int dir) {
 template <bool HALO>
 __device__ __forceinline__ int y_row(int y, const Stage2D &p) {
     if constexpr (HALO) {
-        if (y >= 0 && y < p.ny) return y;
-        return y < -HALO_CELLS ? -HALO_CELLS : (y >= p.ny + HALO_CELLS ? p.ny + HALO_CELLS - 1 : y);
+        if (y < 0 || y >= p.ny)
+            y = y < -HALO_CELLS ? -HALO_CELLS : (y >= p.ny + HALO_CELLS ? p.ny + HALO_CELLS - 1 : y);
+        return chk(p.ctl, y, -HALO_CELLS, p.ny + HALO_CELLS);
     } else {
         if (y < 0 || y >= p.ny) y = ghost_map(y, p.ny, p.bc[2], p.bc[3]);
-        return y;
+        return chk(p.ctl, y, 0, p.ny);
     }
 }
 
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
             if (gi < 0 || gi >= nx) gi = ghost_map(gi, nx, p.bc[0], p.bc[1]);
+            gi = chk(p.ctl, gi, 0, nx);
             T U[4], pr[4], gp[4], gm[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) U[k] = row[(size_t)k * sv + gi];
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) xsweep2d_kernel(const Stage2D p) 
                 } else {
                     r = (fprev[k] - fh[k]) * (1.f / p.f_dx);
                 }
-                R[(size_t)k * N + (size_t)y * nx + j] = r;
+                R[(size_t)k * N + (size_t)y * nx + chk(p.ctl, j, 0, p.nx)] = r;
             }
         }
         __syncwarp();
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
         y = y_row<HALO>(y, p);
         T U[4], pr[4], gp[4], gm[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) U[k] = Us[st_at<HALO>(k, sv, y, nx, x)];
+        for (int k = 0; k < 4; k++) U[k] = Us[st_at<HALO>(k, sv, y, nx, chk(p.ctl, x, 0, p.nx))];
         cell2d<T, 1>(U, gm1, alpha, pr, gp, gm);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) ysweep2d_kernel(const Stage2D p) 
     for (int idx = tid; idx < YB_ROWS * YB_COLS; idx += blockDim.x) {
         const int r = idx / YB_COLS, col = idx % YB_COLS, x = x0 + col, y = r0 + r;
         if (x >= nx || y >= ny) continue;
-        const size_t g = (size_t)y * nx + x;
+        const size_t g = (size_t)chk(p.ctl, y, 0, p.ny) * nx + chk(p.ctl, x, 0, p.nx);
         T o[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -733,6 +735,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
         if (ga < 0 || ga >= nx) ga = ghost_map(ga, nx, p.bc[0], p.bc[1]);
         if (gb < 0 || gb >= nx) gb = ghost_map(gb, nx, p.bc[0], p.bc[1]);
+        ga = chk(p.ctl, ga, 0, nx);
+        gb = chk(p.ctl, gb, 0, nx);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             ua[k] = row[(size_t)k * sv + ga];
@@ -789,9 +793,9 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if constexpr (MIXED)
-                    R[(size_t)k * N + (size_t)y * nx + j] = (to_f64(fprev[k]) - to_f64(fh[k])) * idxD;
+                    R[(size_t)k * N + (size_t)y * nx + chk(p.ctl, j, 0, p.nx)] = (to_f64(fprev[k]) - to_f64(fh[k])) * idxD;
                 else
-                    R[(size_t)k * N + (size_t)y * nx + j] = (fprev[k] - fh[k]) * idx;
+                    R[(size_t)k * N + (size_t)y * nx + chk(p.ctl, j, 0, p.nx)] = (fprev[k] - fh[k]) * idx;
             }
         }
         __syncwarp();
@@ -846,7 +850,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             int y = r0 - 5 + r;
             y = y_row<HALO>(y, p);
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ust[sI][k] = Us[st_at<HALO>(k, sv, y, nx, x)];
+            for (int k = 0; k < 4; k++) Ust[sI][k] = Us[st_at<HALO>(k, sv, y, nx, chk(p.ctl, x, 0, p.nx))];
         }
     }
 #pragma unroll
@@ -924,7 +928,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             const int q = q0 + e * WPB * 32;
             const int r = q / YB_COLS, x = x0 + q % YB_COLS, y = r0 + r;
             if (q < YB_ROWS * YB_COLS && x < nx && y < ny) {
-                const size_t gi = (size_t)y * nx + x;
+                const size_t gi = (size_t)chk(p.ctl, y, 0, p.ny) * nx + chk(p.ctl, x, 0, p.nx);
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     Rv[e][k] = R[(size_t)k * N + gi];
@@ -938,7 +942,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32_kernel(const Stage2D
             const int q = q0 + e * WPB * 32;
             const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col, y = r0 + r;
             if (!(q < YB_ROWS * YB_COLS && x < nx && y < ny)) continue;
-            const size_t gi = (size_t)y * nx + x;
+            const size_t gi = (size_t)chk(p.ctl, y, 0, p.ny) * nx + chk(p.ctl, x, 0, p.nx);
             float of[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -1224,6 +1228,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
             if (lane + 32 * r >= WS2) break;
             int g = c0 - 5 + 32 * r + lane;
             if (g < 0 || g >= nx) g = ghost_map(g, nx, p.bc[0], p.bc[1]);
+            g = chk(p.ctl, g, 0, nx);
 #pragma unroll
             for (int k = 0; k < 4; k++) cp_async4(&sraw[k][32 * r + lane], &row[(size_t)k * sv + g]);
         }
@@ -1298,8 +1303,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float2 r = __fmul2_rn(__fadd2_rn(fprev[k], f2neg(fh[k])), f2(idx));
-                if (updA) Ry[(size_t)k * N + jA] = r.x;
-                if (updB) Ry[(size_t)k * N + jB] = r.y;
+                if (updA) Ry[(size_t)k * N + chk(p.ctl, jA, 0, p.nx)] = r.x;
+                if (updB) Ry[(size_t)k * N + chk(p.ctl, jB, 0, p.nx)] = r.y;
             }
         }
         __syncwarp();  // the next tile overwrites this warp's staging rows
@@ -1362,7 +1367,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
             y = y_row<HALO>(y, p);
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[st_at<HALO>(k, sv, y, nx, x)]);
+                cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[st_at<HALO>(k, sv, y, nx, chk(p.ctl, x, 0, p.nx))]);
         }
         cp_async_commit();
     };
@@ -1434,7 +1439,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
                 const int q = q0 + e * WPB * 32;
                 const int r = q / YB_COLS, x = x0 + q % YB_COLS, y = r0 + r;
                 if (q < YB_ROWS * YB_COLS && x < nx && y < ny) {
-                    const size_t gi = (size_t)y * nx + x;
+                    const size_t gi = (size_t)chk(p.ctl, y, 0, p.ny) * nx + chk(p.ctl, x, 0, p.nx);
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         Rv[e][k] = R[(size_t)k * N + gi];
@@ -1448,7 +1453,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
                 const int q = q0 + e * WPB * 32;
                 const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col, y = r0 + r;
                 if (!(q < YB_ROWS * YB_COLS && x < nx && y < ny)) continue;
-                const size_t gi = (size_t)y * nx + x;
+                const size_t gi = (size_t)chk(p.ctl, y, 0, p.ny) * nx + chk(p.ctl, x, 0, p.nx);
                 float of[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {

@@ -31,6 +31,17 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_checked_build_builds_and_exports_every_declared_symbol():
+    """The index-checked build (T7_CHECKED=1) compiles from the same sources
+    and offers the same entry points (its GPU runs: test_gpu_checked.py)."""
+    from paper_1808_00037_gb300 import build as cuda_build
+    lib_path = cuda_build.build(checked=True)
+    assert lib_path.name == "libteno7_checked.so"
+    lib = ctypes.CDLL(str(lib_path))
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
 def test_binding_binds_every_declared_symbol():
     from paper_1808_00037_gb300 import binding
     lib = binding.load()
