@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
         for (int c = lane; c < WS; c += 32) {
             int gi = c0 - 5 + c;
             if (gi < 0 || gi >= n) gi = ghost_map(gi, n, p.bc_lo, p.bc_hi);
+            gi = chk(p.ctl, gi, 0, n);
             T Uc[3], F[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) Uc[k] = U[(size_t)k * n + gi];
@@ -275,8 +276,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
             T lF[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const T vr = (j + 1 <= n - 1) ? V[(size_t)c * n + (j + 1)] : T(0);
-                const T vl = (j >= 0) ? V[(size_t)c * n + j] : T(0);
+                const T vr = (j + 1 <= n - 1) ? V[(size_t)c * n + chk(p.ctl, j + 1, 0, n)] : T(0);
+                const T vl = (j >= 0) ? V[(size_t)c * n + chk(p.ctl, j, 0, n)] : T(0);
                 lF[c] = sc * ((vr - vl) / dxT);
             }
             T lf[3], lR[3][3];
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
                 lu[0] = T(0.5) * (a10 * s1 + a20 * s2 + alpha * (lgp[0] - lgm[0]));
                 lu[1] = T(0.5) * (s0 + a11 * s1 + a21 * s2 + alpha * (lgp[1] - lgm[1]));
                 lu[2] = T(0.5) * (a12 * s1 + a22 * s2 + alpha * (lgp[2] - lgm[2]));
-                const int cell = ghost_map(j - 3 + t, n, p.bc_lo, p.bc_hi);
+                const int cell = chk(p.ctl, ghost_map(j - 3 + t, n, p.bc_lo, p.bc_hi), 0, n);
 #pragma unroll
                 for (int c = 0; c < 3; c++) add_to(&out[(size_t)c * n + cell], lu[c]);
             }
@@ -335,7 +336,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) rhs_adjoint1d_kernel(const Adjoin
             }
             T lx[6];
             roe_chain(rf, lroe[0], lroe[1], gm1, lx);
-            const int cl = ghost_map(j, n, p.bc_lo, p.bc_hi), cr = ghost_map(j + 1, n, p.bc_lo, p.bc_hi);
+            const int cl = chk(p.ctl, ghost_map(j, n, p.bc_lo, p.bc_hi), 0, n),
+                      cr = chk(p.ctl, ghost_map(j + 1, n, p.bc_lo, p.bc_hi), 0, n);
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 add_to(&out[(size_t)c * n + cl], lx[c]);

@@ -133,6 +133,8 @@ extern "C" t7_status t7_rk3_step_static(const t7_grid *g, void *U, double dt, vo
     if ((e = cudaMemcpyAsync(err, &ctl->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(stream)) != cudaSuccess)
         return report(errbuf, errlen, T7_ECUDA, "status read: %s", cudaGetErrorString(e));
+    if (err[0] & t7::ERR_INDEX)
+        return report(errbuf, errlen, T7_EINDEX, "index check failed (checked build): index %d", err[1]);
     if (err[0] & t7::ERR_NONPHYSICAL)
         return report(errbuf, errlen, T7_ENONPHYSICAL, "non-physical state near index %d", err[1]);
     if (err[0]) return report(errbuf, errlen, T7_ENONFINITE, "non-finite state near index %d", err[1]);

@@ -1,5 +1,6 @@
-"""Runs every form of the forward path through the C ABI at ragged and tiny
-sizes and saves the results: python tests/checked_driver.py <out.npz>.
+"""Runs every form of the forward path, the discrete adjoint and the
+no-allocation step through the C ABI at ragged and tiny sizes and saves the
+results: python tests/checked_driver.py <out.npz>.
 The library is the one binding.LIB_PATH names (T7_LIBRARY: the index-checked
 build).  Any error status -- a failed index check (T7_EINDEX) above all --
 raises.  Used by test_gpu_checked.py, which runs it once with each build."""
@@ -65,6 +66,32 @@ def forms_1d(res):
         c.run(Ug, 0.5, max_steps=5)
         res[f"1d-per-field-{PNAME[prec]}"] = host(Ug)
         c.close()
+
+
+def adjoint_and_static(res):
+    """The discrete adjoint (RHS, RK3 step, recorded step) and the
+    no-allocation step, periodic and zero-gradient."""
+    for name, (U, dx), bc in (("smooth-301", I.random_euler_smooth(9, 301)[:2], (0, 0)),
+                              ("sod-122", I.riemann_tube(122, *I.SOD)[:2], (1, 1))):
+        v = np.random.default_rng(1).standard_normal(U.shape)
+        for prec in (B.T7_F64, B.T7_F32):
+            tag = f"adj-{name}-{PNAME[prec]}"
+            c = B.Context(B.T7_EULER1D, U.shape[1], dx, prec=prec, bc=bc + (0, 0), gamma=1.4)
+            Ug = torch.tensor(U, dtype=DT[prec], device="cuda")
+            vg = torch.tensor(v, dtype=DT[prec], device="cuda")
+            dt = 0.2 * dx
+            res[tag + "-rhs"] = host(c.euler_rhs_adjoint(Ug, vg))
+            lam = vg.clone()
+            res[tag + "-step"] = host(c.rk3_step_adjoint(Ug, dt, lam))
+            tape = torch.empty(c.tape_bytes(), dtype=torch.uint8, device="cuda")
+            U1 = torch.empty_like(Ug)
+            res[tag + "-recorded-U"] = host(c.rk3_step_record(Ug, U1, dt, tape))
+            lam = vg.clone()
+            res[tag + "-recorded"] = host(c.rk3_step_adjoint_recorded(Ug, tape, dt, lam))
+            c.sync()
+            Us = Ug.clone()
+            res[tag + "-static"] = host(c.rk3_step_static(Us, dt))
+            c.close()
 
 
 def slabs_1d(res):
@@ -141,7 +168,7 @@ def slabs_2d(res):
 def main(out):
     B.load()
     res = {}
-    for part in (forms_1d, slabs_1d, batch, forms_2d, slabs_2d):
+    for part in (forms_1d, adjoint_and_static, slabs_1d, batch, forms_2d, slabs_2d):
         part(res)
     torch.cuda.synchronize()
     np.savez(out, **res)

@@ -5,7 +5,8 @@ array, and a failing one returns T7_EINDEX.  checked_driver.py takes every
 form of the forward path through the C ABI at ragged and tiny sizes: 1D
 advection, Burgers and Euler in FP64, FP32 and mixed precision with both
 schemes (N = 3, 61, 97, 122, 200, 759), host-array runs with the parted last
-stage, per-field alphas, slabs of one domain, a ragged batch with tubes of 3
+stage, per-field alphas, the discrete adjoint (RHS, step, recorded step) and
+the no-allocation step, slabs of one domain, a ragged batch with tubes of 3
 to 1000 cells and two group sizes; 2D in every precision at 5 x 7 to
 200 x 233, periodic and transmissive, whole and in slabs.  With the checked
 build it must finish without any error status; its FP64 results equal the
