@@ -81,6 +81,7 @@ def load(path: Path | str | None = None) -> ctypes.CDLL:
         "t7_rk3_step_adjoint_recorded": ([vp, vp, vp, d, vp], i),
         "t7_batch_autotune": ([vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), vp], i),
         "t7_probe_fma": ([i, i, i, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)], i),
+        "t7_probe_index_check": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "t7_slab_alpha": ([vp, vp, vp], i),
         "t7_slab_rhs": ([vp, vp, vp, vp, u8p], i),
         "t7_slab_stage": ([vp, i, vp, vp, vp, vp, d, vp], i),
@@ -356,3 +357,15 @@ def probe_fma(kind: int, iters: int = 4096, repeats: int = 3, stream=None) -> tu
     if st != T7_OK:
         raise T7Error(st, "t7_probe_fma failed")
     return tf.value, ms.value
+
+
+def probe_index_check(i: int, lo: int, hi: int, lib=None) -> tuple[int, bool, bool]:
+    """The index check of the checked build on one index (t7_probe_index_check):
+    (index an access would use, whether the check latched a failure, whether
+    `lib` -- default: the loaded library -- is the checked build)."""
+    lib = lib or load()
+    idx, flagged, checked = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib.t7_probe_index_check(i, lo, hi, ctypes.byref(idx), ctypes.byref(flagged), ctypes.byref(checked))
+    if st != T7_OK:
+        raise T7Error(st, "t7_probe_index_check failed")
+    return idx.value, bool(flagged.value), bool(checked.value)

@@ -16,6 +16,18 @@ cudaError_t launch_batch1d_alpha_f32(const Batch1D &p, double *a, cudaStream_t s
     return launch_batch1d_alpha<float>(p, a, s);
 }
 int batch1d_groups_f32(int group_warps) { return batch1d_groups<float>(group_warps); }
+
+// Self-test of the index check (t7_probe_index_check): one thread passes i
+// through chk against [lo, hi) and writes the index an access would use; no
+// memory is addressed by i.
+__global__ void index_check_probe_kernel(int i, int lo, int hi, DevCtl *ctl, int *out) {
+    out[0] = chk(ctl, i, lo, hi);
+    out[1] = T7_CHECKED;
+}
+cudaError_t launch_index_check_probe(int i, int lo, int hi, DevCtl *ctl, int *out, cudaStream_t s) {
+    index_check_probe_kernel<<<1, 1, 0, s>>>(i, lo, hi, ctl, out);
+    return cudaGetLastError();
+}
 cudaError_t launch_rhs_adjoint1d_f32(const Adjoint1D &p, cudaStream_t s) { return launch_rhs_adjoint1d<float>(p, s); }
 cudaError_t launch_combine_f32(void *out, const void *x, const void *y, const void *z, double c1, double c2,
                                double c3, size_t N, cudaStream_t s) {

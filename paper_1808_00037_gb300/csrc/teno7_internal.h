@@ -115,6 +115,8 @@ struct Alpha2D {
     double *alpha_rec;  // nullable: receives [2] the finished alpha_x, alpha_y
 };
 
+// chk() on one index (teno7_f32.cu): out[0] = the index used, out[1] = T7_CHECKED
+cudaError_t launch_index_check_probe(int i, int lo, int hi, DevCtl *ctl, int *out, cudaStream_t s);
 cudaError_t launch_stage2d_f64(const Stage2D &p, cudaStream_t s);
 cudaError_t launch_stage2d_f32(const Stage2D &p, cudaStream_t s);
 cudaError_t launch_stage2d_mixed(const Stage2D &p, cudaStream_t s);  // FP64 state, FP32 reconstruction

@@ -3,7 +3,9 @@
 // the FP32 (scalar and packed f32x2) and FP64 rates the stage kernels' ALU
 // roofline is taken against.  Not part of the method.
 #include <cuda_runtime.h>
+#include <string.h>
 
+#include "teno7_internal.h"
 #include "teno7_probe.h"
 
 namespace {
@@ -116,5 +118,36 @@ extern "C" t7_status t7_probe_fma(int kind, int iters, int repeats, void *stream
     const double fmas = (double)grid * kThreads * kChains * 16.0 * iters * (kind == T7_PROBE_F32X2 ? 2.0 : 1.0);
     *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
     if (ms) *ms = best;
+    return T7_OK;
+}
+
+extern "C" t7_status t7_probe_index_check(int i, int lo, int hi, int *index_out, int *flagged_out,
+                                          int *checked_build_out) {
+    if (!index_out || !flagged_out || !checked_build_out || lo >= hi) return T7_EINVAL;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(t7::DevCtl) + 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return T7_ENOMEM;
+    }
+    t7::DevCtl *ctl = static_cast<t7::DevCtl *>(buf);
+    int *out = reinterpret_cast<int *>(static_cast<char *>(buf) + sizeof(t7::DevCtl));
+    t7::DevCtl h;
+    memset(&h, 0, sizeof(h));
+    h.err_index = 0x7fffffff;
+    int res[2] = {0, 0};
+    t7_status rc = T7_OK;
+    if (cudaMemcpy(ctl, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
+        t7::launch_index_check_probe(i, lo, hi, ctl, out, 0) != cudaSuccess ||
+        cudaMemcpy(res, out, sizeof(res), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = T7_ECUDA;
+    cudaFree(buf);
+    if (rc != T7_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    *index_out = res[0];
+    *flagged_out = (h.err & t7::ERR_INDEX) && h.err_index == i ? 1 : 0;
+    *checked_build_out = res[1];
     return T7_OK;
 }

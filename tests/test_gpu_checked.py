@@ -53,3 +53,19 @@ def test_checked_build_runs_every_form_and_agrees(tmp_path):
         else:
             scale = max(np.abs(a).max(), 1e-30)
             assert np.abs(a - b).max() <= 1e-4 * scale, (k, np.abs(a - b).max(), scale)
+
+
+@pytest.mark.parametrize("i,lo,hi", [(5, 0, 10), (0, 0, 10), (9, 0, 10), (10, 0, 10), (-1, 0, 10),
+                                     (-4, -4, 20), (-5, -4, 20), (20, -4, 20), (123456, 0, 100)])
+def test_index_check_latches_and_clamps(i, lo, hi):
+    """The check itself (t7_probe_index_check, one index through it on a
+    private control block): in the checked build an index outside [lo, hi)
+    is latched with its value and replaced by lo, one inside passes
+    unchanged; the release build passes every index unchanged and latches
+    nothing."""
+    from paper_1808_00037_gb300 import binding as B
+    inside = lo <= i < hi
+    idx, flagged, checked = B.probe_index_check(i, lo, hi, lib=B.load(build.build(checked=True)))
+    assert checked and idx == (i if inside else lo) and flagged == (not inside)
+    idx, flagged, checked = B.probe_index_check(i, lo, hi, lib=B.load(build.build()))
+    assert not checked and idx == i and not flagged
