@@ -130,7 +130,7 @@ def batch(res):
 
 
 def forms_2d(res):
-    for (nx, ny) in ((5, 7), (37, 29), (70, 45), (200, 233)):
+    for (nx, ny) in ((1, 1), (1, 9), (9, 1), (5, 7), (37, 29), (70, 45), (200, 233)):
         for name, bc in (("quadrants", (1, 1, 1, 1)), ("smooth", (0, 0, 0, 0))):
             if name == "quadrants":
                 U, dx, dy, _ = I.quadrants_2d(4, nx, ny)

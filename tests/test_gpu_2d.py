@@ -44,7 +44,7 @@ def case(name, nx, ny):
 
 
 @pytest.mark.parametrize("name", ["quadrants", "smooth"])
-@pytest.mark.parametrize("nx,ny", [(5, 7), (32, 29), (61, 37), (96, 64)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (2, 3), (5, 7), (32, 29), (61, 37), (96, 64)])
 def test_rhs_2d_f64_bitexact(name, nx, ny):
     U, dx, dy, bc = case(name, nx, ny)
     ro, (ax, ay), (mxo, myo) = oracle.rhs_2d(U, dx, dy, bc=bc, want_masks=True)

@@ -47,18 +47,36 @@ def flux_bound(U, dx, dy):
 @pytest.mark.parametrize("name", ["quadrants", "smooth"])
 @pytest.mark.parametrize("nx,ny", [(5, 7), (61, 37), (96, 64)])
 def test_rhs_2d_f32_against_oracle(name, nx, ny):
+    _rhs_2d_f32(name, nx, ny, 0.999)
+
+
+@pytest.mark.parametrize("name", ["quadrants", "smooth"])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (2, 3)])
+def test_rhs_2d_f32_degenerate_shapes(name, nx, ny):
+    """One column, one row, one cell: the direction of extent 1 sees only
+    copies of the cell itself, so its flux difference vanishes exactly and the
+    RHS is the other direction's; against the oracle as at the other shapes
+    (the Delta codes of so few faces compared at >= 98%)."""
+    rg = _rhs_2d_f32(name, nx, ny, 0.98)
+    if nx == 1 and ny == 1:
+        assert np.all(rg == 0.0)
+
+
+def _rhs_2d_f32(name, nx, ny, codes_equal):
     U, dx, dy, bc = case(name, nx, ny)
     ro, _, (mxo, myo) = oracle.rhs_2d(U, dx, dy, bc=bc, want_masks=True)
     c = ctx(nx, ny, dx, dy, B.T7_F32, bc)
     rg, (mxg, myg) = c.euler_rhs(torch.tensor(U, dtype=torch.float32, device="cuda"), want_masks=True)
     c.sync()
     mxg, myg = mxg.cpu().numpy(), myg.cpu().numpy()
-    assert (mxg == mxo).mean() >= 0.999 and (myg == myo).mean() >= 0.999
+    assert (mxg == mxo).mean() >= codes_equal and (myg == myo).mean() >= codes_equal
     okx = np.all(mxg == mxo, axis=(0, 1))  # [ny, nx+1]
     oky = np.all(myg == myo, axis=(0, 1))  # [nx, ny+1]
     cell_ok = okx[:, :-1] & okx[:, 1:] & (oky[:, :-1] & oky[:, 1:]).T
-    err = np.abs(rg.double().cpu().numpy() - ro)[:, cell_ok]
-    assert np.max(err) <= flux_bound(U, dx, dy)
+    rg = rg.double().cpu().numpy()
+    err = np.abs(rg - ro)[:, cell_ok]
+    assert cell_ok.any() and np.max(err) <= flux_bound(U, dx, dy)
+    return rg
 
 
 @pytest.mark.parametrize("name", ["quadrants", "smooth"])
