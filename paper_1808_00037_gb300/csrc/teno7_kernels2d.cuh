@@ -1535,13 +1535,16 @@ cudaError_t launch_stage2d_paired(const Stage2D &p, cudaStream_t st) {
         const long cap = (long)num_sms() * 2;
         ysweep2d_f32p_kernel<S, HALO><<<(int)(nb < cap ? nb : cap), WPB * 32, smem, st>>>(p);
         return cudaGetLastError();
+    } else {
+        // mixed precision (FP64 state): one block per CTA
+        const size_t smem = ysweep_f32_smem_bytes<S>();
+        e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
+        ysweep2d_f32_kernel<S, HALO><<<grid, WPB * 32, smem, st>>>(p);
+        return cudaGetLastError();
     }
-    const size_t smem = ysweep_f32_smem_bytes<S>();
-    e = cudaFuncSetAttribute(ysweep2d_f32_kernel<S, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((p.nx + YB_COLS - 1) / YB_COLS, (p.ny + YB_ROWS - 1) / YB_ROWS);
-    ysweep2d_f32_kernel<S, HALO><<<grid, WPB * 32, smem, st>>>(p);
-    return cudaGetLastError();
 }
 
 template <typename T, bool HALO = false>
