@@ -1184,14 +1184,17 @@ __device__ __forceinline__ float tiles1d_f32(const TileArgs<float> &A, float (*s
     auto load_tile = [&](int tile) {
         const int c0 = tile * WT;
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
-        if (ga < 0 || ga >= n) ga = ghost_or_halo(ga, n, A.bc_lo, A.bc_hi, A.halo);
-        if (gb < 0 || gb >= n) gb = ghost_or_halo(gb, n, A.bc_lo, A.bc_hi, A.halo);
-        ga = chk(ctl, ga, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
-        gb = chk(ctl, gb, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0));
+        if (!(c0 >= 5 && c0 + WS - 5 <= n)) {
+            // a staged cell outside the grid (first and last tiles; warp-uniform)
+            if (ga < 0 || ga >= n) ga = ghost_or_halo(ga, n, A.bc_lo, A.bc_hi, A.halo);
+            if (gb < 0 || gb >= n) gb = ghost_or_halo(gb, n, A.bc_lo, A.bc_hi, A.halo);
+        }
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            ua[k] = Us[(size_t)k * cs + ga];
-            ub[k] = (lane < WS - 32) ? Us[(size_t)k * cs + gb] : S(0);
+            ua[k] = Us[(size_t)k * cs + chk(ctl, ga, A.halo ? -HALO_CELLS : 0, n + (A.halo ? HALO_CELLS : 0))];
+            ub[k] = (lane < WS - 32) ? Us[(size_t)k * cs + chk(ctl, gb, A.halo ? -HALO_CELLS : 0,
+                                                               n + (A.halo ? HALO_CELLS : 0))]
+                                     : S(0);
         }
     };
     int tile = tile0;
@@ -1595,6 +1598,17 @@ __device__ __forceinline__ float tiles1d_f32_fp(const TileArgs<float> &A, float2
     float ur[3][M];
     auto load_tile = [&](int tile) {
         const int c0 = tile * WT2;
+        if (c0 >= 5 && c0 + WS2 - 5 <= n) {
+            // every staged cell inside the grid (warp-uniform): no boundary map
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                const int g = c0 - 5 + 32 * r + lane;
+#pragma unroll
+                for (int k = 0; k < M; k++)
+                    ur[r][k] = (r < 2 || lane < WS2 - 64) ? Us[(size_t)k * cs + chk(ctl, g, 0, n)] : 0.f;
+            }
+            return;
+        }
 #pragma unroll
         for (int r = 0; r < 3; r++) {
             int g = c0 - 5 + 32 * r + lane;

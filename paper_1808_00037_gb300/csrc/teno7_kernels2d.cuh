@@ -1223,11 +1223,12 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
         const int y = (int)(tile / ntx);
         const int c0 = (int)(tile % ntx) * WT2;
         const float *row = Us + (size_t)y * nx;
+        const bool inside = c0 >= 5 && c0 + WS2 - 5 <= nx;  // every staged cell in the row (warp-uniform)
 #pragma unroll
         for (int r = 0; r < 3; r++) {
             if (lane + 32 * r >= WS2) break;
             int g = c0 - 5 + 32 * r + lane;
-            if (g < 0 || g >= nx) g = ghost_map(g, nx, p.bc[0], p.bc[1]);
+            if (!inside && (g < 0 || g >= nx)) g = ghost_map(g, nx, p.bc[0], p.bc[1]);
             g = chk(p.ctl, g, 0, nx);
 #pragma unroll
             for (int k = 0; k < 4; k++) cp_async4(&sraw[k][32 * r + lane], &row[(size_t)k * sv + g]);
@@ -1360,11 +1361,12 @@ __global__ void __launch_bounds__(WPB * 32, 2) ysweep2d_f32p_kernel(const Stage2
     // columns beyond it skipped)
     auto copy_block = [&](int b) {
         const int x0 = (b % nbx) * YB_COLS, r0 = (b / nbx) * YB_ROWS;
+        const bool inside = r0 >= 5 && r0 + YB_STAGE - 5 <= ny;  // every staged row in the grid (CTA-uniform)
         for (int q = tid; q < YB_STAGE * YB_COLS; q += WPB * 32) {
             const int r = q / YB_COLS, col = q % YB_COLS, x = x0 + col;
             if (x >= nx) continue;
             int y = r0 - 5 + r;
-            y = y_row<HALO>(y, p);
+            y = inside ? chk(p.ctl, y, 0, ny) : y_row<HALO>(y, p);
 #pragma unroll
             for (int k = 0; k < 4; k++)
                 cp_async4(&s_in[(k * YB_STAGE + r) * YB_COLS + col], &Us[st_at<HALO>(k, sv, y, nx, chk(p.ctl, x, 0, p.nx))]);
