@@ -60,7 +60,7 @@ EXEC_FLOPS_PER_CELL_STAGE = {"f32": 584.4, "f64": 812.0}
 # DRAM bytes per stage launch per cell measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, averaged over the three stage launches of one RK3
 # step at N = 16,777,600) for the current kernels; None when not captured.
-TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.53, "f64": None}
+TRAFFIC_PER_CELL_LAUNCH = {"f32": 29.50, "f64": None}
 
 
 def peaks():
