@@ -728,9 +728,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
     // one tile ahead, held in the state type and rounded to float only when
     // the tile is used (a mixed-precision load is then not waited for at once)
     S ua[4], ub[4];
-    auto load_tile = [&](long tile) {
-        const int y = (int)(tile / ntx);
-        const int c0 = (int)(tile % ntx) * WT;
+    auto load_tile = [&](int y, int tx) {
+        const int c0 = tx * WT;
         const S *row = Us + (size_t)y * nx;
         int ga = c0 - 5 + lane, gb = c0 - 5 + 32 + lane;
         if (ga < 0 || ga >= nx) ga = ghost_map(ga, nx, p.bc[0], p.bc[1]);
@@ -743,19 +742,34 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32_kernel(const Stage2D
             ub[k] = (lane < WS - 32) ? row[(size_t)k * sv + gb] : S(0);
         }
     };
-    const long tstride = (long)gridDim.x * WPB;
-    long tile = (long)blockIdx.x * WPB + warp;
-    if (tile < ntiles) load_tile(tile);
-    for (; tile < ntiles; tile += tstride) {
-        const int y = (int)(tile / ntx);
-        const int c0 = (int)(tile % ntx) * WT;
+    // the warp's tiles as row and tile column, stepped instead of divided out
+    // of a tile index every tile (as in the paired x sweep)
+    const long tstride = (long)gridDim.x * WPB, tile0 = (long)blockIdx.x * WPB + warp;
+    const int step_y = (int)(tstride / ntx), step_x = (int)(tstride % ntx);
+    auto next = [&](int &ty, int &tx) {
+        ty += step_y;
+        tx += step_x;
+        if (tx >= ntx) {
+            tx -= ntx;
+            ty += 1;
+        }
+    };
+    int ty = tile0 < ntiles ? (int)(tile0 / ntx) : ny, tx = tile0 < ntiles ? (int)(tile0 % ntx) : 0;
+    if (ty < ny) load_tile(ty, tx);
+    for (; ty < ny; next(ty, tx)) {
+        const int y = ty;
+        const int c0 = tx * WT;
         float cur[2][4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             cur[0][k] = to_f32(ua[k]);
             cur[1][k] = to_f32(ub[k]);
         }
-        if (tile + tstride < ntiles) load_tile(tile + tstride);
+        {
+            int ty1 = ty, tx1 = tx;
+            next(ty1, tx1);
+            if (ty1 < ny) load_tile(ty1, tx1);
+        }
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int c = lane + 32 * r;
@@ -1219,9 +1233,8 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
     __syncthreads();
     // raw state of the staged cells of a tile (rounds r = 0, 1, 2: cells
     // c0-5+32r+lane) into sraw by asynchronous copies, one tile ahead
-    auto copy_tile = [&](long tile) {
-        const int y = (int)(tile / ntx);
-        const int c0 = (int)(tile % ntx) * WT2;
+    auto copy_tile = [&](int y, int tx) {
+        const int c0 = tx * WT2;
         const float *row = Us + (size_t)y * nx;
         const bool inside = c0 >= 5 && c0 + WS2 - 5 <= nx;  // every staged cell in the row (warp-uniform)
 #pragma unroll
@@ -1235,12 +1248,24 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
         }
         cp_async_commit();
     };
-    const long tstride = (long)gridDim.x * WPB;
-    long tile = (long)blockIdx.x * WPB + warp;
-    if (tile < ntiles) copy_tile(tile);
-    for (; tile < ntiles; tile += tstride) {
-        const int y = (int)(tile / ntx);
-        const int c0 = (int)(tile % ntx) * WT2;
+    // the warp's tiles (row-major, grid-stride) as row and tile column,
+    // stepped by the stride's rows and columns instead of divided out of a
+    // tile index every tile
+    const long tstride = (long)gridDim.x * WPB, tile0 = (long)blockIdx.x * WPB + warp;
+    const int step_y = (int)(tstride / ntx), step_x = (int)(tstride % ntx);
+    auto next = [&](int &ty, int &tx) {
+        ty += step_y;
+        tx += step_x;
+        if (tx >= ntx) {
+            tx -= ntx;
+            ty += 1;
+        }
+    };
+    int ty = tile0 < ntiles ? (int)(tile0 / ntx) : ny, tx = tile0 < ntiles ? (int)(tile0 % ntx) : 0;
+    if (ty < ny) copy_tile(ty, tx);
+    for (; ty < ny; next(ty, tx)) {
+        const int y = ty;
+        const int c0 = tx * WT2;
         cp_async_wait_all();
         __syncwarp();
         float cur[3][4];
@@ -1249,7 +1274,11 @@ __global__ void __launch_bounds__(WPB * 32, 2) xsweep2d_f32fp_kernel(const Stage
 #pragma unroll
             for (int k = 0; k < 4; k++) cur[r][k] = (lane + 32 * r < WS2) ? sraw[k][32 * r + lane] : 0.f;
         __syncwarp();  // every lane has read sraw before the next tile's copies land in it
-        if (tile + tstride < ntiles) copy_tile(tile + tstride);
+        {
+            int ty1 = ty, tx1 = tx;
+            next(ty1, tx1);
+            if (ty1 < ny) copy_tile(ty1, tx1);
+        }
         // primitives and split fluxes of the staged cells; after round r >= 1
         // lane l writes pair l + 32 (r - 1) = (round r - 1, round r)
         float vpr[2][4], vgp[2][4], vgm[2][4];
