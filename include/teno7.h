@@ -117,18 +117,27 @@ typedef struct {
 
 typedef struct t7_ctx t7_ctx;
 
-/* Create a context on the current CUDA device bound to `stream` (a
+/* Context management (t7_create .. t7_sync) has no counterpart in the paper:
+ * it holds the problem statement of Sec. 2 (the grid, the conservation law,
+ * the boundary conditions) and the device workspace the other calls use.
+ *
+ * Create a context on the current CUDA device bound to `stream` (a
  * cudaStream_t; NULL = the legacy default stream).  Allocates the workspace
  * (3 state-sized buffers + a control block).  On success *out owns it. */
 t7_status t7_create(const t7_grid *grid, void *stream, t7_ctx **out);
+/* Free the context and its workspace (T7_EINVAL for NULL).  The caller makes
+ * sure no work of the context is still queued.  (Context management: no
+ * counterpart in the paper.) */
 t7_status t7_destroy(t7_ctx *ctx);
 /* Later calls run on `stream`.  Work already queued on the previous stream is
  * ordered before them (the new stream waits on an event recorded on the old
- * one), so the switch needs no synchronisation by the caller. */
+ * one), so the switch needs no synchronisation by the caller.  (Context
+ * management: no counterpart in the paper.) */
 t7_status t7_set_stream(t7_ctx *ctx, void *stream);
-/* Last error message of this context (never NULL). */
+/* Last error message of this context (never NULL; no counterpart in the paper). */
 const char *t7_last_error(const t7_ctx *ctx);
-/* Block until the stream is idle; return and clear any latched device error. */
+/* Block until the stream is idle; return and clear any latched device error
+ * (no counterpart in the paper). */
 t7_status t7_sync(t7_ctx *ctx);
 
 /* Scalar TENO7-ext reconstruction of one sequence of point values
@@ -172,19 +181,25 @@ t7_status t7_cfl_dt(t7_ctx *ctx, const void *U, double cfl, double *dt_out);
  * the next synchronising call. */
 t7_status t7_rk3_step(t7_ctx *ctx, void *U, double dt);
 
-/* March device U in place until t_end (last step clipped to land on it) or
- * max_steps steps, dt = CFL dx / alpha(U^n) computed on the device each step.
- * t_end may be +inf.  Synchronises; steps_out / t_out (host, nullable). */
+/* March device U in place with t7_rk3_step's SSP-RK3 steps (Sec. 2.1) until
+ * t_end (last step clipped to land on it) or max_steps steps, each step's dt
+ * the CFL step of t7_cfl_dt (Sec. "One dimensional Euler equations"),
+ * dt = CFL dx / alpha(U^n), computed on the device.  t_end may be +inf.
+ * Synchronises; steps_out / t_out (host, nullable). */
 t7_status t7_run(t7_ctx *ctx, void *U, double cfl, double t_end, int max_steps, int *steps_out, double *t_out);
 
-/* As t7_run on a HOST array U_host ([m][nx], context precision; pageable or
- * page-locked): copies it to the context's device state, runs, copies the
- * result back.  With t_end = +inf (a known step count) on a 1D system the
+/* As t7_run (SSP-RK3 steps of Sec. 2.1 at the CFL step) on a HOST array U_host ([m][nx],
+ * context precision; pageable or page-locked): copies it to the context's
+ * device state, runs, copies the result back.  With t_end = +inf (a known step count) on a 1D system the
  * result leaves in parts while the last stage computes.  Synchronises. */
 t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int max_steps, int *steps_out,
                       double *t_out);
 
-/* Discrete adjoint of t7_euler_rhs for 1D Euler: out = (dL/dU)^T v at the
+/* The paper has no adjoint; the adjoint calls differentiate its scheme (the
+ * RHS of Eq. app with the TENO7-ext selection frozen, and the SSP-RK3 step of
+ * Sec. 2.1) exactly.
+ *
+ * Discrete adjoint of t7_euler_rhs for 1D Euler: out = (dL/dU)^T v at the
  * state U, with the stencil selection (every Delta_i of both splits and all
  * fields) and the global Lax-Friedrichs alpha frozen at their values for U;
  * the Roe frame, the characteristic projection, the split fluxes and the flux
@@ -193,7 +208,7 @@ t7_status t7_run_host(t7_ctx *ctx, void *U_host, double cfl, double t_end, int m
  * selection is the forward kernel's bit for bit.) */
 t7_status t7_euler_rhs_adjoint(t7_ctx *ctx, const void *U, const void *v, void *out);
 
-/* Adjoint of one SSP-RK3 step of size dt from the state U (the step's start,
+/* Adjoint of one SSP-RK3 step (Sec. 2.1) of size dt from the state U (the step's start,
  * unchanged): recomputes the stage states, then maps lambda (device [3][nx],
  * the adjoint of the step's result) in place to the adjoint of U:
  *   U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U3 = 1/3 U + 2/3 (U2 + dt L(U2))
@@ -201,7 +216,7 @@ t7_status t7_euler_rhs_adjoint(t7_ctx *ctx, const void *U, const void *v, void *
 t7_status t7_rk3_step_adjoint(t7_ctx *ctx, const void *U, double dt, void *lambda);
 
 /* Recorded steps, for reverse sweeps that replay a segment forward first
- * (checkpointing).  A tape entry holds one step's stage states U1 and U2, the
+ * (checkpointing; no counterpart in the paper: the step is Sec. 2.1's).  A tape entry holds one step's stage states U1 and U2, the
  * forward Delta codes of its three stage states and their three alphas.
  * t7_tape_bytes: size of one entry for this context (a multiple of 256).
  * t7_rk3_step_record: one SSP-RK3 step of fixed dt from U_in to U_out (device
@@ -245,7 +260,8 @@ t7_status t7_rk3_step_adjoint_recorded(t7_ctx *ctx, const void *U_in, const void
 t7_status t7_batch_run(t7_ctx *ctx, void *U, const int64_t *offsets, const double *dx, int ntubes, double t_end,
                        double cfl, int max_steps, int group_warps, int *steps_out, double *t_out);
 
-/* Autotuner of the batch tile shape: times trial_steps steps of every tube
+/* Autotuner of the batch tile shape (no counterpart in the paper; the
+ * scheme is t7_batch_run's): times trial_steps steps of every tube
  * for group_warps = 1, 2, 4, 8 on a device copy of U (U is not modified),
  * keeps the fastest in the context for later t7_batch_run calls, and returns
  * it in *group_out (nullable); ms_out (nullable, 4 floats) receives the trial
@@ -299,7 +315,8 @@ t7_status t7_slab_rhs(t7_ctx *ctx, const void *U, const double *alpha, void *dUd
 t7_status t7_slab_stage(t7_ctx *ctx, int k, const void *Us, const void *U0, void *out, const double *alpha, double dt,
                         double *alpha_out);
 
-/* The paper has no counterpart to this call: it serves callers that cannot
+/* The paper has no counterpart to this call (its step is t7_rk3_step's, Sec.
+ * 2.1): it serves callers that cannot
  * allocate device memory -- plug-ins whose host application owns every device
  * allocation, real-time loops that forbid allocation after start-up, and
  * processes whose device memory is budgeted by an external allocator.

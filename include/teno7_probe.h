@@ -16,7 +16,8 @@ extern "C" {
 
 enum { T7_PROBE_F32 = 0, T7_PROBE_F32X2 = 1, T7_PROBE_F64 = 2 };
 
-/* FMA throughput of the device in TFLOP/s (2 flop per fused multiply-add):
+/* FMA throughput of the device in TFLOP/s (2 flop per fused multiply-add; no
+ * counterpart in the paper, which reports no performance figures):
  * every SM filled with CTAs of 256 threads, each running 8 independent
  * chains of 16 x iters FMAs (kind T7_PROBE_F32: scalar FP32; T7_PROBE_F32X2:
  * packed f32x2 FMAs, two per instruction; T7_PROBE_F64: FP64), one warm-up
@@ -28,7 +29,8 @@ enum { T7_PROBE_F32 = 0, T7_PROBE_F32X2 = 1, T7_PROBE_F64 = 2 };
  * CUDA call fails. */
 t7_status t7_probe_fma(int kind, int iters, int repeats, void *stream, double *tflops, float *ms);
 
-/* Self-test of the index check of the checked build (see teno7.h): one
+/* Self-test of the index check of the checked build (see teno7.h; no
+ * counterpart in the paper): one
  * device thread passes index i through the check against [lo, hi) on a
  * private control block, as every kernel does for the indices it forms.
  *   index_out          host, receives the index an access would use: i, or,
