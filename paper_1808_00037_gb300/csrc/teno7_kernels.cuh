@@ -34,6 +34,10 @@
 // pairs two faces of a 61-cell tile (lane l: faces c0-2+l and c0+30+l) and runs
 // the splits one after the other (whole-domain and slab launches of the FP32
 // state).  Both give the same bits.
+// Grids cover whole waves of each kernel's resident CTAs (stage_grid); the
+// loads of a tile take the boundary map only where a staged cell lies outside
+// the grid; every index formed for a global access passes through chk(),
+// which the checked build (T7_CHECKED=1) turns into a bounds check.
 #pragma once
 #include <math.h>
 #include <stdint.h>
